@@ -1,0 +1,269 @@
+"""FP64 CPU oracle for the implicit randomized SVD (arXiv 2111.06312).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use this package; the product path never does.
+It shares no code with the CUDA path (``paper_2111_06312_gb300/csrc``).
+
+The arithmetic lives in ``isvd_oracle.c`` (plain FP64 loops, one function per
+definition in the paper); this module compiles it with gcc and marshals numpy
+arrays through ctypes.  The metric helpers at the bottom (principal angles,
+residuals) use numpy as a library primitive.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "isvd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, OpenMP, strict IEEE) and return the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                               "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Op(C.Structure):
+    _fields_ = [
+        ("form", C.c_int32), ("norm", C.c_int32), ("n", C.c_int64),
+        ("rowptr", C.c_void_p), ("colidx", C.c_void_p), ("aval", C.c_void_p),
+        ("degree", C.c_int32), ("coeff", C.c_void_p),
+        ("ones_coeff", C.c_double), ("adj_coeff", C.c_double),
+        ("d", C.c_int64), ("L", C.c_int32),
+        ("xrowptr", C.c_void_p), ("xcolidx", C.c_void_p), ("xval", C.c_void_p),
+        ("xdense", C.c_void_p),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.c_void_p
+            L.orc_apply.argtypes = [P, P, C.c_int64, P, C.c_int]
+            L.orc_explicit.argtypes = [P, P]
+            L.orc_rows.argtypes = [P]
+            L.orc_rows.restype = C.c_int64
+            L.orc_cols.argtypes = [P]
+            L.orc_cols.restype = C.c_int64
+            L.orc_philox4x32_10.argtypes = [P, P, P]
+            L.orc_gaussian.argtypes = [C.c_uint64, C.c_int64, C.c_int64, P, C.c_int64]
+            L.orc_cholesky.argtypes = [P, C.c_int64, P]
+            L.orc_cholqr.argtypes = [P, C.c_int64, C.c_int64, C.c_double, P]
+            L.orc_cholqr2.argtypes = [P, C.c_int64, C.c_int64, P]
+            L.orc_householder_qr.argtypes = [P, C.c_int64, C.c_int64, P]
+            L.orc_jacobi_svd.argtypes = [P, C.c_int64, C.c_int64, P, P, P, C.c_double, C.c_int]
+            L.orc_isvd.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P, P, P]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Operator:
+    """Implicit design matrix.  ``form='poly'``: sum_k c_k N^k + alpha 11^T +
+    beta A (Eq. 3 with alpha = -lambda, beta = +lambda).  ``form='concat'``:
+    [X | NX | ... | N^L X] (Eq. 6).  ``norm='row'``: N = T = D^-1 A;
+    ``norm='sym'``: N = Â = (D+I)^-1/2 (A+I) (D+I)^-1/2 (Sec. 2)."""
+
+    def __init__(self, n, rowptr, colidx, *, form="poly", norm="row", values=None,
+                 coeffs=(), ones_coeff=0.0, adj_coeff=0.0,
+                 X=None, L=0):
+        self._keep = []
+
+        def keep(a):
+            self._keep.append(a)
+            return a
+
+        s = _Op()
+        s.form = 0 if form == "poly" else 1
+        s.norm = 0 if norm == "row" else 1
+        s.n = int(n)
+        s.rowptr = _p(keep(np.ascontiguousarray(rowptr, dtype=np.int32)))
+        s.colidx = _p(keep(np.ascontiguousarray(colidx, dtype=np.int32)))
+        s.aval = _p(keep(_f64(values))) if values is not None else None
+        c = keep(_f64(np.asarray(coeffs, dtype=np.float64).reshape(-1)))
+        s.degree = len(c)
+        s.coeff = _p(c) if len(c) else None
+        s.ones_coeff = float(ones_coeff)
+        s.adj_coeff = float(adj_coeff)
+        s.L = int(L)
+        if X is not None:
+            if isinstance(X, np.ndarray):
+                s.d = X.shape[1]
+                s.xdense = _p(keep(_f64(X)))
+            else:  # (d, rowptr, colidx, values)
+                d, xr, xc, xv = X
+                s.d = int(d)
+                s.xrowptr = _p(keep(np.ascontiguousarray(xr, dtype=np.int32)))
+                s.xcolidx = _p(keep(np.ascontiguousarray(xc, dtype=np.int32)))
+                s.xval = _p(keep(_f64(xv)))
+        self.s = s
+        self.form = form
+        self.norm = norm
+
+    @property
+    def _ptr(self):
+        return C.addressof(self.s)
+
+    @property
+    def shape(self):
+        return int(lib().orc_rows(self._ptr)), int(lib().orc_cols(self._ptr))
+
+    def apply(self, G, transpose=False):
+        r, c = self.shape
+        G = _f64(G)
+        squeeze = G.ndim == 1
+        if squeeze:
+            G = G[:, None]
+        assert G.shape[0] == (r if transpose else c)
+        out = np.empty(((c if transpose else r), G.shape[1]), dtype=np.float64)
+        lib().orc_apply(self._ptr, _p(G), G.shape[1], _p(out), 1 if transpose else 0)
+        return out[:, 0] if squeeze else out
+
+    def explicit(self):
+        r, c = self.shape
+        M = np.empty((r, c), dtype=np.float64)
+        lib().orc_explicit(self._ptr, _p(M))
+        return M
+
+    def isvd(self, k, p, iters, seed):
+        """Alg. 1 in FP64: returns U (r x k), S (k), V (c x k), passes."""
+        r, c = self.shape
+        U = np.empty((r, k))
+        S = np.empty(k)
+        V = np.empty((c, k))
+        info = np.zeros(4, dtype=np.int32)
+        rc = lib().orc_isvd(self._ptr, k, p, iters, C.c_uint64(seed), _p(U), _p(S), _p(V), _p(info))
+        if rc != 0:
+            raise RuntimeError(f"oracle isvd failed ({rc})")
+        return U, S, V, int(info[0])
+
+
+def graph_operator(g, **kw) -> Operator:
+    return Operator(g.n, g.rowptr, g.colidx, **kw)
+
+
+def ne_coefficients(C_window: int) -> np.ndarray:
+    """c_q = 2 (C - q + 1) / (C (C + 1)), q = 1..C: the context distribution of
+    Sec. 2.1 normalised to sum 1 (Fig. 1 uses [3, 2, 1]/6 for C = 3)."""
+    q = np.arange(1, C_window + 1, dtype=np.float64)
+    return 2.0 * (C_window - q + 1) / (C_window * (C_window + 1))
+
+
+def philox4x32_10(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def gaussian(seed, rows, cols):
+    out = np.empty((rows, cols))
+    lib().orc_gaussian(C.c_uint64(seed), rows, cols, _p(out), cols)
+    return out
+
+
+def cholesky(W):
+    W = _f64(W)
+    Lf = np.empty_like(W)
+    info = lib().orc_cholesky(_p(W), W.shape[0], _p(Lf))
+    return Lf, info
+
+
+def cholqr(Q, shift=0.0):
+    Q = _f64(Q).copy()
+    R = np.empty((Q.shape[1], Q.shape[1]))
+    info = lib().orc_cholqr(_p(Q), Q.shape[0], Q.shape[1], shift, _p(R))
+    return Q, R, info
+
+
+def cholqr2(Q):
+    Q = _f64(Q).copy()
+    R = np.empty((Q.shape[1], Q.shape[1]))
+    passes = lib().orc_cholqr2(_p(Q), Q.shape[0], Q.shape[1], _p(R))
+    return Q, R, passes
+
+
+def householder_qr(Q):
+    Q = _f64(Q).copy()
+    R = np.empty((Q.shape[1], Q.shape[1]))
+    lib().orc_householder_qr(_p(Q), Q.shape[0], Q.shape[1], _p(R))
+    return Q, R
+
+
+def jacobi_svd(A, tol=1e-15, max_sweeps=100):
+    """A (r x c, r >= c) = U diag(S) V^T, S descending."""
+    A = _f64(A)
+    r, c = A.shape
+    assert r >= c
+    U = np.empty((r, c))
+    S = np.empty(c)
+    V = np.empty((c, c))
+    sweeps = lib().orc_jacobi_svd(_p(A), r, c, _p(U), _p(S), _p(V), tol, max_sweeps)
+    if sweeps < 0:
+        raise RuntimeError("Jacobi did not converge")
+    return U, S, V
+
+
+def svd_any(A):
+    """Jacobi SVD for either orientation (wide matrices via the transpose)."""
+    A = _f64(A)
+    if A.shape[0] >= A.shape[1]:
+        return jacobi_svd(A)
+    U, S, V = jacobi_svd(A.T)
+    return V, S, U
+
+
+def num_threads() -> int:
+    lib()
+    return int(C.CDLL(_LIB_PATH).orc_num_threads())
+
+
+# ---- metrics ----------------------------------------------------------------
+
+def sin_principal_angles(U_ref, U):
+    """sin of the principal angles between span(U_ref) and span(U) (both with
+    orthonormal columns): singular values of (I - U_ref U_ref^T) U."""
+    U_ref = np.asarray(U_ref, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    Qr, _ = np.linalg.qr(U_ref)
+    Qu, _ = np.linalg.qr(U)
+    P = Qu - Qr @ (Qr.T @ Qu)
+    return np.linalg.svd(P, compute_uv=False)
+
+
+def max_principal_angle(U_ref, U) -> float:
+    s = sin_principal_angles(U_ref, U)
+    return float(np.arcsin(min(1.0, float(s.max())))) if len(s) else 0.0
+
+
+def residuals(op: Operator, U, S, V):
+    """r_i = max(||M v_i - s_i u_i||, ||M^T u_i - s_i v_i||), FP64 products."""
+    MV = op.apply(V, transpose=False)
+    MtU = op.apply(U, transpose=True)
+    r1 = np.linalg.norm(MV - U * S[None, :], axis=0)
+    r2 = np.linalg.norm(MtU - V * S[None, :], axis=0)
+    return np.maximum(r1, r2)

@@ -1,0 +1,406 @@
+"""Pins for the FP64 oracle: each check ties an oracle function to something
+other than itself (a published value, a closed form, LAPACK, an exact
+invariant), so that a dropped term, a wrong sign or index or a transposed
+operand in the oracle fails at least one of them.  CPU only."""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.stats
+
+import oracle
+from paper_2111_06312_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+LAM = 0.05
+C5 = oracle.ne_coefficients(5)
+
+
+def poly(c, x):
+    return sum(c[k] * x ** (k + 1) for k in range(len(c)))
+
+
+# ---- Philox / Box-Muller (start block of Alg. 1) ----------------------------
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_gaussian_is_standard_normal():
+    z = oracle.gaussian(7, 4096, 48).ravel()
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+    assert scipy.stats.kstest(z, "norm").pvalue > 1e-3
+    # columns are uncorrelated
+    Z = oracle.gaussian(11, 20000, 8)
+    C = np.corrcoef(Z.T)
+    assert np.abs(C - np.eye(8)).max() < 0.04
+
+
+def test_gaussian_prefix_and_seed():
+    # element (i, j) depends only on (seed, i, j): a narrower block is a prefix
+    a = oracle.gaussian(5, 50, 42)
+    b = oracle.gaussian(5, 50, 40)
+    assert np.array_equal(a[:, :40], b)
+    assert not np.allclose(oracle.gaussian(6, 50, 40), b)
+
+
+# ---- coefficients (Eq. 3 read with Fig. 1) ----------------------------------
+
+def test_context_weights_match_fig1():
+    for l in open(os.path.join(GOLD, "fig1_context_weights.txt")):
+        if not l.strip() or l[0] == "#":
+            continue
+        parts = l.split()
+        Cw = int(parts[0])
+        want = [float(Fraction(x)) for x in parts[1:]]
+        assert np.allclose(oracle.ne_coefficients(Cw), want, rtol=0, atol=1e-15)
+    assert np.allclose(C5, (6 - np.arange(1, 6)) / 15.0)
+    assert abs(C5.sum() - 1) < 1e-15
+
+
+# ---- closed-form spectra -----------------------------------------------------
+
+@pytest.mark.parametrize("n", [7, 12, 13])
+def test_cycle_spectrum_row(n):
+    # T on C_n has eigenvalues cos(2 pi j / n), eigenvector 1 for j = 0; M is
+    # symmetric (regular graph) so singular values are |eigenvalues|.
+    g = synth.cycle(n)
+    op = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+    mu = np.cos(2 * np.pi * np.arange(n) / n)
+    ev = poly(C5, mu)
+    ev[0] = poly(C5, 1.0) - LAM * n
+    want = np.sort(np.abs(ev))[::-1]
+    M = op.explicit()
+    _, S, _ = oracle.jacobi_svd(M)
+    assert np.allclose(S, want, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [6, 9])
+def test_cycle_spectrum_with_adjacency_term(n):
+    # Eq. 3 exactly: M = p(T) - lam (J - A).  On C_n, A = 2T.
+    g = synth.cycle(n)
+    op = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM, adj_coeff=LAM)
+    mu = np.cos(2 * np.pi * np.arange(n) / n)
+    ev = poly(C5, mu) + LAM * 2 * mu
+    ev[0] -= LAM * n
+    want = np.sort(np.abs(ev))[::-1]
+    _, S, _ = oracle.jacobi_svd(op.explicit())
+    assert np.allclose(S, want, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [5, 8])
+def test_complete_graph_spectrum(n):
+    g = synth.complete(n)
+    op = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+    ev = np.array([poly(C5, 1.0) - LAM * n] + [poly(C5, -1.0 / (n - 1))] * (n - 1))
+    _, S, _ = oracle.jacobi_svd(op.explicit())
+    assert np.allclose(S, np.sort(np.abs(ev))[::-1], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [7, 10])
+def test_cycle_spectrum_sym(n):
+    # Â on C_n: (A+I)/3, eigenvalues (1 + 2 cos(2 pi j/n)) / 3
+    g = synth.cycle(n)
+    op = oracle.graph_operator(g, norm="sym", coeffs=C5, ones_coeff=-LAM)
+    mu = (1 + 2 * np.cos(2 * np.pi * np.arange(n) / n)) / 3
+    ev = poly(C5, mu)
+    ev[0] -= LAM * n
+    _, S, _ = oracle.jacobi_svd(op.explicit())
+    assert np.allclose(S, np.sort(np.abs(ev))[::-1], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_concat_identity_features(L):
+    # X = I: M M^T = sum_l Â^(2l), sigma_j = sqrt(sum_l mu_j^(2l))
+    n = 9
+    g = synth.cycle(n)
+    op = oracle.graph_operator(g, form="concat", norm="sym", X=np.eye(n), L=L)
+    mu = (1 + 2 * np.cos(2 * np.pi * np.arange(n) / n)) / 3
+    want = np.sqrt(sum(mu ** (2 * l) for l in range(L + 1)))
+    M = op.explicit()
+    assert M.shape == (n, n * (L + 1))
+    _, S, _ = oracle.svd_any(M)
+    assert np.allclose(S[:n], np.sort(want)[::-1], rtol=1e-12)
+
+
+# ---- exact invariants on irregular graphs ------------------------------------
+
+def _irregular(n=300, m=1400, seed=3):
+    return synth.chung_lu(n, m, seed)
+
+
+def test_row_operator_invariants():
+    g = _irregular()
+    d = g.degrees().astype(np.float64)
+    op = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+    one = np.ones(g.n)
+    # T 1 = 1  =>  M 1 = (sum c - lam n) 1
+    assert np.allclose(op.apply(one), (C5.sum() - LAM * g.n) * one, rtol=1e-13)
+    # T^T d = d  =>  M^T d = (sum c) d - lam (1^T d) 1,   1^T d = nnz
+    assert np.allclose(op.apply(d, transpose=True), C5.sum() * d - LAM * g.nnz * one, rtol=1e-12, atol=1e-9)
+    # the transpose is not the forward operator on an irregular graph
+    assert not np.allclose(op.apply(d), op.apply(d, transpose=True))
+
+
+def test_sym_operator_invariant():
+    g = _irregular()
+    v = np.sqrt(g.degrees() + 1.0)
+    op = oracle.graph_operator(g, norm="sym", coeffs=C5)
+    assert np.allclose(op.apply(v), v, rtol=1e-13)  # Â v = v, sum c = 1
+    assert np.allclose(op.apply(v, transpose=True), v, rtol=1e-13)
+
+
+def test_weighted_row_operator():
+    g = _irregular()
+    rng = np.random.default_rng(0)
+    w = rng.uniform(0.5, 2.0, g.nnz)
+    # symmetric weights: w_ij = w_ji
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    key = np.minimum(rows, g.colidx) * g.n + np.maximum(rows, g.colidx)
+    _, inv = np.unique(key, return_inverse=True)
+    w = rng.uniform(0.5, 2.0, inv.max() + 1)[inv]
+    op = oracle.graph_operator(g, values=w, coeffs=[1.0])
+    one = np.ones(g.n)
+    assert np.allclose(op.apply(one), one, rtol=1e-13)
+    dw = np.bincount(rows, weights=w, minlength=g.n)
+    assert np.allclose(op.apply(dw, transpose=True), dw, rtol=1e-12)
+
+
+@pytest.mark.parametrize("form,norm", [("poly", "row"), ("poly", "sym"), ("concat", "sym"), ("concat", "row")])
+def test_adjoint_identity(form, norm):
+    g = _irregular(120, 500, 9)
+    rng = np.random.default_rng(1)
+    kw = dict(form=form, norm=norm)
+    if form == "poly":
+        kw.update(coeffs=C5, ones_coeff=-LAM, adj_coeff=0.02)
+    else:
+        x = synth.tfidf_features(g.n, 17, 0.2, 4)
+        kw.update(X=(x.d, x.rowptr, x.colidx, x.values), L=2)
+    op = oracle.graph_operator(g, **kw)
+    r, c = op.shape
+    G = rng.standard_normal((c, 5))
+    H = rng.standard_normal((r, 5))
+    lhs = np.sum(op.apply(G) * H)
+    rhs = np.sum(G * op.apply(H, transpose=True))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1)
+
+
+def _all_graphs(n):
+    pairs = list(itertools.combinations(range(n), 2))
+    for mask in range(1 << len(pairs)):
+        e = [p for b, p in enumerate(pairs) if mask >> b & 1]
+        deg = np.zeros(n, int)
+        for a, b in e:
+            deg[a] += 1
+            deg[b] += 1
+        yield synth.from_edges(n, e, self_loops=np.nonzero(deg == 0)[0])
+
+
+def test_implicit_matches_explicit_all_graphs_n4():
+    rng = np.random.default_rng(2)
+    count = 0
+    for g in _all_graphs(4):
+        for norm in ("row", "sym"):
+            op = oracle.graph_operator(g, norm=norm, coeffs=C5, ones_coeff=-LAM, adj_coeff=0.3)
+            M = op.explicit()
+            G = rng.standard_normal((4, 3))
+            assert np.abs(op.apply(G) - M @ G).max() <= 1e-13
+            assert np.abs(op.apply(G, transpose=True) - M.T @ G).max() <= 1e-13
+            count += 1
+    assert count == 2 * 64
+
+
+def test_implicit_matches_explicit_concat():
+    g = _irregular(60, 240, 5)
+    x = synth.tfidf_features(g.n, 7, 0.3, 8)
+    op = oracle.graph_operator(g, form="concat", norm="sym", X=(x.d, x.rowptr, x.colidx, x.values), L=2)
+    M = op.explicit()
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((M.shape[1], 4))
+    H = rng.standard_normal((M.shape[0], 4))
+    assert np.abs(op.apply(G) - M @ G).max() <= 1e-13
+    assert np.abs(op.apply(H, transpose=True) - M.T @ H).max() <= 1e-13
+    # block 0 of M is X itself
+    Xd = np.zeros((g.n, x.d))
+    for i in range(g.n):
+        Xd[i, x.colidx[x.rowptr[i]:x.rowptr[i + 1]]] = x.values[x.rowptr[i]:x.rowptr[i + 1]]
+    assert np.allclose(M[:, :x.d], Xd, rtol=0, atol=1e-7)
+
+
+# ---- dense kernels: Jacobi SVD, Cholesky, CholeskyQR, Householder -----------
+
+@pytest.mark.parametrize("shape,cond", [((50, 20), 1e2), ((30, 30), 1e8), ((200, 12), 1e12)])
+def test_jacobi_matches_lapack(shape, cond):
+    rng = np.random.default_rng(4)
+    r, c = shape
+    Ua, _ = np.linalg.qr(rng.standard_normal((r, c)))
+    Va, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    s = np.geomspace(1.0, 1.0 / cond, c)
+    A = (Ua * s) @ Va.T
+    U, S, V = oracle.jacobi_svd(A)
+    S_ref = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(S, S_ref, rtol=1e-10, atol=1e-15 * S_ref[0])
+    assert np.abs(U.T @ U - np.eye(c)).max() < 1e-12
+    assert np.abs(V.T @ V - np.eye(c)).max() < 1e-12
+    assert np.abs((U * S) @ V.T - A).max() < 1e-13 * S_ref[0]
+    assert np.all(np.diff(S) <= 0)
+
+
+def test_eckart_young():
+    g = _irregular(80, 300, 12)
+    op = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+    M = op.explicit()
+    U, S, V = oracle.jacobi_svd(M)
+    for k in (1, 5, 20):
+        E = M - (U[:, :k] * S[:k]) @ V[:, :k].T
+        assert abs(np.sum(E * E) - np.sum(S[k:] ** 2)) <= 1e-10 * np.sum(S ** 2)
+
+
+def test_cholesky_matches_lapack():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((40, 25))
+    W = A.T @ A
+    Lf, info = oracle.cholesky(W)
+    assert info == 0
+    assert np.allclose(Lf, np.linalg.cholesky(W), rtol=1e-12, atol=1e-12)
+    W[3, 3] = -1.0
+    _, info = oracle.cholesky(W)
+    assert info == 4
+
+
+def _cond_matrix(r, c, cond, seed):
+    rng = np.random.default_rng(seed)
+    Ua, _ = np.linalg.qr(rng.standard_normal((r, c)))
+    Va, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    return (Ua * np.geomspace(1, 1 / cond, c)) @ Va.T
+
+
+def test_cholqr_alg2():
+    Q0 = _cond_matrix(500, 30, 1e3, 6)
+    Q, R, info = oracle.cholqr(Q0)
+    assert info == 0
+    assert np.abs(Q.T @ Q - np.eye(30)).max() < 1e-9  # one pass: O(u cond^2)
+    assert np.abs(Q @ R - Q0).max() < 1e-13
+    assert np.allclose(R, np.triu(R))
+    Qh, Rh = oracle.householder_qr(Q0)
+    assert oracle.max_principal_angle(Qh, Q) < 1e-10  # same span (Alg. 2 footnote)
+    Qn, Rn = np.linalg.qr(Q0)
+    sg = np.sign(np.diag(Rn)) * np.sign(np.diag(Rh))
+    assert np.allclose(Qh, Qn * sg, atol=1e-12)
+
+
+@pytest.mark.parametrize("cond,passes", [(1e3, 2), (1e7, 2), (1e11, 3)])
+def test_cholqr2_orthonormal(cond, passes):
+    Q0 = _cond_matrix(800, 24, cond, 7)
+    Q, R, p = oracle.cholqr2(Q0)
+    assert p == passes
+    assert np.abs(Q.T @ Q - np.eye(24)).max() < 1e-14 * 800
+    assert np.abs(Q @ R - Q0).max() < 1e-12 * np.abs(Q0).max()
+    Qh, _ = oracle.householder_qr(Q0)
+    assert oracle.max_principal_angle(Qh, Q) < 1e-12 * cond
+
+
+# ---- Alg. 1 ------------------------------------------------------------------
+
+def test_isvd_cycle_closed_form():
+    n = 64
+    g = synth.cycle(n)
+    op = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+    mu = np.cos(2 * np.pi * np.arange(n) / n)
+    ev = poly(C5, mu)
+    ev[0] = poly(C5, 1.0) - LAM * n
+    want = np.sort(np.abs(ev))[::-1]
+    # k = 5 sits at a gap (pairs of equal values follow the first)
+    U, S, V, _ = op.isvd(5, 10, 8, 99)
+    assert want[4] - want[5] > 1e-3
+    assert np.allclose(S, want[:5], rtol=1e-10)
+    assert np.abs(U.T @ U - np.eye(5)).max() < 1e-13
+    assert np.abs(V.T @ V - np.eye(5)).max() < 1e-13
+    # vectors converge at the square root of the values' rate: more iterations
+    U, S, V, _ = op.isvd(5, 10, 40, 99)
+    assert oracle.residuals(op, U, S, V).max() < 1e-9
+
+
+def test_isvd_error_falls_with_iterations():
+    # Thm. 4 (Halko et al. Thm 1.2): error decays with the number of
+    # iterations towards the optimal rank-k error.
+    g = _irregular(250, 1200, 21)
+    op = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+    M = op.explicit()
+    S_ref = np.linalg.svd(M, compute_uv=False)
+    k = 10
+    errs = []
+    for q in (0, 1, 2, 4, 8):
+        U, S, V, _ = op.isvd(k, 5, q, 4)
+        E = M - (U * S) @ V.T
+        errs.append(np.linalg.norm(E, 2))
+        assert np.all(S <= S_ref[:k] * (1 + 1e-12))  # Ritz values never exceed the truth
+    opt = S_ref[k]
+    assert errs[-1] <= 1.05 * opt
+    assert errs[0] <= 4 * opt * np.sqrt(250)
+    assert errs[-1] <= errs[0]
+
+
+def test_isvd_matches_lapack_when_gapped():
+    g = _irregular(200, 1000, 22)
+    op = oracle.graph_operator(g, norm="sym", coeffs=C5, ones_coeff=-LAM)
+    M = op.explicit()
+    Ur, Sr, Vrt = np.linalg.svd(M)
+    k = int(np.argmax(np.diff(-Sr[:12]))) + 1  # largest gap among the top 12
+    U, S, V, _ = op.isvd(k, 8, 10, 5)
+    assert np.allclose(S, Sr[:k], rtol=1e-8)
+    assert oracle.max_principal_angle(Ur[:, :k], U) < 1e-5
+    assert oracle.max_principal_angle(Vrt[:k].T, V) < 1e-5
+
+
+def test_isvd_concat_matches_lapack():
+    g = _irregular(150, 600, 23)
+    x = synth.tfidf_features(g.n, 20, 0.2, 24)
+    op = oracle.graph_operator(g, form="concat", norm="sym", X=(x.d, x.rowptr, x.colidx, x.values), L=2)
+    M = op.explicit()
+    Sr = np.linalg.svd(M, compute_uv=False)
+    U, S, V, _ = op.isvd(8, 8, 40, 6)  # sigma_8 / sigma_9 = 1.002: slow
+    assert U.shape == (150, 8) and V.shape == (60, 8)
+    assert np.allclose(S, Sr[:8], rtol=1e-10)
+
+
+def test_isvd_ritz_prefix_consistency():
+    # The start block for width l is the same whatever split k + p = l
+    # (counter-based draw), so the Ritz values agree.
+    g = _irregular(200, 900, 25)
+    op = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+    _, S1, _, _ = op.isvd(10, 6, 3, 8)
+    _, S2, _, _ = op.isvd(16, 0, 3, 8)
+    assert np.allclose(S1, S2[:10], rtol=1e-12)
+
+
+# ---- sensitivity: plausible mistakes fail a pin -------------------------------
+
+def test_pins_reject_planted_mistakes():
+    n = 12
+    g = synth.cycle(n)
+    mu = np.cos(2 * np.pi * np.arange(n) / n)
+    ev = poly(C5, mu)
+    ev[0] = poly(C5, 1.0) - LAM * n
+    want = np.sort(np.abs(ev))[::-1]
+    # dropped all-ones term
+    _, S, _ = oracle.jacobi_svd(oracle.graph_operator(g, coeffs=C5).explicit())
+    assert not np.allclose(S, want, rtol=1e-6)
+    # wrong sign of the all-ones term
+    _, S, _ = oracle.jacobi_svd(oracle.graph_operator(g, coeffs=C5, ones_coeff=+LAM).explicit())
+    assert not np.allclose(S, want, rtol=1e-6)
+    # reversed coefficients (index slip c_k <-> c_{K+1-k})
+    _, S, _ = oracle.jacobi_svd(oracle.graph_operator(g, coeffs=C5[::-1], ones_coeff=-LAM).explicit())
+    assert not np.allclose(S, want, rtol=1e-6)
+    # symmetric normalisation in place of T fails the row-stochastic invariant
+    gi = _irregular()
+    one = np.ones(gi.n)
+    wrong = oracle.graph_operator(gi, norm="sym", coeffs=C5).apply(one)
+    assert not np.allclose(wrong, one)
