@@ -1,0 +1,221 @@
+/*
+ * isvd.h -- C ABI of libisvd.so: randomized truncated SVD of an implicit
+ * design matrix on one GB300 (sm_103a).
+ *
+ * Method: "Implicit SVD for Graph Representation Learning" (arXiv 2111.06312).
+ *   - The matrix M is never formed.  Only M.G and M^T.G are evaluated from
+ *     M's defining expression (Sec. 4 and App. A.3: shape, dot, T).
+ *   - Two expression forms are supported:
+ *       POLY:   M = sum_{k=1..K} c_k N^k + alpha 1 1^T + beta A + sum_t a_t u_t v_t^T
+ *               (Eq. 3 is c_q from the context window, alpha = -lambda,
+ *               beta = +lambda; Sec. 3.1 also allows N = Â)
+ *       CONCAT: M = [X | N X | ... | N^L X]                       (Eq. 6)
+ *     with N = T = D^-1 A (ISVD_NORM_ROW) or
+ *          N = Â = (D+I)^-1/2 (A+I) (D+I)^-1/2 (ISVD_NORM_SYM_SELFLOOP)  (Sec. 2).
+ *   - isvd_svd runs Alg. 1 (randomized range finder with power iterations,
+ *     App. A.2) with orthonorm = CholeskyQR (Alg. 2, right), applied twice
+ *     with an adaptive shift on breakdown, and Rayleigh-Ritz.
+ *
+ * Conventions (every entry point):
+ *   - Pointers are DEVICE pointers unless marked HOST.
+ *   - Dense blocks are row-major [rows][ld] with ld >= cols, ld % 8 == 0 and
+ *     the base 16-byte aligned.  Columns at or beyond the logical width are
+ *     never written by isvd_apply / isvd_apply_T.
+ *   - The caller owns every buffer passed in.  An operator BORROWS the CSR
+ *     and feature arrays of its descriptor for its whole lifetime.
+ *   - Work is asynchronous on the given cudaStream_t (passed as void*; NULL is
+ *     the legacy default stream).  isvd_create_operator synchronises once to
+ *     validate its input.  Calls on one operator must be ordered (one stream,
+ *     or explicit events): the operator owns a reusable workspace.
+ *   - Errors are returned as isvd_status; no exception or abort crosses the
+ *     ABI.  isvd_last_error() returns a thread-local detail string.  Errors
+ *     that only the GPU can see (CholeskyQR breakdown) are written to a
+ *     device-resident isvd_info that the caller reads after synchronising.
+ */
+#ifndef ISVD_H_
+#define ISVD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ISVD_API __attribute__((visibility("default")))
+#else
+#define ISVD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ISVD_OK = 0,
+  ISVD_ERR_INVALID_ARGUMENT = 1,   /* null pointer, bad ld/alignment, k < 1, ... */
+  ISVD_ERR_INVALID_GRAPH = 2,      /* CSR not well formed, zero degree for T, asymmetric A */
+  ISVD_ERR_SHAPE = 3,              /* block width or rank does not fit the operator */
+  ISVD_ERR_NOT_POSITIVE_DEFINITE = 4, /* CholeskyQR broke down even with a shift */
+  ISVD_ERR_TIMEOUT = 5,            /* a bounded device wait expired */
+  ISVD_ERR_WORKSPACE = 6,          /* the allocator returned NULL */
+  ISVD_ERR_CUDA = 7,               /* a CUDA runtime call failed (detail in last_error) */
+  ISVD_ERR_UNSUPPORTED = 8         /* valid request outside what this build implements */
+} isvd_status;
+
+typedef enum { ISVD_F32 = 0, ISVD_BF16 = 1 } isvd_dtype;
+
+/* FP32: all blocks stored in FP32, FP32-accurate Gram and products.
+ * MIXED: power iterations store blocks in BF16 (FP32 accumulation), then one
+ * FP32 refinement power step and an FP32 Rayleigh-Ritz.                     */
+typedef enum { ISVD_PREC_FP32 = 0, ISVD_PREC_MIXED = 1 } isvd_precision;
+
+typedef enum {
+  ISVD_NORM_ROW = 0,          /* N = T = D^-1 A                   (Sec. 2) */
+  ISVD_NORM_SYM_SELFLOOP = 1  /* N = Â = (D+I)^-1/2 (A+I) (D+I)^-1/2  (Sec. 2) */
+} isvd_norm;
+
+typedef enum {
+  ISVD_FORM_POLY = 0,    /* sum_k c_k N^k + corrections         (Eq. 3) */
+  ISVD_FORM_CONCAT = 1   /* [X | N X | ... | N^L X]             (Eq. 6) */
+} isvd_form;
+
+/* Sparse matrix in CSR: rowptr[rows+1] (rowptr[0] == 0, nondecreasing,
+ * rowptr[rows] == nnz), colidx[nnz] in [0, cols), values[nnz] or NULL for a
+ * pattern whose entries are all 1.  int32 indices: nnz < 2^31.             */
+typedef struct {
+  int64_t rows, cols, nnz;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  const float *values;
+} isvd_csr;
+
+/* Workspace allocator.  alloc(bytes, stream, ctx) returns device memory that
+ * is usable in stream order on `stream`, or NULL; free(ptr, stream, ctx)
+ * releases it.  Pass NULL for the allocator to use cudaMallocAsync /
+ * cudaFreeAsync.                                                            */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, void *stream, void *ctx);
+  void *ctx;
+} isvd_allocator;
+
+enum {
+  ISVD_FLAG_SKIP_SYMMETRY_CHECK = 1  /* trust that A is symmetric (pattern and values) */
+};
+
+#define ISVD_MAX_DEGREE 16
+#define ISVD_MAX_LOWRANK 8
+#define ISVD_MAX_BLOCK 160   /* largest block width l = k + p of isvd_svd */
+
+typedef struct {
+  isvd_form form;
+  isvd_norm norm;
+  isvd_csr A;              /* n x n adjacency, both directions stored; symmetric */
+  /* POLY */
+  int32_t degree;          /* K in 1..ISVD_MAX_DEGREE */
+  const double *coeffs;    /* HOST, c_1..c_K (copied at creation) */
+  double ones_coeff;       /* alpha of alpha 1 1^T (Eq. 3: -lambda); 0 = none */
+  double adj_coeff;        /* beta of beta A (Eq. 3 as printed: +lambda); 0 = none */
+  int32_t lr_rank;         /* extra sum_t a_t u_t v_t^T terms, 0..ISVD_MAX_LOWRANK */
+  const float *lr_u;       /* n x lr_rank row-major (ld = lr_rank) */
+  const float *lr_v;       /* n x lr_rank row-major (ld = lr_rank) */
+  const double *lr_alpha;  /* HOST, lr_rank values (copied) */
+  /* CONCAT */
+  int64_t d;               /* feature width */
+  int32_t L;               /* propagation depth, >= 0 */
+  isvd_csr X;              /* sparse X (n x d), or all-null when X_dense is given */
+  const float *X_dense;    /* dense X, row-major n x d (ld = d) */
+  int32_t flags;           /* ISVD_FLAG_* */
+} isvd_operator_desc;
+
+/* Device-resident status of isvd_svd / isvd_orthonormalize, written by the
+ * GPU.  status: an isvd_status.  chol_shifts: CholeskyQR passes that needed
+ * a diagonal shift.  cholqr_passes: passes run.  iters_done: power
+ * iterations completed.                                                      */
+typedef struct {
+  int32_t status;
+  int32_t chol_shifts;
+  int32_t cholqr_passes;
+  int32_t iters_done;
+} isvd_info;
+
+typedef struct isvd_operator isvd_operator;
+
+/* Build an operator from a descriptor (the leaf and symbolic nodes of
+ * Sec. 4 / App. A.3 folded into one description).  Validates the CSR (and,
+ * unless ISVD_FLAG_SKIP_SYMMETRY_CHECK, the symmetry of A) on the GPU,
+ * computes degrees and scale vectors, builds X^T for CONCAT and the row
+ * work lists of the sparse products.  Synchronises `stream` once.
+ * Errors: INVALID_ARGUMENT, INVALID_GRAPH, UNSUPPORTED, WORKSPACE, CUDA.
+ * On success *out owns device workspace; free with isvd_destroy_operator. */
+ISVD_API isvd_status isvd_create_operator(const isvd_operator_desc *desc, const isvd_allocator *alloc,
+                                 void *stream, isvd_operator **out);
+
+/* Free an operator and its workspace (after its last stream work).  NULL ok. */
+ISVD_API void isvd_destroy_operator(isvd_operator *op);
+
+/* (rows, cols) of M: (n, n) for POLY, (n, d (L+1)) for CONCAT (App. A.3: shape). */
+ISVD_API isvd_status isvd_operator_shape(const isvd_operator *op, int64_t *rows, int64_t *cols);
+
+/* out (rows x b) = M G, G (cols x b): App. A.3 `dot`.  dtype gives the
+ * storage type of G and out (FP32 accumulation either way).  G and out must
+ * not overlap.  b in 1..1024. */
+ISVD_API isvd_status isvd_apply(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out,
+                       int64_t ldo, isvd_dtype dtype, void *stream);
+
+/* out (cols x b) = M^T G, G (rows x b): App. A.3 `T().dot`. */
+ISVD_API isvd_status isvd_apply_T(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out,
+                         int64_t ldo, isvd_dtype dtype, void *stream);
+
+/* Rank-k SVD of M by Alg. 1 with block width l = k + oversample (the paper
+ * uses l = 2k), `iters` power iterations (Alg. 1's `iterations`), start block
+ * N(0,1) from Philox4x32-10 keyed by `seed`.  Outputs: U (rows x k, ldu),
+ * S (k, descending), V (cols x k, ldv), all FP32.  dev_info may be NULL.
+ * Requires 1 <= k, l <= min(rows, cols), l <= ISVD_MAX_BLOCK.  The sequence
+ * is captured once per argument set into a CUDA graph and replayed. */
+ISVD_API isvd_status isvd_svd(isvd_operator *op, int32_t k, int32_t oversample, int32_t iters, uint64_t seed,
+                     isvd_precision precision, float *U, int64_t ldu, float *S, float *V, int64_t ldv,
+                     isvd_info *dev_info, void *stream);
+
+/* --- individual steps, exported for verification and reuse --------------- */
+
+/* out[i][j] (rows x cols) = standard normal from Philox4x32-10 (Salmon et al.
+ * 2011): counter (j/4, i mod 2^32, i / 2^32, 0), key (seed mod 2^32,
+ * seed / 2^32), words (0,1) and (2,3) turned into normals j%4 = 0,1 and 2,3
+ * by Box-Muller with u = (word + 1/2) 2^-32.  Alg. 1's start block.
+ * dtype selects FP32 or BF16 storage.  Columns cols..ld-1 are set to zero. */
+ISVD_API isvd_status isvd_gaussian(uint64_t seed, int64_t rows, int32_t cols, void *out, int64_t ld,
+                          isvd_dtype dtype, void *stream);
+
+/* Raw Philox4x32-10 words for counters (c0 = j, c1 = i mod 2^32,
+ * c2 = i / 2^32, 0) with i in [0, rows), j in [0, 4): out[i][4 j + w]
+ * (uint32, rows x 16).  For known-answer and bit-parity checks. */
+ISVD_API isvd_status isvd_philox_words(uint64_t seed, int64_t rows, uint32_t *out, void *stream);
+
+/* In-place orthonormalisation of Q (rows x l, FP32, ldq): CholeskyQR2
+ * (Alg. 2, right, applied twice); when a Gram matrix is not numerically
+ * positive definite a diagonal shift is added and two further plain passes
+ * follow (up to 4 passes).  R_out (DEVICE, l x l FP64, row-major, upper)
+ * receives R with Q_in = Q_out R, or NULL.  dev_info as in
+ * isvd_svd.  Uses the operator's workspace (any operator; pass the one whose
+ * calls this is ordered with).  l <= ISVD_MAX_BLOCK. */
+ISVD_API isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t rows, int32_t l, int64_t ldq,
+                                double *R_out, isvd_info *dev_info, void *stream);
+
+/* SVD of a small square upper-triangular-or-dense FP64 matrix by one-sided
+ * Jacobi on its transpose (the Rayleigh-Ritz step of Alg. 1, done as
+ * SVD(R^T) after a QR of B^T).  A (l x l, row-major, DEVICE) = Uo diag(S) Vo^T
+ * with Uo, Vo (l x l, FP64, row-major) and S (l, FP64, descending). */
+ISVD_API isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double *Uo, double *S,
+                           double *Vo, isvd_info *dev_info, void *stream);
+
+/* Number of kernel launches in the CUDA graph that the last isvd_svd call on
+ * this operator replayed (-1 if none yet).  Introspection for benchmarks. */
+ISVD_API int64_t isvd_graph_kernel_nodes(const isvd_operator *op);
+
+ISVD_API const char *isvd_status_string(isvd_status s);
+ISVD_API const char *isvd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISVD_H_ */

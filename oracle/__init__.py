@@ -46,6 +46,7 @@ class _Op(C.Structure):
         ("d", C.c_int64), ("L", C.c_int32),
         ("xrowptr", C.c_void_p), ("xcolidx", C.c_void_p), ("xval", C.c_void_p),
         ("xdense", C.c_void_p),
+        ("lr_rank", C.c_int32), ("lr_u", C.c_void_p), ("lr_v", C.c_void_p), ("lr_alpha", C.c_void_p),
     ]
 
 
@@ -83,12 +84,13 @@ def _f64(a):
 
 class Operator:
     """Implicit design matrix.  ``form='poly'``: sum_k c_k N^k + alpha 11^T +
-    beta A (Eq. 3 with alpha = -lambda, beta = +lambda).  ``form='concat'``:
+    beta A + sum_t a_t u_t v_t^T (Eq. 3 with alpha = -lambda, beta = +lambda;
+    ``lowrank=(u, v, a)``).  ``form='concat'``:
     [X | NX | ... | N^L X] (Eq. 6).  ``norm='row'``: N = T = D^-1 A;
     ``norm='sym'``: N = Â = (D+I)^-1/2 (A+I) (D+I)^-1/2 (Sec. 2)."""
 
     def __init__(self, n, rowptr, colidx, *, form="poly", norm="row", values=None,
-                 coeffs=(), ones_coeff=0.0, adj_coeff=0.0,
+                 coeffs=(), ones_coeff=0.0, adj_coeff=0.0, lowrank=None,
                  X=None, L=0):
         self._keep = []
 
@@ -109,6 +111,13 @@ class Operator:
         s.ones_coeff = float(ones_coeff)
         s.adj_coeff = float(adj_coeff)
         s.L = int(L)
+        if lowrank is not None:  # (u, v, alpha): n x r, n x r, r
+            u, v, alpha = lowrank
+            al = keep(_f64(np.asarray(alpha).reshape(-1)))
+            s.lr_rank = len(al)
+            s.lr_u = _p(keep(_f64(np.asarray(u).reshape(n, -1))))
+            s.lr_v = _p(keep(_f64(np.asarray(v).reshape(n, -1))))
+            s.lr_alpha = _p(al)
         if X is not None:
             if isinstance(X, np.ndarray):
                 s.d = X.shape[1]

@@ -14,7 +14,9 @@
  * What is computed, and where it is defined:
  *   - T = D^-1 A and  Â = (D+I)^-1/2 (A+I) (D+I)^-1/2            (Sec. 2)
  *   - M_NE = sum_q c_q T^q - lambda (1 1^T - A)                    (Sec. 3.1, Eq. 3)
- *     with the all-ones and adjacency coefficients given separately
+ *     with the all-ones and adjacency coefficients given separately, plus
+ *     optional low-rank terms sum_t a_t u_t v_t^T (the outer-product leaves
+ *     of Sec. 4)
  *   - M_NC = [X | ÂX | ... | Â^L X]                               (Sec. 3.2, Eq. 6)
  *   - products M G and M^T G from those expressions                (Sec. 4; App. A.3)
  *   - orthonormOurs: L = chol(Q^T Q), Q <- Q (L^-1)^T              (Alg. 2, right)
@@ -56,6 +58,9 @@ typedef struct {
   int32_t L;           /* number of propagation blocks (concatenation)          */
   const int32_t *xrowptr, *xcolidx; const double *xval; /* sparse X, or     */
   const double *xdense; /* dense X, row-major n x d                            */
+  int32_t lr_rank;     /* extra terms sum_t a_t u_t v_t^T (polynomial form)     */
+  const double *lr_u, *lr_v; /* n x lr_rank, row-major                         */
+  const double *lr_alpha;
 } orc_op;
 
 static double a_val(const orc_op *op, int64_t e) { return op->aval ? op->aval[e] : 1.0; }
@@ -209,6 +214,16 @@ int orc_apply(const orc_op *op, const double *G, int64_t b, double *out, int tra
       }
     }
     if (op->adj_coeff != 0.0) adj_apply_acc(op, G, out, b, op->adj_coeff, transpose);
+    /* sum_t a_t u_t (v_t^T G); the transpose swaps u and v */
+    for (int t = 0; t < op->lr_rank; ++t) {
+      const double *u = transpose ? op->lr_v : op->lr_u;
+      const double *v = transpose ? op->lr_u : op->lr_v;
+      for (int64_t c = 0; c < b; ++c) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += v[i * op->lr_rank + t] * G[i * b + c];
+        for (int64_t i = 0; i < n; ++i) out[i * b + c] += op->lr_alpha[t] * u[i * op->lr_rank + t] * s;
+      }
+    }
     free(P);
     free(Pn);
   } else {
@@ -281,6 +296,10 @@ int orc_explicit(const orc_op *op, double *M) {
     for (int64_t i = 0; i < n; ++i)
       for (int64_t e = op->rowptr[i]; e < op->rowptr[i + 1]; ++e)
         M[i * n + op->colidx[e]] += op->adj_coeff * a_val(op, e);
+    for (int t = 0; t < op->lr_rank; ++t)
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j)
+          M[i * n + j] += op->lr_alpha[t] * op->lr_u[i * op->lr_rank + t] * op->lr_v[j * op->lr_rank + t];
     free(P);
     free(Pn);
   } else {

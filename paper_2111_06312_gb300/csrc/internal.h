@@ -1,0 +1,206 @@
+// Internal declarations shared by the libisvd translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "isvd.h"
+
+namespace isvd {
+
+// ---- errors -----------------------------------------------------------------
+void set_error(const char *fmt, ...);
+isvd_status fail(isvd_status s, const char *fmt, ...);
+
+#define ISVD_CUDA_TRY(expr)                                                                      \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return ::isvd::fail(ISVD_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                          __FILE__, __LINE__);                                                   \
+  } while (0)
+
+#define ISVD_TRY(expr)                   \
+  do {                                   \
+    isvd_status s_ = (expr);             \
+    if (s_ != ISVD_OK) return s_;        \
+  } while (0)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+constexpr int kNumSMs = 152;
+
+// ---- dtype helpers ------------------------------------------------------------
+enum DType : int { DT_F32 = 0, DT_BF16 = 1 };
+inline size_t dtype_size(int dt) { return dt == DT_F32 ? 4 : 2; }
+
+// ---- sparse products ---------------------------------------------------------
+// One column slab of an SpMM: columns [col0, col0 + width) of the logical
+// block, read from `in` and written to `out` (both already offset to the
+// slab's first column and to the slab's row segment).  `group` lanes cooperate
+// on one row (power of two, 1..32); each lane owns 16 bytes of columns.
+struct SpmmSlab {
+  const void *in;
+  int64_t ldi;
+  void *out;
+  int64_t ldo;
+  const void *axpy;  // optional, same layout as out (offset to the slab)
+  int64_t lda;
+  int32_t col0;      // first column of the slab in the low-rank coefficient block
+  int32_t width;     // valid columns in this slab
+  int32_t group;     // lanes per row
+  int32_t pad_;
+};
+
+constexpr int kMaxSlabs = 24;
+
+struct SpmmArgs {
+  int64_t rows;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  const float *values;      // nullable: all ones
+  const float *colw;        // nullable: gathered weight of the source row j
+  int32_t self_term;        // add colw_i * in_i (or in_i)
+  const float *rowscale;    // nullable
+  float scalar;             // multiplies the gathered sum
+  float ax_scalar;          // axpy term: ax_scalar * ax_rowscale_i * axpy_i
+  const float *ax_rowscale; // nullable
+  int32_t lr_rank;          // low-rank epilogue: sum_t lr_alpha_t * u_it * c_t
+  int32_t lr_ones_first;    // term 0 has u = 1; terms t >= 1 read lr_u column t-1
+  const float *lr_u;        // nullable = ones; rows x (lr_rank - lr_ones_first) (ld lr_ldu)
+  int64_t lr_ldu;
+  const float *lr_c;        // lr_rank x lr_ldc (FP32)
+  int64_t lr_ldc;
+  float lr_alpha[ISVD_MAX_LOWRANK];
+  int32_t heavy_threshold;  // rows with more nonzeros go through the split path
+  int32_t nslabs;
+  SpmmSlab slab[kMaxSlabs];
+};
+
+// Heavy rows: nonzeros split into chunks processed independently, partial
+// sums combined in chunk order (deterministic).
+struct HeavyPlan {
+  int32_t n_rows = 0;       // heavy rows
+  int32_t n_chunks = 0;
+  int2 *chunks = nullptr;   // (row, first nnz) per chunk; chunk end = next chunk or row end
+  int32_t *chunk_end = nullptr;
+  int4 *rows = nullptr;     // (row, first chunk, chunk count, 0)
+  int32_t threshold = 1 << 30;
+  int32_t chunk = 256;
+};
+
+// Launch the SpMM described by `a` (dtype of in/axpy/out), splitting heavy
+// rows per `hp` using `partial` (hp.n_chunks x pw FP32, pw >= slab columns).
+cudaError_t spmm_launch(const SpmmArgs &a, int dtype, const HeavyPlan &hp, float *partial,
+                        int64_t pw, cudaStream_t s);
+
+// Column slabs for a block of width b (row-major, 16-byte aligned).
+int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out);
+
+// ---- dense helpers -----------------------------------------------------------
+cudaError_t gaussian_launch(uint64_t seed, int64_t rows, int32_t cols, void *out, int64_t ld, int dtype,
+                            cudaStream_t s);
+cudaError_t philox_words_launch(uint64_t seed, int64_t rows, uint32_t *out, cudaStream_t s);
+
+// c (r x b, FP32, ld ldc) = V^T G.  Column t of V is all ones when t == 0 and
+// ones_first, or when V is null; otherwise column t - ones_first of V (rows x ldv).
+cudaError_t lowrank_project_launch(const void *G, int64_t ldg, int dtype, int64_t rows, int32_t b,
+                                   const float *V, int64_t ldv, int32_t r, int32_t ones_first,
+                                   double *partial, int32_t n_part, float *c, int64_t ldc, cudaStream_t s);
+int32_t lowrank_partials(int64_t rows);
+
+// Gram W (FP64, l x l) = Q^T Q over rows; partial workspace n_part x l x l FP32.
+// gate: when non-null and *gate_flag says so, the kernels return at once
+// (conditional CholeskyQR passes).
+struct PassGate {
+  const int32_t *state = nullptr;  // orthonormalisation state (see small.cu)
+  int32_t pass = 0;                // 1-based pass number; passes > 2 are conditional
+};
+int32_t gram_partials(int64_t rows);
+cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, float *partial,
+                        int32_t n_part, double *W, PassGate g, cudaStream_t s);
+
+// out (rows x w) = Q (rows x l) B (l x w, FP32, ld ldb); upper: B upper
+// triangular.  out may equal Q (in place) when w == l and out dtype == in dtype.
+cudaError_t gemm_small_launch(const void *Q, int64_t ldq, int in_dtype, int64_t rows, int32_t l,
+                              const float *B, int64_t ldb, int32_t w, bool upper, void *out,
+                              int64_t ldo, int out_dtype, PassGate g, cudaStream_t s);
+
+// ---- small FP64 kernels -------------------------------------------------------
+// Orthonormalisation state block (device, int32[8]):
+//  [0] last pass that needed a shift (0 = none)   [1] breakdown flag
+constexpr int kOrthStateInts = 8;
+cudaError_t orth_reset_launch(int32_t *state, cudaStream_t s);
+// Cholesky of W (+ adaptive shift) -> Rinv (FP32, l x ldr), R (FP64 l x l, optional),
+// accumulates Racc <- R Racc when Racc non-null.
+cudaError_t chol_inv_launch(const double *W, int32_t l, int64_t rows, int dtype, float *Rinv, int64_t ldr,
+                            double *R, double *Racc, double *tmp, int32_t *state, isvd_info *info, int32_t pass,
+                            cudaStream_t s);
+cudaError_t racc_init_launch(double *Racc, int32_t l, cudaStream_t s);
+// SVD A = Uo diag(S) Vo^T of an l x l FP64 matrix by one-sided Jacobi on the
+// columns of A^T.  Optional FP32 copies of the first k columns (Uk, Vk: l x k)
+// and of S (k).  work: l2 x l2 FP64 (l2 = l rounded up to even).
+cudaError_t small_svd_launch(const double *A, int32_t l, double *Uo, double *S, double *Vo, double *work,
+                             float *Uk, float *Vk, float *Sk, int32_t k, isvd_info *info, int32_t iters,
+                             cudaStream_t s);
+cudaError_t small_kernels_init();
+cudaError_t dense_kernels_init();
+
+}  // namespace isvd
+
+// ---- the operator ------------------------------------------------------------
+struct isvd_operator {
+  isvd_operator_desc desc{};
+  isvd_allocator alloc{};
+  bool has_alloc = false;
+  int64_t n = 0, rows = 0, cols = 0;
+  std::vector<double> coeffs;
+  std::vector<double> lr_alpha;
+  // device arrays owned by the operator
+  float *deg = nullptr, *inv_d = nullptr, *s = nullptr, *s2 = nullptr;
+  // X^T (CONCAT) and dense-X-as-CSR
+  int32_t *xt_rowptr = nullptr, *xt_colidx = nullptr;
+  float *xt_values = nullptr;
+  int32_t *xd_rowptr = nullptr, *xd_colidx = nullptr;  // dense X viewed as CSR
+  const int32_t *x_rowptr = nullptr, *x_colidx = nullptr;
+  const float *x_values = nullptr;
+  int64_t x_nnz = 0;
+  isvd::HeavyPlan heavy_A, heavy_X, heavy_XT;
+  std::vector<void *> owned;  // allocations released at destroy
+  // workspace arena (grow only)
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  cudaStream_t capture_stream = nullptr;
+  int32_t slab_cols_f32 = 32, slab_cols_bf16 = 64;
+  struct GraphEntry {
+    uint64_t key[16];
+    cudaGraphExec_t exec;
+    int64_t kernel_nodes;
+  };
+  std::vector<GraphEntry> graphs;
+  int64_t last_kernel_nodes = -1;
+};
+
+namespace isvd {
+void *op_alloc(isvd_operator *op, size_t bytes, cudaStream_t s);
+void op_free(isvd_operator *op, void *p, cudaStream_t s);
+isvd_status ensure_arena(isvd_operator *op, size_t bytes, cudaStream_t s);
+
+// Scratch layout for one apply (offsets into a region of the arena).
+struct ApplyScratch {
+  void *z1 = nullptr, *z2 = nullptr, *p = nullptr;  // Horner temps, CONCAT P block
+  float *lr_c = nullptr;
+  double *lr_partial = nullptr;
+  float *heavy_partial = nullptr;
+};
+size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool transpose);
+void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool transpose, char *base,
+                         ApplyScratch *sc);
+isvd_status apply_impl(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
+                       int dtype, bool transpose, const ApplyScratch &sc, cudaStream_t s);
+}  // namespace isvd

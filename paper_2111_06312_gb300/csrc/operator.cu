@@ -1,0 +1,824 @@
+// The implicit operator: construction (validation, degrees, scale vectors,
+// X^T, row work lists) and the products M.G / M^T.G (Sec. 4, App. A.3).
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace isvd {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+isvd_status fail(isvd_status s, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+const char *last_error() { return g_last_error.c_str(); }
+
+void *op_alloc(isvd_operator *op, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  bytes = (size_t)round_up((int64_t)bytes, 256);
+  if (op->has_alloc) return op->alloc.alloc(bytes, (void *)s, op->alloc.ctx);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void op_free(isvd_operator *op, void *p, cudaStream_t s) {
+  if (!p) return;
+  if (op->has_alloc) op->alloc.free(p, (void *)s, op->alloc.ctx);
+  else cudaFreeAsync(p, s);
+}
+
+isvd_status ensure_arena(isvd_operator *op, size_t bytes, cudaStream_t s) {
+  if (bytes <= op->arena_bytes) return ISVD_OK;
+  // captured graphs point into the old arena
+  for (auto &g : op->graphs) cudaGraphExecDestroy(g.exec);
+  op->graphs.clear();
+  op_free(op, op->arena, s);
+  op->arena = nullptr;
+  op->arena_bytes = 0;
+  const size_t want = (size_t)round_up((int64_t)bytes, 1 << 20);
+  op->arena = op_alloc(op, want, s);
+  if (!op->arena) return fail(ISVD_ERR_WORKSPACE, "workspace allocation of %zu bytes failed", want);
+  op->arena_bytes = want;
+  return ISVD_OK;
+}
+
+namespace {
+
+// ---- construction kernels ----------------------------------------------------
+// flags: [0] rowptr malformed  [1] column index out of range  [2] non-finite value
+//        [3] zero or negative degree where T = D^-1 A needs 1/d
+__global__ void validate_csr_kernel(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rowptr,
+                                    const int32_t *colidx, const float *values, int32_t *flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= rows; i += stride) {
+    const int32_t a = rowptr[i];
+    if (i == 0 && a != 0) flags[0] = 1;
+    if (i == rows && (int64_t)a != nnz) flags[0] = 1;
+    if (i < rows && rowptr[i + 1] < a) flags[0] = 1;
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const int32_t c = colidx[e];
+    if (c < 0 || (int64_t)c >= cols) flags[1] = 1;
+    if (values && !isfinite(values[e])) flags[2] = 1;
+  }
+}
+
+// d_i = sum_j A_ij (Sec. 2); 1/d_i for T = D^-1 A; s_i = (d_i + 1)^-1/2 and
+// s_i^2 for Â = (D+I)^-1/2 (A+I) (D+I)^-1/2.
+__global__ void degree_kernel(int64_t n, const int32_t *rowptr, const float *values, int need_positive, float *deg,
+                              float *inv_d, float *s, float *s2, int32_t *flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int32_t e0 = rowptr[i], e1 = rowptr[i + 1];
+    double d = 0.0;
+    if (values) {
+      for (int32_t e = e0; e < e1; ++e) d += (double)values[e];
+    } else {
+      d = (double)(e1 - e0);
+    }
+    deg[i] = (float)d;
+    if (need_positive && !(d > 0.0)) flags[3] = 1;
+    inv_d[i] = d > 0.0 ? (float)(1.0 / d) : 0.f;
+    if (d + 1.0 <= 0.0) flags[3] = 1;
+    const double si = d + 1.0 > 0.0 ? 1.0 / sqrt(d + 1.0) : 0.0;
+    s[i] = (float)si;
+    s2[i] = (float)(si * si);
+  }
+}
+
+__global__ void edge_keys_kernel(int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                                 uint64_t *key_rc, uint64_t *key_cr) {
+  // one thread per row (rows are short on average); keys (row, col) and (col, row)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const uint64_t c = (uint64_t)colidx[e];
+      key_rc[e] = (uint64_t)i * (uint64_t)n + c;
+      key_cr[e] = c * (uint64_t)n + (uint64_t)i;
+    }
+  }
+}
+
+__global__ void compare_kernel(int64_t nnz, const uint64_t *ka, const uint64_t *kb, const float *va,
+                               const float *vb, int32_t *flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    if (ka[e] != kb[e]) flags[4] = 1;
+    if (va && va[e] != vb[e]) flags[4] = 1;
+  }
+}
+
+__global__ void iota_kernel(int64_t n, int32_t *out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (int32_t)i;
+}
+
+__global__ void row_of_entry_kernel(int64_t rows, const int32_t *rowptr, int32_t *row_of) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride)
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) row_of[e] = (int32_t)i;
+}
+
+__global__ void gather_transpose_kernel(int64_t nnz, const int32_t *perm, const int32_t *row_of,
+                                        const float *values, int32_t *t_colidx, float *t_values) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const int32_t e = perm[p];
+    t_colidx[p] = row_of[e];
+    t_values[p] = values ? values[e] : 1.f;
+  }
+}
+
+__global__ void count_kernel(int64_t nnz, const int32_t *keys, int32_t *counts) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
+    atomicAdd(&counts[keys[e]], 1);
+}
+
+__global__ void dense_csr_kernel(int64_t n, int64_t d, int32_t *rowptr, int32_t *colidx) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) rowptr[i] = (int32_t)(i * d);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * d; e += stride)
+    colidx[e] = (int32_t)(e % d);
+}
+
+unsigned grid_for(int64_t work) {
+  int64_t b = ceil_div(work, 256);
+  if (b > kNumSMs * 8) b = kNumSMs * 8;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+int bits_for(uint64_t maxval) {
+  int b = 1;
+  while (b < 64 && (maxval >> b) != 0) ++b;
+  return b;
+}
+
+struct Scratch {
+  isvd_operator *op;
+  cudaStream_t s;
+  std::vector<void *> ptrs;
+  void *get(size_t bytes) {
+    void *p = op_alloc(op, bytes, s);
+    if (p) ptrs.push_back(p);
+    return p;
+  }
+  ~Scratch() {
+    for (void *p : ptrs) op_free(op, p, s);
+  }
+};
+
+void *owned_alloc(isvd_operator *op, size_t bytes, cudaStream_t s) {
+  void *p = op_alloc(op, bytes, s);
+  if (p) op->owned.push_back(p);
+  return p;
+}
+
+// Build the hub-row split plan from a host copy of rowptr.
+isvd_status build_heavy(isvd_operator *op, const int32_t *rowptr_dev, int64_t rows, HeavyPlan *hp,
+                        cudaStream_t s) {
+  std::vector<int32_t> rp((size_t)rows + 1);
+  ISVD_CUDA_TRY(cudaMemcpyAsync(rp.data(), rowptr_dev, sizeof(int32_t) * (rows + 1), cudaMemcpyDeviceToHost, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int2> chunks;
+  std::vector<int32_t> ends;
+  std::vector<int4> hrows;
+  for (int64_t i = 0; i < rows; ++i) {
+    const int32_t e0 = rp[i], e1 = rp[i + 1];
+    if (e1 - e0 <= hp->threshold) continue;
+    const int first = (int)chunks.size();
+    for (int32_t e = e0; e < e1; e += hp->chunk) {
+      chunks.push_back(make_int2((int)i, e));
+      ends.push_back(std::min<int32_t>(e1, e + hp->chunk));
+    }
+    hrows.push_back(make_int4((int)i, first, (int)chunks.size() - first, 0));
+  }
+  hp->n_rows = (int32_t)hrows.size();
+  hp->n_chunks = (int32_t)chunks.size();
+  if (hp->n_chunks == 0) return ISVD_OK;
+  hp->chunks = (int2 *)owned_alloc(op, sizeof(int2) * chunks.size(), s);
+  hp->chunk_end = (int32_t *)owned_alloc(op, sizeof(int32_t) * ends.size(), s);
+  hp->rows = (int4 *)owned_alloc(op, sizeof(int4) * hrows.size(), s);
+  if (!hp->chunks || !hp->chunk_end || !hp->rows) return fail(ISVD_ERR_WORKSPACE, "heavy-row plan allocation failed");
+  ISVD_CUDA_TRY(cudaMemcpyAsync(hp->chunks, chunks.data(), sizeof(int2) * chunks.size(), cudaMemcpyHostToDevice, s));
+  ISVD_CUDA_TRY(cudaMemcpyAsync(hp->chunk_end, ends.data(), sizeof(int32_t) * ends.size(), cudaMemcpyHostToDevice, s));
+  ISVD_CUDA_TRY(cudaMemcpyAsync(hp->rows, hrows.data(), sizeof(int4) * hrows.size(), cudaMemcpyHostToDevice, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  return ISVD_OK;
+}
+
+isvd_status check_csr_host(const isvd_csr &m, const char *name) {
+  if (m.rows < 1 || m.cols < 1) return fail(ISVD_ERR_INVALID_ARGUMENT, "%s: empty shape", name);
+  if (m.nnz < 0 || m.nnz >= ((int64_t)1 << 31)) return fail(ISVD_ERR_INVALID_ARGUMENT, "%s: nnz out of range", name);
+  if (m.rows >= ((int64_t)1 << 31) || m.cols >= ((int64_t)1 << 31))
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "%s: dimension >= 2^31", name);
+  if (!m.rowptr || (m.nnz > 0 && !m.colidx)) return fail(ISVD_ERR_INVALID_ARGUMENT, "%s: null CSR array", name);
+  return ISVD_OK;
+}
+
+isvd_status validate_csr_dev(isvd_operator *op, const isvd_csr &m, int32_t *flags, const char *name, cudaStream_t s) {
+  ISVD_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 8, s));
+  validate_csr_kernel<<<grid_for(std::max(m.rows + 1, m.nnz)), 256, 0, s>>>(m.rows, m.cols, m.nnz, m.rowptr,
+                                                                            m.colidx, m.values, flags);
+  ISVD_CUDA_TRY(cudaGetLastError());
+  int32_t h[8];
+  ISVD_CUDA_TRY(cudaMemcpyAsync(h, flags, sizeof h, cudaMemcpyDeviceToHost, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  (void)op;
+  if (h[0]) return fail(ISVD_ERR_INVALID_GRAPH, "%s: rowptr is not a valid CSR row pointer", name);
+  if (h[1]) return fail(ISVD_ERR_INVALID_GRAPH, "%s: column index out of range", name);
+  if (h[2]) return fail(ISVD_ERR_INVALID_GRAPH, "%s: non-finite value", name);
+  return ISVD_OK;
+}
+
+// Stable transpose of a CSR (rows x cols) into (cols x rows) with explicit values.
+isvd_status transpose_csr(isvd_operator *op, int64_t rows, int64_t cols, int64_t nnz, const int32_t *rowptr,
+                          const int32_t *colidx, const float *values, int32_t **t_rowptr, int32_t **t_colidx,
+                          float **t_values, cudaStream_t s) {
+  Scratch sc{op, s, {}};
+  int32_t *keys_out = (int32_t *)sc.get(sizeof(int32_t) * nnz);
+  int32_t *idx_in = (int32_t *)sc.get(sizeof(int32_t) * nnz);
+  int32_t *idx_out = (int32_t *)sc.get(sizeof(int32_t) * nnz);
+  int32_t *row_of = (int32_t *)sc.get(sizeof(int32_t) * nnz);
+  int32_t *counts = (int32_t *)sc.get(sizeof(int32_t) * (cols + 1));
+  *t_rowptr = (int32_t *)owned_alloc(op, sizeof(int32_t) * (cols + 1), s);
+  *t_colidx = (int32_t *)owned_alloc(op, sizeof(int32_t) * nnz, s);
+  *t_values = (float *)owned_alloc(op, sizeof(float) * nnz, s);
+  if (!keys_out || !idx_in || !idx_out || !row_of || !counts || !*t_rowptr || !*t_colidx || !*t_values)
+    return fail(ISVD_ERR_WORKSPACE, "transpose workspace allocation failed");
+  iota_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, idx_in);
+  row_of_entry_kernel<<<grid_for(rows), 256, 0, s>>>(rows, rowptr, row_of);
+  ISVD_CUDA_TRY(cudaGetLastError());
+  size_t tmp_bytes = 0;
+  const int end_bit = bits_for((uint64_t)cols);
+  ISVD_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, colidx, keys_out, idx_in, idx_out, (int)nnz, 0,
+                                                end_bit, s));
+  void *tmp = sc.get(tmp_bytes);
+  if (!tmp) return fail(ISVD_ERR_WORKSPACE, "sort workspace allocation failed");
+  ISVD_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, colidx, keys_out, idx_in, idx_out, (int)nnz, 0,
+                                                end_bit, s));
+  gather_transpose_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, idx_out, row_of, values, *t_colidx, *t_values);
+  ISVD_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (cols + 1), s));
+  count_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, keys_out, counts);
+  ISVD_CUDA_TRY(cudaGetLastError());
+  size_t scan_bytes = 0;
+  ISVD_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, counts, *t_rowptr, (int)(cols + 1), s));
+  void *tmp2 = sc.get(scan_bytes);
+  if (!tmp2) return fail(ISVD_ERR_WORKSPACE, "scan workspace allocation failed");
+  ISVD_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp2, scan_bytes, counts, *t_rowptr, (int)(cols + 1), s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  return ISVD_OK;
+}
+
+// A == A^T (pattern and values) by sorting the (row, col) and (col, row) keys.
+isvd_status check_symmetry(isvd_operator *op, const isvd_csr &A, int32_t *flags, cudaStream_t s) {
+  const int64_t nnz = A.nnz, n = A.rows;
+  if (nnz == 0) return ISVD_OK;
+  Scratch sc{op, s, {}};
+  uint64_t *ka = (uint64_t *)sc.get(sizeof(uint64_t) * nnz);
+  uint64_t *kb = (uint64_t *)sc.get(sizeof(uint64_t) * nnz);
+  uint64_t *ka2 = (uint64_t *)sc.get(sizeof(uint64_t) * nnz);
+  uint64_t *kb2 = (uint64_t *)sc.get(sizeof(uint64_t) * nnz);
+  float *va = nullptr, *vb = nullptr;
+  if (A.values) {
+    va = (float *)sc.get(sizeof(float) * nnz);
+    vb = (float *)sc.get(sizeof(float) * nnz);
+  }
+  if (!ka || !kb || !ka2 || !kb2 || (A.values && (!va || !vb)))
+    return fail(ISVD_ERR_WORKSPACE, "symmetry-check workspace allocation failed");
+  edge_keys_kernel<<<grid_for(n), 256, 0, s>>>(n, nnz, A.rowptr, A.colidx, ka, kb);
+  ISVD_CUDA_TRY(cudaGetLastError());
+  const int end_bit = bits_for((uint64_t)n * (uint64_t)n);
+  size_t tmp_bytes = 0;
+  if (A.values)
+    ISVD_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, ka, ka2, A.values, va, (int)nnz, 0, end_bit, s));
+  else
+    ISVD_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, ka, ka2, (int)nnz, 0, end_bit, s));
+  void *tmp = sc.get(tmp_bytes);
+  if (!tmp) return fail(ISVD_ERR_WORKSPACE, "sort workspace allocation failed");
+  if (A.values) {
+    ISVD_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, ka, ka2, A.values, va, (int)nnz, 0, end_bit, s));
+    ISVD_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, kb, kb2, A.values, vb, (int)nnz, 0, end_bit, s));
+  } else {
+    ISVD_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, ka, ka2, (int)nnz, 0, end_bit, s));
+    ISVD_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp, tmp_bytes, kb, kb2, (int)nnz, 0, end_bit, s));
+  }
+  ISVD_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 8, s));
+  compare_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, ka2, kb2, va, vb, flags);
+  ISVD_CUDA_TRY(cudaGetLastError());
+  int32_t h[8];
+  ISVD_CUDA_TRY(cudaMemcpyAsync(h, flags, sizeof h, cudaMemcpyDeviceToHost, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h[4]) return fail(ISVD_ERR_INVALID_GRAPH, "A is not symmetric (pattern or values)");
+  return ISVD_OK;
+}
+
+isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaStream_t s) {
+  const isvd_operator_desc &d = *desc;
+  ISVD_TRY(check_csr_host(d.A, "A"));
+  if (d.A.rows != d.A.cols) return fail(ISVD_ERR_SHAPE, "A must be square");
+  if (d.norm != ISVD_NORM_ROW && d.norm != ISVD_NORM_SYM_SELFLOOP)
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown normalisation %d", (int)d.norm);
+  op->n = d.A.rows;
+  if (d.form == ISVD_FORM_POLY) {
+    if (d.degree < 1 || d.degree > ISVD_MAX_DEGREE)
+      return fail(ISVD_ERR_INVALID_ARGUMENT, "degree must be in 1..%d", ISVD_MAX_DEGREE);
+    if (!d.coeffs) return fail(ISVD_ERR_INVALID_ARGUMENT, "coeffs is null");
+    if (d.lr_rank < 0 || d.lr_rank > ISVD_MAX_LOWRANK - 1)
+      return fail(ISVD_ERR_INVALID_ARGUMENT, "lr_rank must be in 0..%d", ISVD_MAX_LOWRANK - 1);
+    if (d.lr_rank > 0 && (!d.lr_u || !d.lr_v || !d.lr_alpha))
+      return fail(ISVD_ERR_INVALID_ARGUMENT, "low-rank factors are null");
+    if (!std::isfinite(d.ones_coeff) || !std::isfinite(d.adj_coeff))
+      return fail(ISVD_ERR_INVALID_ARGUMENT, "non-finite coefficient");
+    op->coeffs.assign(d.coeffs, d.coeffs + d.degree);
+    for (double c : op->coeffs)
+      if (!std::isfinite(c)) return fail(ISVD_ERR_INVALID_ARGUMENT, "non-finite polynomial coefficient");
+    if (d.lr_rank > 0) op->lr_alpha.assign(d.lr_alpha, d.lr_alpha + d.lr_rank);
+    op->rows = op->cols = op->n;
+  } else if (d.form == ISVD_FORM_CONCAT) {
+    if (d.L < 0 || d.L > 8) return fail(ISVD_ERR_INVALID_ARGUMENT, "L must be in 0..8");
+    if (d.d < 1) return fail(ISVD_ERR_INVALID_ARGUMENT, "feature width d must be >= 1");
+    if (d.ones_coeff != 0.0 || d.adj_coeff != 0.0 || d.lr_rank != 0)
+      return fail(ISVD_ERR_UNSUPPORTED, "corrections are only implemented for the polynomial form");
+    const bool sparse = d.X.rowptr != nullptr;
+    if (sparse == (d.X_dense != nullptr)) return fail(ISVD_ERR_INVALID_ARGUMENT, "give exactly one of X (CSR) and X_dense");
+    if (sparse) {
+      ISVD_TRY(check_csr_host(d.X, "X"));
+      if (d.X.rows != op->n || d.X.cols != d.d) return fail(ISVD_ERR_SHAPE, "X must be n x d");
+    } else if (op->n * d.d >= ((int64_t)1 << 31)) {
+      return fail(ISVD_ERR_UNSUPPORTED, "dense X with n*d >= 2^31 entries");
+    }
+    op->rows = op->n;
+    op->cols = d.d * (d.L + 1);
+  } else {
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown form %d", (int)d.form);
+  }
+  ISVD_CUDA_TRY(small_kernels_init());
+  ISVD_CUDA_TRY(dense_kernels_init());
+  ISVD_CUDA_TRY(cudaStreamCreateWithFlags(&op->capture_stream, cudaStreamNonBlocking));
+
+  const int64_t n = op->n;
+  float *vecs = (float *)owned_alloc(op, sizeof(float) * 4 * n, s);
+  int32_t *flags = (int32_t *)owned_alloc(op, sizeof(int32_t) * 8, s);
+  if (!vecs || !flags) return fail(ISVD_ERR_WORKSPACE, "operator allocation failed");
+  op->deg = vecs;
+  op->inv_d = vecs + n;
+  op->s = vecs + 2 * n;
+  op->s2 = vecs + 3 * n;
+  ISVD_TRY(validate_csr_dev(op, d.A, flags, "A", s));
+  ISVD_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 8, s));
+  degree_kernel<<<grid_for(n), 256, 0, s>>>(n, d.A.rowptr, d.A.values, d.norm == ISVD_NORM_ROW ? 1 : 0, op->deg,
+                                            op->inv_d, op->s, op->s2, flags);
+  ISVD_CUDA_TRY(cudaGetLastError());
+  {
+    int32_t h[8];
+    ISVD_CUDA_TRY(cudaMemcpyAsync(h, flags, sizeof h, cudaMemcpyDeviceToHost, s));
+    ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h[3])
+      return fail(ISVD_ERR_INVALID_GRAPH,
+                  "a row of A has zero (or negative) degree: T = D^-1 A is undefined (add a self-loop)");
+  }
+  if (!(d.flags & ISVD_FLAG_SKIP_SYMMETRY_CHECK)) ISVD_TRY(check_symmetry(op, d.A, flags, s));
+  ISVD_TRY(build_heavy(op, d.A.rowptr, n, &op->heavy_A, s));
+
+  if (d.form == ISVD_FORM_CONCAT) {
+    if (d.X.rowptr) {
+      ISVD_TRY(validate_csr_dev(op, d.X, flags, "X", s));
+      op->x_rowptr = d.X.rowptr;
+      op->x_colidx = d.X.colidx;
+      op->x_values = d.X.values;
+      op->x_nnz = d.X.nnz;
+    } else {
+      const int64_t nnz = n * d.d;
+      op->xd_rowptr = (int32_t *)owned_alloc(op, sizeof(int32_t) * (n + 1), s);
+      op->xd_colidx = (int32_t *)owned_alloc(op, sizeof(int32_t) * nnz, s);
+      if (!op->xd_rowptr || !op->xd_colidx) return fail(ISVD_ERR_WORKSPACE, "dense-X index allocation failed");
+      dense_csr_kernel<<<grid_for(nnz), 256, 0, s>>>(n, d.d, op->xd_rowptr, op->xd_colidx);
+      ISVD_CUDA_TRY(cudaGetLastError());
+      op->x_rowptr = op->xd_rowptr;
+      op->x_colidx = op->xd_colidx;
+      op->x_values = d.X_dense;
+      op->x_nnz = nnz;
+    }
+    ISVD_TRY(transpose_csr(op, n, d.d, op->x_nnz, op->x_rowptr, op->x_colidx, op->x_values, &op->xt_rowptr,
+                           &op->xt_colidx, &op->xt_values, s));
+    ISVD_TRY(build_heavy(op, op->x_rowptr, n, &op->heavy_X, s));
+    ISVD_TRY(build_heavy(op, op->xt_rowptr, d.d, &op->heavy_XT, s));
+  }
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  return ISVD_OK;
+}
+
+// ---- apply ---------------------------------------------------------------------
+
+struct Chain {
+  const isvd_operator *op;
+  int dtype;
+  cudaStream_t s;
+  const ApplyScratch *sc;
+};
+
+int slab_cols(const isvd_operator *op, int dtype) { return dtype == DT_F32 ? op->slab_cols_f32 : op->slab_cols_bf16; }
+
+SpmmArgs base_args_A(const isvd_operator *op) {
+  SpmmArgs a{};
+  a.rows = op->n;
+  a.rowptr = op->desc.A.rowptr;
+  a.colidx = op->desc.A.colidx;
+  a.values = op->desc.A.values;
+  a.scalar = 1.f;
+  a.ax_scalar = 1.f;
+  a.heavy_threshold = op->heavy_A.n_chunks > 0 ? op->heavy_A.threshold : INT_MAX;
+  return a;
+}
+
+// fill slabs for one segment of width b
+void add_slabs(SpmmArgs &a, int dtype, int32_t b, int32_t scols, int32_t col_base, const void *in, int64_t ldi,
+               void *out, int64_t ldo, const void *axpy, int64_t lda) {
+  SpmmSlab tmp[kMaxSlabs];
+  const int ns = make_slabs(dtype, b, scols, tmp);
+  const size_t es = dtype_size(dtype);
+  for (int i = 0; i < ns && a.nslabs < kMaxSlabs; ++i) {
+    SpmmSlab sl = tmp[i];
+    sl.in = (const char *)in + (size_t)sl.col0 * es;
+    sl.ldi = ldi;
+    sl.out = (char *)out + (size_t)sl.col0 * es;
+    sl.ldo = ldo;
+    sl.axpy = axpy ? (const char *)axpy + (size_t)sl.col0 * es : nullptr;
+    sl.lda = lda;
+    sl.col0 += col_base;
+    a.slab[a.nslabs++] = sl;
+  }
+}
+
+int slabs_needed(int dtype, int32_t b, int32_t scols) {
+  const int vn = dtype == DT_F32 ? 4 : 8;
+  int sc = scols > 32 * vn ? 32 * vn : scols;
+  return (int)ceil_div(b, sc);
+}
+
+cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, int64_t pw) {
+  return spmm_launch(a, c.dtype, hp, c.sc->heavy_partial, pw, c.s);
+}
+
+}  // namespace
+
+size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool transpose) {
+  (void)transpose;
+  const size_t es = dtype_size(dtype);
+  const int64_t bseg = round_up(b, 8);
+  size_t total = 0;
+  auto add = [&](size_t x) { total += (size_t)round_up((int64_t)x, 256); };
+  add(es * op->n * bseg);  // z1
+  add(es * op->n * bseg);  // z2
+  int64_t pw = bseg;
+  if (op->desc.form == ISVD_FORM_CONCAT) {
+    add(es * op->n * bseg * (op->desc.L + 1));  // P
+    pw = bseg * (op->desc.L + 1);
+  }
+  const int r = (op->desc.ones_coeff != 0.0 ? 1 : 0) + op->desc.lr_rank;
+  add(sizeof(float) * (size_t)std::max(r, 1) * bseg);
+  add(sizeof(double) * (size_t)lowrank_partials(op->n) * std::max(r, 1) * bseg);
+  int64_t chunks = std::max<int64_t>({op->heavy_A.n_chunks, op->heavy_X.n_chunks, op->heavy_XT.n_chunks, 1});
+  add(sizeof(float) * (size_t)chunks * pw);
+  return total;
+}
+
+void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool transpose, char *base,
+                         ApplyScratch *sc) {
+  (void)transpose;
+  const size_t es = dtype_size(dtype);
+  const int64_t bseg = round_up(b, 8);
+  size_t off = 0;
+  auto take = [&](size_t x) {
+    char *p = base + off;
+    off += (size_t)round_up((int64_t)x, 256);
+    return p;
+  };
+  sc->z1 = take(es * op->n * bseg);
+  sc->z2 = take(es * op->n * bseg);
+  if (op->desc.form == ISVD_FORM_CONCAT) sc->p = take(es * op->n * bseg * (op->desc.L + 1));
+  const int r = (op->desc.ones_coeff != 0.0 ? 1 : 0) + op->desc.lr_rank;
+  sc->lr_c = (float *)take(sizeof(float) * (size_t)std::max(r, 1) * bseg);
+  sc->lr_partial = (double *)take(sizeof(double) * (size_t)lowrank_partials(op->n) * std::max(r, 1) * bseg);
+  int64_t pw = op->desc.form == ISVD_FORM_CONCAT ? bseg * (op->desc.L + 1) : bseg;
+  int64_t chunks = std::max<int64_t>({op->heavy_A.n_chunks, op->heavy_X.n_chunks, op->heavy_XT.n_chunks, 1});
+  sc->heavy_partial = (float *)take(sizeof(float) * (size_t)chunks * pw);
+}
+
+// Horner evaluation of sum_{k=1..K} c_k N^k G (+ corrections), Eq. 3 with the
+// products taken right to left (Sec. 4; App. A.3's lazy cache is subsumed:
+// K sparse products per apply).  N^T for N = D^-1 A is A D^-1 (A symmetric),
+// evaluated on D^-1-scaled iterates; Â is symmetric and evaluated on
+// (D+I)^-1/2-scaled iterates so that only the first product gathers a weight.
+static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
+                              int dtype, bool transpose, const ApplyScratch &sc, cudaStream_t s) {
+  const isvd_operator_desc &d = op->desc;
+  const int K = d.degree;
+  const std::vector<double> &c = op->coeffs;  // c[k-1] = c_k
+  const bool row = d.norm == ISVD_NORM_ROW;
+  const int64_t bseg = round_up(b, 8);
+  const int scols = slab_cols(op, dtype);
+  const Chain ch{op, dtype, s, &sc};
+
+  // corrections: c = V^T G with the all-ones vector first (transpose swaps u and v)
+  const int ones = d.ones_coeff != 0.0 ? 1 : 0;
+  const int r = ones + d.lr_rank;
+  if (r > 0) {
+    const float *V = transpose ? d.lr_u : d.lr_v;
+    ISVD_CUDA_TRY(lowrank_project_launch(G, ldg, dtype, op->n, b, d.lr_rank ? V : nullptr, d.lr_rank, r, ones,
+                                         sc.lr_partial, lowrank_partials(op->n), sc.lr_c, bseg, s));
+  }
+  auto set_lowrank = [&](SpmmArgs &a) {
+    if (r == 0) return;
+    a.lr_rank = r;
+    a.lr_ones_first = ones;
+    a.lr_u = d.lr_rank ? (transpose ? d.lr_v : d.lr_u) : nullptr;
+    a.lr_ldu = d.lr_rank;
+    a.lr_c = sc.lr_c;
+    a.lr_ldc = bseg;
+    int t = 0;
+    if (ones) a.lr_alpha[t++] = (float)d.ones_coeff;
+    for (int q = 0; q < d.lr_rank; ++q) a.lr_alpha[t++] = (float)op->lr_alpha[q];
+  };
+
+  const void *cur = G;
+  int64_t ldcur = ldg;
+  void *bufs[2] = {sc.z1, sc.z2};
+  int which = 0;
+  for (int step = K; step >= 1; --step) {
+    // step k computes Z_{k-1}-like iterate: first step (k == K) consumes G itself
+    const bool first = step == K;
+    const bool last = step == 1;
+    SpmmArgs a = base_args_A(op);
+    a.scalar = first ? (float)c[K - 1] : 1.f;
+    void *dst = last ? out : bufs[which];
+    const int64_t lddst = last ? ldo : bseg;
+    const void *axp = nullptr;
+    if (!last) {
+      axp = G;
+      a.ax_scalar = (float)c[step - 2];
+    }
+    if (row && !transpose) {
+      a.rowscale = op->inv_d;
+    } else if (row && transpose) {
+      if (first) a.colw = op->inv_d;
+      a.rowscale = last ? nullptr : op->inv_d;
+      a.ax_rowscale = op->inv_d;
+    } else {  // Â
+      if (first) a.colw = op->s;
+      a.self_term = 1;
+      a.rowscale = last ? op->s : op->s2;
+      a.ax_rowscale = op->s;
+    }
+    if (last) set_lowrank(a);
+    add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, axp, ldg);
+    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, bseg));
+    cur = dst;
+    ldcur = lddst;
+    which ^= 1;
+  }
+  if (d.adj_coeff != 0.0) {
+    // + beta A G  (A symmetric, so the same for the transpose)
+    SpmmArgs a = base_args_A(op);
+    a.scalar = (float)d.adj_coeff;
+    a.ax_scalar = 1.f;
+    add_slabs(a, dtype, b, scols, 0, G, ldg, out, ldo, out, ldo);
+    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, bseg));
+  }
+  return ISVD_OK;
+}
+
+// M = [X | N X | ... | N^L X] (Eq. 6).  M G = sum_l N^l X G_l evaluated as
+// P = X [G_0 | ... | G_L] (one sparse product over all blocks), then Horner
+// Y = P_L, Y <- P_l + N Y.  M^T H = [X^T H ; X^T N^T H ; ...]: the iterates
+// N^T^l H are stacked side by side and X^T is applied once to all of them.
+static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
+                                int dtype, bool transpose, const ApplyScratch &sc, cudaStream_t s) {
+  const isvd_operator_desc &d = op->desc;
+  const int L = d.L;
+  const bool row = d.norm == ISVD_NORM_ROW;
+  const int64_t bseg = round_up(b, 8);
+  const int64_t ldp = bseg * (L + 1);
+  const size_t es = dtype_size(dtype);
+  const int scols = slab_cols(op, dtype);
+  const Chain ch{op, dtype, s, &sc};
+  if ((int64_t)(L + 1) * slabs_needed(dtype, b, scols) > kMaxSlabs)
+    return fail(ISVD_ERR_UNSUPPORTED, "block too wide for the stacked feature product (L+1 = %d, b = %d)", L + 1, b);
+  char *P = (char *)sc.p;
+  auto seg = [&](int l) { return P + (size_t)l * bseg * es; };
+
+  if (!transpose) {
+    // P_l = X G_l
+    SpmmArgs ax{};
+    ax.rows = op->n;
+    ax.rowptr = op->x_rowptr;
+    ax.colidx = op->x_colidx;
+    ax.values = op->x_values;
+    ax.scalar = 1.f;
+    ax.ax_scalar = 1.f;
+    ax.heavy_threshold = op->heavy_X.n_chunks > 0 ? op->heavy_X.threshold : INT_MAX;
+    for (int l = 0; l <= L; ++l) {
+      const char *gin = (const char *)G + (size_t)l * d.d * ldg * es;
+      if (L == 0) add_slabs(ax, dtype, b, scols, 0, gin, ldg, out, ldo, nullptr, 0);
+      else add_slabs(ax, dtype, b, scols, (int32_t)(l * bseg), gin, ldg, seg(l), ldp, nullptr, 0);
+    }
+    ISVD_CUDA_TRY(run(ch, ax, op->heavy_X, ldp));
+    if (L == 0) return ISVD_OK;
+    // Horner over N
+    const void *cur = seg(L);
+    int64_t ldcur = ldp;
+    void *bufs[2] = {sc.z1, sc.z2};
+    int which = 0;
+    for (int l = L - 1; l >= 0; --l) {
+      const bool first = l == L - 1, last = l == 0;
+      SpmmArgs a = base_args_A(op);
+      void *dst = last ? out : bufs[which];
+      const int64_t lddst = last ? ldo : bseg;
+      if (row) {
+        a.rowscale = op->inv_d;
+      } else {
+        if (first) a.colw = op->s;
+        a.self_term = 1;
+        a.rowscale = last ? op->s : op->s2;
+        a.ax_rowscale = last ? nullptr : op->s;
+      }
+      add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, seg(l), ldp);
+      ISVD_CUDA_TRY(run(ch, a, op->heavy_A, bseg));
+      cur = dst;
+      ldcur = lddst;
+      which ^= 1;
+    }
+    return ISVD_OK;
+  }
+  // transpose: Q_0 = H, Q_l = N^T Q_{l-1} into P's segments
+  const void *cur = G;
+  int64_t ldcur = ldg;
+  for (int l = 1; l <= L; ++l) {
+    SpmmArgs a = base_args_A(op);
+    if (row) {
+      a.colw = op->inv_d;  // T^T = A D^-1
+    } else {
+      a.colw = op->s;
+      a.self_term = 1;
+      a.rowscale = op->s;
+    }
+    add_slabs(a, dtype, b, scols, 0, cur, ldcur, seg(l), ldp, nullptr, 0);
+    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, bseg));
+    cur = seg(l);
+    ldcur = ldp;
+  }
+  SpmmArgs at{};
+  at.rows = d.d;
+  at.rowptr = op->xt_rowptr;
+  at.colidx = op->xt_colidx;
+  at.values = op->xt_values;
+  at.scalar = 1.f;
+  at.ax_scalar = 1.f;
+  at.heavy_threshold = op->heavy_XT.n_chunks > 0 ? op->heavy_XT.threshold : INT_MAX;
+  for (int l = 0; l <= L; ++l) {
+    const void *in = l == 0 ? G : (const void *)seg(l);
+    const int64_t ldi = l == 0 ? ldg : ldp;
+    char *o = (char *)out + (size_t)l * d.d * ldo * es;
+    add_slabs(at, dtype, b, scols, (int32_t)(l * bseg), in, ldi, o, ldo, nullptr, 0);
+  }
+  ISVD_CUDA_TRY(run(ch, at, op->heavy_XT, ldp));
+  return ISVD_OK;
+}
+
+isvd_status apply_impl(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo, int dtype,
+                       bool transpose, const ApplyScratch &sc, cudaStream_t s) {
+  if (op->desc.form == ISVD_FORM_POLY) return apply_poly(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
+  return apply_concat(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
+}
+
+}  // namespace isvd
+
+using namespace isvd;
+
+extern "C" {
+
+const char *isvd_last_error(void) { return isvd::last_error(); }
+
+const char *isvd_status_string(isvd_status s) {
+  switch (s) {
+    case ISVD_OK: return "ok";
+    case ISVD_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case ISVD_ERR_INVALID_GRAPH: return "invalid graph";
+    case ISVD_ERR_SHAPE: return "shape mismatch";
+    case ISVD_ERR_NOT_POSITIVE_DEFINITE: return "Gram matrix not positive definite";
+    case ISVD_ERR_TIMEOUT: return "device wait timed out";
+    case ISVD_ERR_WORKSPACE: return "workspace allocation failed";
+    case ISVD_ERR_CUDA: return "CUDA error";
+    case ISVD_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+isvd_status isvd_create_operator(const isvd_operator_desc *desc, const isvd_allocator *alloc, void *stream,
+                                 isvd_operator **out) {
+  if (!desc || !out) return fail(ISVD_ERR_INVALID_ARGUMENT, "null descriptor or output");
+  *out = nullptr;
+  isvd_operator *op = new isvd_operator();
+  op->desc = *desc;
+  if (alloc) {
+    if (!alloc->alloc || !alloc->free) {
+      delete op;
+      return fail(ISVD_ERR_INVALID_ARGUMENT, "allocator with null callbacks");
+    }
+    op->alloc = *alloc;
+    op->has_alloc = true;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const isvd_status st = create_impl(desc, op, s);
+  if (st != ISVD_OK) {
+    const std::string keep = isvd::last_error();
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    isvd_destroy_operator(op);
+    isvd::set_error("%s", keep.c_str());
+    return st;
+  }
+  // descriptor copies must not keep pointers into caller-owned host arrays
+  op->desc.coeffs = nullptr;
+  op->desc.lr_alpha = nullptr;
+  *out = op;
+  return ISVD_OK;
+}
+
+void isvd_destroy_operator(isvd_operator *op) {
+  if (!op) return;
+  cudaDeviceSynchronize();
+  for (auto &g : op->graphs) cudaGraphExecDestroy(g.exec);
+  op->graphs.clear();
+  cudaStream_t s = nullptr;
+  op_free(op, op->arena, s);
+  for (void *p : op->owned) op_free(op, p, s);
+  if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
+  cudaStreamSynchronize(s);
+  delete op;
+}
+
+isvd_status isvd_operator_shape(const isvd_operator *op, int64_t *rows, int64_t *cols) {
+  if (!op || !rows || !cols) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  *rows = op->rows;
+  *cols = op->cols;
+  return ISVD_OK;
+}
+
+static isvd_status apply_entry(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
+                               isvd_dtype dtype, void *stream, bool transpose) {
+  if (!op || !G || !out) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (dtype != ISVD_F32 && dtype != ISVD_BF16) return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown dtype");
+  if (b < 1 || b > 1024) return fail(ISVD_ERR_INVALID_ARGUMENT, "block width b must be in 1..1024");
+  if (ldg < b || ldo < b || ldg % 8 || ldo % 8) return fail(ISVD_ERR_INVALID_ARGUMENT, "ld must be >= b and a multiple of 8");
+  if (((uintptr_t)G | (uintptr_t)out) & 15) return fail(ISVD_ERR_INVALID_ARGUMENT, "blocks must be 16-byte aligned");
+  const int dt = dtype == ISVD_F32 ? DT_F32 : DT_BF16;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = apply_scratch_bytes(op, b, dt, transpose);
+  ISVD_TRY(ensure_arena(op, bytes, s));
+  ApplyScratch sc;
+  apply_scratch_carve(op, b, dt, transpose, (char *)op->arena, &sc);
+  return apply_impl(op, G, ldg, b, out, ldo, dt, transpose, sc, s);
+}
+
+isvd_status isvd_apply(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
+                       isvd_dtype dtype, void *stream) {
+  return apply_entry(op, G, ldg, b, out, ldo, dtype, stream, false);
+}
+
+isvd_status isvd_apply_T(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
+                         isvd_dtype dtype, void *stream) {
+  return apply_entry(op, G, ldg, b, out, ldo, dtype, stream, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,330 @@
+// Sparse x tall-skinny dense products with fused epilogues.
+//
+// Every implicit product of the paper reduces to the row computation
+//     y_i = s * r_i * ( sum_{j in N(i)} a_ij w_j z_j  +  [self] w_i z_i )
+//           + a * h_i * x_i  +  sum_t alpha_t u_it c_t
+// (Sec. 4: only M.G and M^T.G are needed).  The Horner form of the
+// polynomial sum_k c_k N^k G (Eq. 3) is a chain of such rows with the axpy
+// term carrying c_k G; N = D^-1 A uses r = 1/d, N = Â uses gathered w = s
+// and the self term for +I; the all-ones and low-rank corrections of Eq. 3
+// are the last term, broadcast from precomputed c = V^T G (the O(n) product
+// of Sec. 4's outer-product example).
+//
+// Layout: dense blocks are row-major.  A launch covers column slabs (grid y);
+// inside a slab `group` lanes cooperate on one row, each lane owning 16 bytes
+// of columns, so one gathered neighbour row is one coalesced 32..128-byte
+// read.  Slabs run one after another in launch order so that the slab of
+// the gathered block stays resident in L2.  Rows with more than
+// `heavy_threshold` nonzeros are split into chunks whose partial sums are
+// combined in chunk order, so results are deterministic.
+#include "internal.h"
+
+namespace isvd {
+namespace {
+
+template <int DT>
+struct Vec;
+
+template <>
+struct Vec<DT_F32> {
+  static constexpr int N = 4;
+  static constexpr int BYTES = 4;
+  __device__ __forceinline__ static void load(const void *p, float *v) {
+    const float4 x = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+  __device__ __forceinline__ static void load_plain(const void *p, float *v) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+  __device__ __forceinline__ static void store(void *p, const float *v, int valid) {
+    float *q = reinterpret_cast<float *>(p);
+    if (valid >= 4) {
+      *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      for (int k = 0; k < valid; ++k) q[k] = v[k];
+    }
+  }
+};
+
+template <>
+struct Vec<DT_BF16> {
+  static constexpr int N = 8;
+  static constexpr int BYTES = 2;
+  __device__ __forceinline__ static void unpack(const uint4 x, float *v) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&x);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __bfloat1622float2(h[k]);
+      v[2 * k] = f.x;
+      v[2 * k + 1] = f.y;
+    }
+  }
+  __device__ __forceinline__ static void load(const void *p, float *v) {
+    unpack(__ldg(reinterpret_cast<const uint4 *>(p)), v);
+  }
+  __device__ __forceinline__ static void load_plain(const void *p, float *v) {
+    unpack(*reinterpret_cast<const uint4 *>(p), v);
+  }
+  __device__ __forceinline__ static void store(void *p, const float *v, int valid) {
+    if (valid >= 8) {
+      uint4 x;
+      __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&x);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+      *reinterpret_cast<uint4 *>(p) = x;
+    } else {
+      __nv_bfloat16 *q = reinterpret_cast<__nv_bfloat16 *>(p);
+      for (int k = 0; k < valid; ++k) q[k] = __float2bfloat16_rn(v[k]);
+    }
+  }
+};
+
+struct Lane {
+  int G;          // lanes per row
+  int gl;         // lane within the group
+  int sub;        // group index within the warp
+  unsigned mask;  // lanes of this group
+  int col;        // first column (within the slab) owned by this lane
+  bool active;    // col < width
+};
+
+template <int DT>
+__device__ __forceinline__ Lane make_lane(const SpmmSlab &sl) {
+  Lane L;
+  const int lane = threadIdx.x & 31;
+  L.G = sl.group;
+  L.gl = lane & (L.G - 1);
+  L.sub = lane / L.G;
+  L.mask = (L.G == 32) ? 0xffffffffu : (((1u << L.G) - 1u) << (L.sub * L.G));
+  L.col = L.gl * Vec<DT>::N;
+  L.active = L.col < sl.width;
+  return L;
+}
+
+// acc += sum over nonzeros e in [e0, e1) of a_e w_j in_j (slab columns of this lane)
+template <int DT>
+__device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int e0,
+                                             int e1, float *acc) {
+  using V = Vec<DT>;
+  constexpr int VN = V::N;
+  const char *inb = reinterpret_cast<const char *>(sl.in) + (size_t)L.col * V::BYTES;
+  const size_t ldb = (size_t)sl.ldi * V::BYTES;
+  for (int e = e0; e < e1; e += L.G) {
+    const int me = e + L.gl;
+    int j = 0;
+    float w = 0.f;
+    if (me < e1) {
+      j = __ldg(a.colidx + me);
+      w = a.values ? __ldg(a.values + me) : 1.f;
+      if (a.colw) w *= __ldg(a.colw + j);
+    }
+    const int cnt = min(L.G, e1 - e);
+    int t = 0;
+    for (; t + 4 <= cnt; t += 4) {
+      const int j0 = __shfl_sync(L.mask, j, t, L.G);
+      const int j1 = __shfl_sync(L.mask, j, t + 1, L.G);
+      const int j2 = __shfl_sync(L.mask, j, t + 2, L.G);
+      const int j3 = __shfl_sync(L.mask, j, t + 3, L.G);
+      const float w0 = __shfl_sync(L.mask, w, t, L.G);
+      const float w1 = __shfl_sync(L.mask, w, t + 1, L.G);
+      const float w2 = __shfl_sync(L.mask, w, t + 2, L.G);
+      const float w3 = __shfl_sync(L.mask, w, t + 3, L.G);
+      if (L.active) {
+        float v0[VN], v1[VN], v2[VN], v3[VN];
+        V::load(inb + (size_t)j0 * ldb, v0);
+        V::load(inb + (size_t)j1 * ldb, v1);
+        V::load(inb + (size_t)j2 * ldb, v2);
+        V::load(inb + (size_t)j3 * ldb, v3);
+#pragma unroll
+        for (int k = 0; k < VN; ++k) {
+          acc[k] = fmaf(w0, v0[k], acc[k]);
+          acc[k] = fmaf(w1, v1[k], acc[k]);
+          acc[k] = fmaf(w2, v2[k], acc[k]);
+          acc[k] = fmaf(w3, v3[k], acc[k]);
+        }
+      }
+    }
+    for (; t < cnt; ++t) {
+      const int j0 = __shfl_sync(L.mask, j, t, L.G);
+      const float w0 = __shfl_sync(L.mask, w, t, L.G);
+      if (L.active) {
+        float v0[VN];
+        V::load(inb + (size_t)j0 * ldb, v0);
+#pragma unroll
+        for (int k = 0; k < VN; ++k) acc[k] = fmaf(w0, v0[k], acc[k]);
+      }
+    }
+  }
+}
+
+template <int DT>
+__device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int64_t r,
+                                         float *acc) {
+  using V = Vec<DT>;
+  constexpr int VN = V::N;
+  if (!L.active) return;
+  if (a.self_term) {
+    float v[VN];
+    V::load(reinterpret_cast<const char *>(sl.in) + ((size_t)r * sl.ldi + L.col) * V::BYTES, v);
+    const float w = a.colw ? __ldg(a.colw + r) : 1.f;
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = fmaf(w, v[k], acc[k]);
+  }
+  const float sc = a.scalar * (a.rowscale ? __ldg(a.rowscale + r) : 1.f);
+#pragma unroll
+  for (int k = 0; k < VN; ++k) acc[k] *= sc;
+  if (sl.axpy) {
+    float v[VN];
+    // plain load: the axpy block may be the output block (in-place accumulate)
+    V::load_plain(reinterpret_cast<const char *>(sl.axpy) + ((size_t)r * sl.lda + L.col) * V::BYTES, v);
+    const float as = a.ax_scalar * (a.ax_rowscale ? __ldg(a.ax_rowscale + r) : 1.f);
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = fmaf(as, v[k], acc[k]);
+  }
+  for (int t = 0; t < a.lr_rank; ++t) {
+    const int tu = t - a.lr_ones_first;
+    const float u = (tu < 0 || !a.lr_u) ? 1.f : __ldg(a.lr_u + (size_t)r * a.lr_ldu + tu);
+    const float al = a.lr_alpha[t] * u;
+    const float *c = a.lr_c + (size_t)t * a.lr_ldc + sl.col0 + L.col;
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = fmaf(al, __ldg(c + k), acc[k]);
+  }
+  const int valid = min(VN, sl.width - L.col);
+  V::store(reinterpret_cast<char *>(sl.out) + ((size_t)r * sl.ldo + L.col) * V::BYTES, acc, valid);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) spmm_rows_kernel(const __grid_constant__ SpmmArgs a) {
+  constexpr int VN = Vec<DT>::N;
+  const SpmmSlab &sl = a.slab[blockIdx.y];
+  const Lane L = make_lane<DT>(sl);
+  const int rpw = 32 / L.G;
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t base = warp * rpw; base < a.rows; base += nwarp * rpw) {
+    const int64_t r = base + L.sub;
+    if (r >= a.rows) continue;  // uniform within the group
+    const int e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
+    if (e1 - e0 > a.heavy_threshold) continue;
+    float acc[VN];
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = 0.f;
+    gather_range<DT>(a, sl, L, e0, e1, acc);
+    epilogue<DT>(a, sl, L, r, acc);
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant__ SpmmArgs a,
+                                                          const int2 *__restrict__ chunks,
+                                                          const int32_t *__restrict__ chunk_end, int32_t n,
+                                                          float *__restrict__ partial, int64_t pw) {
+  constexpr int VN = Vec<DT>::N;
+  const SpmmSlab &sl = a.slab[blockIdx.y];
+  const Lane L = make_lane<DT>(sl);
+  const int rpw = 32 / L.G;
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t base = warp * rpw; base < n; base += nwarp * rpw) {
+    const int64_t c = base + L.sub;
+    if (c >= n) continue;
+    const int e0 = chunks[c].y, e1 = chunk_end[c];
+    float acc[VN];
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = 0.f;
+    gather_range<DT>(a, sl, L, e0, e1, acc);
+    if (L.active) {
+      float *p = partial + (size_t)c * pw + sl.col0 + L.col;
+#pragma unroll
+      for (int k = 0; k < VN; ++k) p[k] = acc[k];
+    }
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) spmm_finish_kernel(const __grid_constant__ SpmmArgs a,
+                                                          const int4 *__restrict__ hrows, int32_t n,
+                                                          const float *__restrict__ partial, int64_t pw) {
+  constexpr int VN = Vec<DT>::N;
+  const SpmmSlab &sl = a.slab[blockIdx.y];
+  const Lane L = make_lane<DT>(sl);
+  const int rpw = 32 / L.G;
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t base = warp * rpw; base < n; base += nwarp * rpw) {
+    const int64_t h = base + L.sub;
+    if (h >= n) continue;
+    const int4 hr = hrows[h];
+    float acc[VN];
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = 0.f;
+    if (L.active) {
+      for (int c = hr.y; c < hr.y + hr.z; ++c) {
+        const float *p = partial + (size_t)c * pw + sl.col0 + L.col;
+#pragma unroll
+        for (int k = 0; k < VN; ++k) acc[k] += p[k];
+      }
+    }
+    epilogue<DT>(a, sl, L, hr.x, acc);
+  }
+}
+
+int pow2_ceil(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+template <int DT>
+cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s) {
+  const int threads = 256;
+  int gmin = 32;
+  for (int i = 0; i < a.nslabs; ++i) gmin = gmin < a.slab[i].group ? gmin : a.slab[i].group;
+  const int64_t rows_per_block = (threads / 32) * (32 / gmin);
+  int64_t bx = ceil_div(a.rows, rows_per_block);
+  const int64_t cap = (int64_t)kNumSMs * 16;
+  if (bx > cap) bx = cap;
+  if (bx < 1) bx = 1;
+  dim3 grid((unsigned)bx, (unsigned)a.nslabs);
+  spmm_rows_kernel<DT><<<grid, threads, 0, s>>>(a);
+  if (hp.n_chunks > 0) {
+    int64_t cx = ceil_div(hp.n_chunks, rows_per_block);
+    if (cx > cap) cx = cap;
+    spmm_chunks_kernel<DT><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, s>>>(
+        a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
+    int64_t fx = ceil_div(hp.n_rows, rows_per_block);
+    if (fx > cap) fx = cap;
+    spmm_finish_kernel<DT><<<dim3((unsigned)fx, (unsigned)a.nslabs), threads, 0, s>>>(a, hp.rows, hp.n_rows,
+                                                                                      partial, pw);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out) {
+  const int vn = dtype == DT_F32 ? 4 : 8;
+  int max_cols = 32 * vn;
+  if (slab_cols > max_cols) slab_cols = max_cols;
+  if (slab_cols < vn) slab_cols = vn;
+  int n = 0;
+  for (int c0 = 0; c0 < b; c0 += slab_cols) {
+    const int w = (b - c0) < slab_cols ? (b - c0) : slab_cols;
+    SpmmSlab sl{};
+    sl.col0 = c0;
+    sl.width = w;
+    sl.group = pow2_ceil((w + vn - 1) / vn);
+    out[n++] = sl;
+  }
+  return n;
+}
+
+cudaError_t spmm_launch(const SpmmArgs &a, int dtype, const HeavyPlan &hp, float *partial, int64_t pw,
+                        cudaStream_t s) {
+  if (a.rows == 0 || a.nslabs == 0) return cudaSuccess;
+  return dtype == DT_F32 ? launch_dt<DT_F32>(a, hp, partial, pw, s)
+                         : launch_dt<DT_BF16>(a, hp, partial, pw, s);
+}
+
+}  // namespace isvd

@@ -1,0 +1,298 @@
+// Alg. 1 (App. A.2): randomized range finder with power iterations,
+// CholeskyQR orthonormalisation (Alg. 2, right) and Rayleigh-Ritz, as one
+// stream-ordered sequence that is captured once into a CUDA graph.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace isvd {
+namespace {
+
+__global__ void cast_kernel_bf16_f32(const __nv_bfloat16 *in, float *out, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = __bfloat162float(in[i]);
+}
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t count) {
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += (size_t)round_up((int64_t)(sizeof(T) * count), 256);
+    return p;
+  }
+};
+
+struct OrthBufs {
+  float *gram_partial = nullptr;
+  double *W = nullptr, *tmp = nullptr;
+  float *Rinv = nullptr;
+  int32_t *state = nullptr;
+  int32_t n_part = 0;
+};
+
+void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o) {
+  o->n_part = gram_partials(rows);
+  o->gram_partial = c.take<float>((size_t)o->n_part * l * l);
+  o->W = c.take<double>((size_t)l * l);
+  o->tmp = c.take<double>((size_t)l * l);
+  o->Rinv = c.take<float>((size_t)l * l);
+  o->state = c.take<int32_t>(kOrthStateInts);
+}
+
+// CholeskyQR2 with conditional extra passes after a shifted one (passes 3, 4
+// return at once unless a shift happened in the two passes before them).
+isvd_status orth_enqueue(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, double *Racc, const OrthBufs &o,
+                         isvd_info *info, cudaStream_t s) {
+  ISVD_CUDA_TRY(orth_reset_launch(o.state, s));
+  if (Racc) ISVD_CUDA_TRY(racc_init_launch(Racc, l, s));
+  for (int pass = 1; pass <= 4; ++pass) {
+    PassGate g{o.state, pass};
+    ISVD_CUDA_TRY(gram_launch(Q, ldq, dt, rows, l, o.gram_partial, o.n_part, o.W, g, s));
+    ISVD_CUDA_TRY(chol_inv_launch(o.W, l, rows, dt, o.Rinv, l, nullptr, Racc, o.tmp, o.state, info, pass, s));
+    ISVD_CUDA_TRY(gemm_small_launch(Q, ldq, dt, rows, l, o.Rinv, l, l, true, Q, ldq, dt, g, s));
+  }
+  return ISVD_OK;
+}
+
+struct SvdPlan {
+  int32_t k, p, l, ld, iters;
+  uint64_t seed;
+  int prec;
+  float *U, *S, *V;
+  int64_t ldu, ldv;
+  isvd_info *info;
+};
+
+struct SvdBufs {
+  void *qr, *qc;        // blocks in the iteration dtype
+  float *qr32, *qc32;   // FP32 blocks (alias qr/qc in FP32 mode)
+  char *apply_base;
+  OrthBufs orth;
+  double *Racc, *Uo, *So, *Vo, *jwork;
+  float *Lk, *Rk;
+  isvd_info *info;
+};
+
+size_t carve_svd(const isvd_operator *op, const SvdPlan &P, char *base, SvdBufs *b) {
+  Carver c{base};
+  const int64_t rows = op->rows, cols = op->cols;
+  const bool mixed = P.prec == ISVD_PREC_MIXED;
+  const size_t es = mixed ? 2 : 4;
+  b->qr = c.take<char>(es * rows * P.ld);
+  b->qc = c.take<char>(es * cols * P.ld);
+  if (mixed) {
+    b->qr32 = c.take<float>((size_t)rows * P.ld);
+    b->qc32 = c.take<float>((size_t)cols * P.ld);
+  } else {
+    b->qr32 = (float *)b->qr;
+    b->qc32 = (float *)b->qc;
+  }
+  const size_t ab = std::max(apply_scratch_bytes(op, P.l, DT_F32, false), apply_scratch_bytes(op, P.l, DT_F32, true));
+  b->apply_base = c.take<char>(ab);
+  carve_orth(c, std::max(rows, cols), P.l, &b->orth);
+  const int32_t l2 = (P.l + 1) & ~1;
+  b->Racc = c.take<double>((size_t)P.l * P.l);
+  b->Uo = c.take<double>((size_t)P.l * P.l);
+  b->Vo = c.take<double>((size_t)P.l * P.l);
+  b->So = c.take<double>((size_t)P.l);
+  b->jwork = c.take<double>((size_t)l2 * l2);
+  b->Lk = c.take<float>((size_t)P.l * P.k);
+  b->Rk = c.take<float>((size_t)P.l * P.k);
+  b->info = c.take<isvd_info>(1);
+  return c.off;
+}
+
+isvd_status apply_step(isvd_operator *op, const void *in, void *out, int32_t l, int64_t ld, int dt, bool transpose,
+                       const SvdBufs &b, cudaStream_t s) {
+  ApplyScratch sc;
+  apply_scratch_carve(op, l, dt, transpose, b.apply_base, &sc);
+  return apply_impl(op, in, ld, l, out, ld, dt, transpose, sc, s);
+}
+
+isvd_status svd_enqueue(isvd_operator *op, const SvdPlan &P, const SvdBufs &b, cudaStream_t s) {
+  const int64_t rows = op->rows, cols = op->cols;
+  const bool mixed = P.prec == ISVD_PREC_MIXED;
+  const int dt = mixed ? DT_BF16 : DT_F32;
+  isvd_info *info = P.info ? P.info : b.info;
+  ISVD_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(isvd_info), s));
+  // Q ~ N(0,1)^{c x l}
+  ISVD_CUDA_TRY(gaussian_launch(P.seed, cols, P.l, b.qc, P.ld, dt, s));
+  for (int it = 0; it < P.iters; ++it) {
+    ISVD_TRY(apply_step(op, b.qc, b.qr, P.l, P.ld, dt, false, b, s));  // M Q
+    ISVD_TRY(orth_enqueue(b.qr, P.ld, dt, rows, P.l, nullptr, b.orth, info, s));
+    ISVD_TRY(apply_step(op, b.qr, b.qc, P.l, P.ld, dt, true, b, s));   // M^T Q
+    ISVD_TRY(orth_enqueue(b.qc, P.ld, dt, cols, P.l, nullptr, b.orth, info, s));
+  }
+  if (mixed) {
+    // the refinement step and the Rayleigh-Ritz step run in FP32
+    const int64_t n = cols * P.ld;
+    int64_t blocks = std::min<int64_t>(ceil_div(n, 256), kNumSMs * 16);
+    cast_kernel_bf16_f32<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>((const __nv_bfloat16 *)b.qc,
+                                                                                 b.qc32, n);
+    ISVD_CUDA_TRY(cudaGetLastError());
+  }
+  ISVD_TRY(apply_step(op, b.qc32, b.qr32, P.l, P.ld, DT_F32, false, b, s));
+  ISVD_TRY(orth_enqueue(b.qr32, P.ld, DT_F32, rows, P.l, nullptr, b.orth, info, s));
+  // B^T = M^T Q = Qt R  (CholeskyQR of B^T, R accumulated over the passes)
+  ISVD_TRY(apply_step(op, b.qr32, b.qc32, P.l, P.ld, DT_F32, true, b, s));
+  ISVD_TRY(orth_enqueue(b.qc32, P.ld, DT_F32, cols, P.l, b.Racc, b.orth, info, s));
+  // B = R^T Qt^T;  R = Uo S Vo^T  =>  B = Vo S (Qt Uo)^T:  U = Q Vo, V = Qt Uo
+  ISVD_CUDA_TRY(small_svd_launch(b.Racc, P.l, b.Uo, b.So, b.Vo, b.jwork, /*Uk=*/b.Rk, /*Vk=*/b.Lk, /*Sk=*/P.S, P.k,
+                                 info, P.iters, s));
+  ISVD_CUDA_TRY(gemm_small_launch(b.qr32, P.ld, DT_F32, rows, P.l, b.Lk, P.k, P.k, false, P.U, P.ldu, DT_F32,
+                                  PassGate{}, s));
+  ISVD_CUDA_TRY(gemm_small_launch(b.qc32, P.ld, DT_F32, cols, P.l, b.Rk, P.k, P.k, false, P.V, P.ldv, DT_F32,
+                                  PassGate{}, s));
+  return ISVD_OK;
+}
+
+}  // namespace
+}  // namespace isvd
+
+using namespace isvd;
+
+extern "C" {
+
+isvd_status isvd_svd(isvd_operator *op, int32_t k, int32_t oversample, int32_t iters, uint64_t seed,
+                     isvd_precision precision, float *U, int64_t ldu, float *S, float *V, int64_t ldv,
+                     isvd_info *dev_info, void *stream) {
+  if (!op || !U || !S || !V) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (k < 1 || oversample < 0 || iters < 0) return fail(ISVD_ERR_INVALID_ARGUMENT, "need k >= 1, oversample >= 0, iters >= 0");
+  if (precision != ISVD_PREC_FP32 && precision != ISVD_PREC_MIXED)
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown precision");
+  const int64_t l = (int64_t)k + oversample;
+  if (l > ISVD_MAX_BLOCK) return fail(ISVD_ERR_UNSUPPORTED, "block width k + oversample = %lld > %d", (long long)l, ISVD_MAX_BLOCK);
+  if (l > std::min(op->rows, op->cols))
+    return fail(ISVD_ERR_SHAPE, "block width k + oversample = %lld exceeds min(rows, cols)", (long long)l);
+  if (ldu < k || ldv < k) return fail(ISVD_ERR_INVALID_ARGUMENT, "ldu and ldv must be >= k");
+  cudaStream_t s = (cudaStream_t)stream;
+  SvdPlan P{};
+  P.k = k;
+  P.p = oversample;
+  P.l = (int32_t)l;
+  P.ld = (int32_t)round_up(l, 8);
+  P.iters = iters;
+  P.seed = seed;
+  P.prec = precision;
+  P.U = U;
+  P.S = S;
+  P.V = V;
+  P.ldu = ldu;
+  P.ldv = ldv;
+  P.info = dev_info;
+  SvdBufs b{};
+  const size_t bytes = carve_svd(op, P, nullptr, &b);
+  ISVD_TRY(ensure_arena(op, bytes, s));
+  carve_svd(op, P, (char *)op->arena, &b);
+
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  ISVD_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return svd_enqueue(op, P, b, s);  // caller is capturing
+
+  uint64_t key[16] = {(uint64_t)k,      (uint64_t)oversample, (uint64_t)iters,     seed,
+                      (uint64_t)precision, (uint64_t)(uintptr_t)U, (uint64_t)ldu, (uint64_t)(uintptr_t)S,
+                      (uint64_t)(uintptr_t)V, (uint64_t)ldv, (uint64_t)(uintptr_t)dev_info,
+                      (uint64_t)(uintptr_t)op->arena, 0, 0, 0, 0};
+  for (auto &g : op->graphs) {
+    if (memcmp(g.key, key, sizeof key) == 0) {
+      op->last_kernel_nodes = g.kernel_nodes;
+      ISVD_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+      return ISVD_OK;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  ISVD_CUDA_TRY(cudaStreamBeginCapture(op->capture_stream, cudaStreamCaptureModeThreadLocal));
+  const isvd_status st = svd_enqueue(op, P, b, op->capture_stream);
+  const cudaError_t ce = cudaStreamEndCapture(op->capture_stream, &graph);
+  if (st != ISVD_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(ISVD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+  }
+  int64_t kernels = 0;
+  {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+        }
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(ISVD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+  if (op->graphs.size() >= 8) {
+    cudaGraphExecDestroy(op->graphs.front().exec);
+    op->graphs.erase(op->graphs.begin());
+  }
+  isvd_operator::GraphEntry e;
+  memcpy(e.key, key, sizeof key);
+  e.exec = exec;
+  e.kernel_nodes = kernels;
+  op->graphs.push_back(e);
+  op->last_kernel_nodes = kernels;
+  ISVD_CUDA_TRY(cudaGraphLaunch(exec, s));
+  return ISVD_OK;
+}
+
+int64_t isvd_graph_kernel_nodes(const isvd_operator *op) { return op ? op->last_kernel_nodes : -1; }
+
+isvd_status isvd_gaussian(uint64_t seed, int64_t rows, int32_t cols, void *out, int64_t ld, isvd_dtype dtype,
+                          void *stream) {
+  if (!out || rows < 0 || cols < 0 || ld < cols || ld % 8) return fail(ISVD_ERR_INVALID_ARGUMENT, "bad block arguments");
+  if (dtype != ISVD_F32 && dtype != ISVD_BF16) return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown dtype");
+  ISVD_CUDA_TRY(gaussian_launch(seed, rows, cols, out, ld, dtype == ISVD_F32 ? DT_F32 : DT_BF16, (cudaStream_t)stream));
+  return ISVD_OK;
+}
+
+isvd_status isvd_philox_words(uint64_t seed, int64_t rows, uint32_t *out, void *stream) {
+  if (!out || rows < 0) return fail(ISVD_ERR_INVALID_ARGUMENT, "bad arguments");
+  ISVD_CUDA_TRY(philox_words_launch(seed, rows, out, (cudaStream_t)stream));
+  return ISVD_OK;
+}
+
+isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t rows, int32_t l, int64_t ldq, double *R_out,
+                                isvd_info *dev_info, void *stream) {
+  if (!op || !Q) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (l < 1 || l > ISVD_MAX_BLOCK || rows < l) return fail(ISVD_ERR_SHAPE, "need 1 <= l <= min(rows, %d)", ISVD_MAX_BLOCK);
+  if (ldq < l) return fail(ISVD_ERR_INVALID_ARGUMENT, "ldq must be >= l");
+  cudaStream_t s = (cudaStream_t)stream;
+  Carver c{nullptr};
+  OrthBufs o;
+  carve_orth(c, rows, l, &o);
+  c.take<isvd_info>(1);
+  ISVD_TRY(ensure_arena(op, c.off, s));
+  Carver c2{(char *)op->arena};
+  carve_orth(c2, rows, l, &o);
+  isvd_info *own = c2.take<isvd_info>(1);
+  isvd_info *info = dev_info ? dev_info : own;
+  if (!dev_info) ISVD_CUDA_TRY(cudaMemsetAsync(own, 0, sizeof(isvd_info), s));
+  return orth_enqueue(Q, ldq, DT_F32, rows, l, R_out, o, info, s);
+}
+
+isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double *Uo, double *S, double *Vo,
+                           isvd_info *dev_info, void *stream) {
+  if (!op || !A || !Uo || !S || !Vo) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (l < 1 || l > ISVD_MAX_BLOCK) return fail(ISVD_ERR_SHAPE, "need 1 <= l <= %d", ISVD_MAX_BLOCK);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t l2 = (l + 1) & ~1;
+  Carver c{nullptr};
+  c.take<double>((size_t)l2 * l2);
+  ISVD_TRY(ensure_arena(op, c.off, s));
+  ISVD_CUDA_TRY(small_svd_launch(A, l, Uo, S, Vo, (double *)op->arena, nullptr, nullptr, nullptr, 0, dev_info, 0, s));
+  return ISVD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,342 @@
+"""Python binding of libisvd.so (C ABI in ``include/isvd.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  PyTorch provides device memory (tensors and the
+library's workspace, through the caching allocator) and the current stream.
+If the library has not been built, every entry point raises -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+ISVD_OK = 0
+STATUS_NAMES = {
+    0: "OK", 1: "INVALID_ARGUMENT", 2: "INVALID_GRAPH", 3: "SHAPE", 4: "NOT_POSITIVE_DEFINITE",
+    5: "TIMEOUT", 6: "WORKSPACE", 7: "CUDA", 8: "UNSUPPORTED",
+}
+F32, BF16 = 0, 1
+PREC = {"fp32": 0, "mixed": 1}
+NORM = {"row": 0, "sym": 1}
+FORM = {"poly": 0, "concat": 1}
+FLAG_SKIP_SYMMETRY_CHECK = 1
+MAX_BLOCK = 160
+
+
+class IsvdError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {self.name}: {detail}")
+
+
+class _Csr(C.Structure):
+    _fields_ = [("rows", C.c_int64), ("cols", C.c_int64), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("colidx", C.c_void_p), ("values", C.c_void_p)]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("form", C.c_int), ("norm", C.c_int), ("A", _Csr),
+                ("degree", C.c_int32), ("coeffs", C.c_void_p), ("ones_coeff", C.c_double),
+                ("adj_coeff", C.c_double), ("lr_rank", C.c_int32), ("lr_u", C.c_void_p),
+                ("lr_v", C.c_void_p), ("lr_alpha", C.c_void_p), ("d", C.c_int64), ("L", C.c_int32),
+                ("X", _Csr), ("X_dense", C.c_void_p), ("flags", C.c_int32)]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class _Allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:  # the library reports ISVD_ERR_WORKSPACE
+        return None
+
+
+def _torch_free(ptr, stream, ctx):
+    try:
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+_alloc_cb = _ALLOC_FN(_torch_alloc)
+_free_cb = _FREE_FN(_torch_free)
+_TORCH_ALLOCATOR = _Allocator(_alloc_cb, _free_cb, None)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libisvd.so; raise if it is missing (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libisvd.so is not built ({path}); run paper_2111_06312_gb300.build.build()")
+            L = C.CDLL(path)
+            P, I32, I64, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+            L.isvd_create_operator.argtypes = [P, P, P, P]
+            L.isvd_destroy_operator.argtypes = [P]
+            L.isvd_destroy_operator.restype = None
+            L.isvd_operator_shape.argtypes = [P, P, P]
+            L.isvd_apply.argtypes = [P, P, I64, I32, P, I64, C.c_int, P]
+            L.isvd_apply_T.argtypes = [P, P, I64, I32, P, I64, C.c_int, P]
+            L.isvd_svd.argtypes = [P, I32, I32, I32, U64, C.c_int, P, I64, P, P, I64, P, P]
+            L.isvd_gaussian.argtypes = [U64, I64, I32, P, I64, C.c_int, P]
+            L.isvd_philox_words.argtypes = [U64, I64, P, P]
+            L.isvd_orthonormalize.argtypes = [P, P, I64, I32, I64, P, P, P]
+            L.isvd_small_svd.argtypes = [P, P, I32, P, P, P, P, P]
+            L.isvd_graph_kernel_nodes.argtypes = [P]
+            L.isvd_graph_kernel_nodes.restype = C.c_int64
+            L.isvd_status_string.argtypes = [C.c_int]
+            L.isvd_status_string.restype = C.c_char_p
+            L.isvd_last_error.argtypes = []
+            L.isvd_last_error.restype = C.c_char_p
+            for name in ("isvd_create_operator", "isvd_operator_shape", "isvd_apply", "isvd_apply_T", "isvd_svd",
+                         "isvd_gaussian", "isvd_philox_words", "isvd_orthonormalize", "isvd_small_svd"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != ISVD_OK:
+        raise IsvdError(status, where, lib().isvd_last_error().decode(errors="replace"))
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"blocks must be float32 or bfloat16, got {t.dtype}")
+
+
+def _as_block(G: torch.Tensor) -> torch.Tensor:
+    """A 2-D CUDA block whose row stride is a multiple of 8 and whose base is
+    16-byte aligned (copying into a padded buffer when needed)."""
+    if G.dim() == 1:
+        G = G[:, None]
+    if G.dim() != 2 or not G.is_cuda:
+        raise ValueError("blocks must be 2-D CUDA tensors")
+    ok = G.stride(1) == 1 and G.stride(0) % 8 == 0 and G.stride(0) >= G.shape[1] and G.data_ptr() % 16 == 0
+    if ok:
+        return G
+    ld = (G.shape[1] + 7) // 8 * 8
+    buf = torch.zeros((G.shape[0], ld), dtype=G.dtype, device=G.device)
+    buf[:, : G.shape[1]] = G
+    return buf[:, : G.shape[1]]
+
+
+def new_block(rows: int, b: int, dtype=torch.float32, device="cuda") -> torch.Tensor:
+    ld = (b + 7) // 8 * 8
+    return torch.zeros((rows, ld), dtype=dtype, device=device)[:, :b]
+
+
+class Operator:
+    """Implicit design matrix on the GPU (App. A.3: shape, dot, T).
+
+    form='poly':   M = sum_k c_k N^k + ones_coeff 11^T + adj_coeff A + sum_t a_t u_t v_t^T  (Eq. 3)
+    form='concat': M = [X | N X | ... | N^L X]                                              (Eq. 6)
+    norm='row': N = D^-1 A;  norm='sym': N = (D+I)^-1/2 (A+I) (D+I)^-1/2  (Sec. 2).
+    Arrays may be numpy or torch; they are copied to the device and kept
+    alive for the operator's lifetime."""
+
+    def __init__(self, n, rowptr, colidx, *, values=None, form="poly", norm="row", coeffs=(1.0,),
+                 ones_coeff=0.0, adj_coeff=0.0, lowrank=None, X=None, L=0, check_symmetry=True,
+                 device="cuda", use_torch_allocator=True):
+        L_ = lib()
+        dev = torch.device(device)
+        self._keep = []
+
+        def dev_t(a, dtype):
+            t = torch.as_tensor(np.asarray(a) if not torch.is_tensor(a) else a)
+            t = t.to(device=dev, dtype=dtype).contiguous()
+            self._keep.append(t)
+            return t
+
+        self.n = int(n)
+        rp = dev_t(rowptr, torch.int32)
+        ci = dev_t(colidx, torch.int32)
+        vals = dev_t(values, torch.float32) if values is not None else None
+        d = _Desc()
+        d.form = FORM[form]
+        d.norm = NORM[norm]
+        d.A = _Csr(self.n, self.n, int(ci.numel()), rp.data_ptr(), ci.data_ptr(),
+                   vals.data_ptr() if vals is not None else None)
+        coeffs_np = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64).reshape(-1))
+        self._coeffs = coeffs_np
+        d.degree = len(coeffs_np) if form == "poly" else 0
+        d.coeffs = coeffs_np.ctypes.data if form == "poly" else None
+        d.ones_coeff = float(ones_coeff)
+        d.adj_coeff = float(adj_coeff)
+        if lowrank is not None:
+            u, v, alpha = lowrank
+            ut = dev_t(u, torch.float32)
+            vt = dev_t(v, torch.float32)
+            al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(-1))
+            self._alpha = al
+            d.lr_rank = len(al)
+            d.lr_u, d.lr_v, d.lr_alpha = ut.data_ptr(), vt.data_ptr(), al.ctypes.data
+        d.L = int(L)
+        if X is not None:
+            if isinstance(X, (tuple, list)):  # (d, rowptr, colidx, values)
+                dd, xr, xc, xv = X
+                xr_t = dev_t(xr, torch.int32)
+                xc_t = dev_t(xc, torch.int32)
+                xv_t = dev_t(xv, torch.float32)
+                d.d = int(dd)
+                d.X = _Csr(self.n, int(dd), int(xc_t.numel()), xr_t.data_ptr(), xc_t.data_ptr(), xv_t.data_ptr())
+            else:
+                xt = dev_t(X, torch.float32)
+                d.d = int(xt.shape[1])
+                d.X_dense = xt.data_ptr()
+        d.flags = 0 if check_symmetry else FLAG_SKIP_SYMMETRY_CHECK
+        self._desc = d
+        self._handle = C.c_void_p()
+        alloc = C.byref(_TORCH_ALLOCATOR) if use_torch_allocator else None
+        _check(L_.isvd_create_operator(C.byref(d), alloc, _stream(), C.byref(self._handle)), "isvd_create_operator")
+        r, c = C.c_int64(), C.c_int64()
+        _check(L_.isvd_operator_shape(self._handle, C.byref(r), C.byref(c)), "isvd_operator_shape")
+        self.shape = (r.value, c.value)
+        self.device = dev
+
+    # ---- products (App. A.3: dot and T().dot) ----
+    def apply(self, G: torch.Tensor, out: torch.Tensor | None = None, transpose: bool = False) -> torch.Tensor:
+        squeeze = G.dim() == 1
+        G = _as_block(G)
+        rows_in = self.shape[0] if transpose else self.shape[1]
+        rows_out = self.shape[1] if transpose else self.shape[0]
+        if G.shape[0] != rows_in:
+            raise ValueError(f"G has {G.shape[0]} rows, operator needs {rows_in}")
+        b = G.shape[1]
+        if out is None:
+            out = new_block(rows_out, b, G.dtype, G.device)
+        elif out.shape != (rows_out, b) or out.dtype != G.dtype:
+            raise ValueError("out has the wrong shape or dtype")
+        fn = lib().isvd_apply_T if transpose else lib().isvd_apply
+        _check(fn(self._handle, _ptr(G), G.stride(0), b, _ptr(out), out.stride(0), _dtype_code(G), _stream()),
+               "isvd_apply_T" if transpose else "isvd_apply")
+        return out[:, 0] if squeeze else out
+
+    def dot(self, G):
+        return self.apply(G)
+
+    def dot_T(self, G):
+        return self.apply(G, transpose=True)
+
+    # ---- Alg. 1 ----
+    def svd(self, k: int, oversample: int = 10, iters: int = 4, seed: int = 0, precision: str = "fp32",
+            U=None, S=None, V=None, info=None, check: bool = True):
+        r, c = self.shape
+        U = new_block(r, k) if U is None else U
+        V = new_block(c, k) if V is None else V
+        S = torch.empty(k, dtype=torch.float32, device=self.device) if S is None else S
+        info = torch.zeros(4, dtype=torch.int32, device=self.device) if info is None else info
+        _check(lib().isvd_svd(self._handle, k, oversample, iters, C.c_uint64(seed), PREC[precision], _ptr(U),
+                              U.stride(0), _ptr(S), _ptr(V), V.stride(0), _ptr(info), _stream()), "isvd_svd")
+        if check:
+            torch.cuda.current_stream().synchronize()
+            st = int(info[0].item())
+            if st != ISVD_OK:
+                raise IsvdError(st, "isvd_svd (device)", "reported by the GPU")
+        return U, S, V, info
+
+    def graph_kernel_nodes(self) -> int:
+        """Kernel launches in the graph replayed by the last svd() call."""
+        return int(lib().isvd_graph_kernel_nodes(self._handle))
+
+    def close(self):
+        if getattr(self, "_handle", None) and self._handle.value:
+            lib().isvd_destroy_operator(self._handle)
+            self._handle = C.c_void_p()
+        self._keep = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def graph_operator(g, **kw) -> Operator:
+    """Operator on a ``synth.Graph`` (undirected CSR)."""
+    return Operator(g.n, g.rowptr, g.colidx, **kw)
+
+
+def info_dict(info: torch.Tensor) -> dict:
+    v = info.cpu().tolist()
+    return {"status": STATUS_NAMES.get(v[0], v[0]), "chol_shifts": v[1], "cholqr_passes": v[2], "iters_done": v[3]}
+
+
+def gaussian(seed: int, rows: int, cols: int, dtype=torch.float32, device="cuda") -> torch.Tensor:
+    """Alg. 1's N(0,1) start block from Philox4x32-10 (counter-based)."""
+    out = new_block(rows, cols, dtype, device)
+    code = F32 if dtype == torch.float32 else BF16
+    _check(lib().isvd_gaussian(C.c_uint64(seed), rows, cols, _ptr(out), out.stride(0), code, _stream()),
+           "isvd_gaussian")
+    return out
+
+
+def philox_words(seed: int, rows: int, device="cuda") -> torch.Tensor:
+    out = torch.zeros((rows, 16), dtype=torch.int32, device=device)
+    _check(lib().isvd_philox_words(C.c_uint64(seed), rows, _ptr(out), _stream()), "isvd_philox_words")
+    return out
+
+
+def orthonormalize(op: Operator, Q: torch.Tensor, want_r: bool = True):
+    """CholeskyQR2 (Alg. 2) in place on an FP32 block; returns (Q, R, info)."""
+    if Q.dtype != torch.float32:
+        raise TypeError("orthonormalize takes an FP32 block")
+    Q = _as_block(Q)
+    rows, l = Q.shape
+    R = torch.zeros((l, l), dtype=torch.float64, device=Q.device) if want_r else None
+    info = torch.zeros(4, dtype=torch.int32, device=Q.device)
+    _check(lib().isvd_orthonormalize(op._handle, _ptr(Q), rows, l, Q.stride(0), _ptr(R), _ptr(info), _stream()),
+           "isvd_orthonormalize")
+    return Q, R, info
+
+
+def small_svd(op: Operator, A: torch.Tensor):
+    """SVD of a small square FP64 matrix (one-sided Jacobi): A = U diag(S) V^T."""
+    A = A.to(torch.float64).contiguous()
+    l = A.shape[0]
+    U = torch.zeros((l, l), dtype=torch.float64, device=A.device)
+    V = torch.zeros((l, l), dtype=torch.float64, device=A.device)
+    S = torch.zeros(l, dtype=torch.float64, device=A.device)
+    _check(lib().isvd_small_svd(op._handle, _ptr(A), l, _ptr(U), _ptr(S), _ptr(V), None, _stream()),
+           "isvd_small_svd")
+    return U, S, V

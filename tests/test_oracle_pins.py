@@ -404,3 +404,29 @@ def test_pins_reject_planted_mistakes():
     one = np.ones(gi.n)
     wrong = oracle.graph_operator(gi, norm="sym", coeffs=C5).apply(one)
     assert not np.allclose(wrong, one)
+
+
+def test_lowrank_term_closed_form():
+    # u v^T with v orthogonal to the all-ones vector and u = 1: on C_n the
+    # matrix p(T) + a 1 v^T has p(T)'s spectrum deformed only in the 1
+    # direction; check against the definition through its action instead:
+    # (a u v^T) G = a u (v^T G) -- and the transpose swaps u and v.
+    g = _irregular(100, 400, 31)
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal((g.n, 2))
+    v = rng.standard_normal((g.n, 2))
+    al = np.array([0.3, -1.2])
+    base = oracle.graph_operator(g, coeffs=C5)
+    op = oracle.graph_operator(g, coeffs=C5, lowrank=(u, v, al))
+    G = rng.standard_normal((g.n, 3))
+    want = base.apply(G) + (u * al) @ (v.T @ G)
+    assert np.allclose(op.apply(G), want, rtol=1e-13, atol=1e-12)
+    want_t = base.apply(G, transpose=True) + (v * al) @ (u.T @ G)
+    assert np.allclose(op.apply(G, transpose=True), want_t, rtol=1e-13, atol=1e-12)
+    M = op.explicit()
+    assert np.allclose(M @ G, want, rtol=1e-12, atol=1e-11)
+    # rank-one all-ones coefficient equals the low-rank form with u = v = 1
+    one = np.ones((g.n, 1))
+    a1 = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM).apply(G)
+    a2 = oracle.graph_operator(g, coeffs=C5, lowrank=(one, one, [-LAM])).apply(G)
+    assert np.allclose(a1, a2, rtol=1e-13, atol=1e-12)
