@@ -53,18 +53,7 @@ WORKLOADS = {
 def load_graph(name):
     from paper_2111_06312_gb300 import synth
 
-    cache = os.path.join(tempfile.gettempdir(), f"isvd_synth_{name}_v1.npz")
-    if os.path.exists(cache):
-        z = np.load(cache)
-        return synth.Graph(int(z["n"]), z["rowptr"], z["colidx"])
-    g = synth.workload_ne_large() if name == "ne_large" else synth.workload_ne_small()
-    try:
-        tmp = cache + f".{os.getpid()}.npz"
-        np.savez(tmp, n=g.n, rowptr=g.rowptr, colidx=g.colidx)
-        os.replace(tmp, cache)
-    except OSError:
-        pass
-    return g
+    return synth.cached(name)
 
 
 def measured_peaks():

@@ -207,6 +207,29 @@ ISVD_API isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t ro
 ISVD_API isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double *Uo, double *S,
                            double *Vo, isvd_info *dev_info, void *stream);
 
+/* Launch shape of the sparse products (no counterpart in the paper, which ran
+ * library kernels).  slab_cols_*: columns of the dense block processed per
+ * pass over the CSR (the gathered slab of the block should stay L2-resident);
+ * heavy_threshold: rows with more nonzeros are split into chunks of
+ * heavy_chunk nonzeros whose partial sums are combined in order. */
+typedef struct {
+  int32_t slab_cols_f32;   /* 4..128, multiple of 4 */
+  int32_t slab_cols_bf16;  /* 8..256, multiple of 8 */
+  int32_t heavy_threshold; /* >= 32 */
+  int32_t heavy_chunk;     /* >= 32 */
+  int32_t flags;           /* ISVD_TUNE_* */
+} isvd_tuning;
+
+enum {
+  ISVD_TUNE_CACHE_HINTS = 1  /* L2 eviction priorities: keep gathered rows, stream the rest */
+};
+
+/* Read / replace the operator's launch shapes.  isvd_set_tuning rebuilds the
+ * row split lists (synchronises `stream`) and drops captured graphs.
+ * Errors: INVALID_ARGUMENT (out-of-range field), WORKSPACE, CUDA. */
+ISVD_API isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out);
+ISVD_API isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *stream);
+
 /* Number of kernel launches in the CUDA graph that the last isvd_svd call on
  * this operator replayed (-1 if none yet).  Introspection for benchmarks. */
 ISVD_API int64_t isvd_graph_kernel_nodes(const isvd_operator *op);

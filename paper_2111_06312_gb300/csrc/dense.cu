@@ -53,11 +53,18 @@ __global__ void gaussian_kernel(uint32_t k0, uint32_t k1, int64_t rows, int32_t 
       const uint32_t w[4] = {c0, c1, c2, c3};
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const float ua = fmaf((float)w[2 * h], 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-        const float ub = fmaf((float)w[2 * h + 1], 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-        const float rho = sqrtf(-2.0f * logf(ua));
+        // u = (w + 1/2) 2^-32.  Near u = 1 the float form of u loses the
+        // distance 1 - u = (~w + 1/2) 2^-32, so ln u is taken as log1p of that
+        // distance and 2u as the equivalent angle 2u - 2 (period 2 of sincospi).
+        const uint32_t wa = w[2 * h], wb = w[2 * h + 1];
+        const float lnu = (wa < 0x80000000u)
+                              ? logf(fmaf((float)wa, 2.3283064365386963e-10f, 1.1641532182693481e-10f))
+                              : log1pf(-fmaf((float)(~wa), 2.3283064365386963e-10f, 1.1641532182693481e-10f));
+        const float t = (wb < 0x80000000u) ? fmaf((float)wb, 4.6566128730773926e-10f, 2.3283064365386963e-10f)
+                                           : -fmaf((float)(~wb), 4.6566128730773926e-10f, 2.3283064365386963e-10f);
+        const float rho = sqrtf(-2.0f * lnu);
         float sn, cs;
-        sincospif(2.0f * ub, &sn, &cs);
+        sincospif(t, &sn, &cs);
         z[2 * h] = rho * cs;
         z[2 * h + 1] = rho * sn;
       }

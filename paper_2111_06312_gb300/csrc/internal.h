@@ -78,6 +78,7 @@ struct SpmmArgs {
   int64_t lr_ldc;
   float lr_alpha[ISVD_MAX_LOWRANK];
   int32_t heavy_threshold;  // rows with more nonzeros go through the split path
+  int32_t cache_hints;      // L2 eviction-priority hints on gathers and streams
   int32_t nslabs;
   SpmmSlab slab[kMaxSlabs];
 };
@@ -90,8 +91,8 @@ struct HeavyPlan {
   int2 *chunks = nullptr;   // (row, first nnz) per chunk; chunk end = next chunk or row end
   int32_t *chunk_end = nullptr;
   int4 *rows = nullptr;     // (row, first chunk, chunk count, 0)
-  int32_t threshold = 1 << 30;
-  int32_t chunk = 256;
+  int32_t threshold = 128;
+  int32_t chunk = 128;
 };
 
 // Launch the SpMM described by `a` (dtype of in/axpy/out), splitting heavy
@@ -176,7 +177,8 @@ struct isvd_operator {
   void *arena = nullptr;
   size_t arena_bytes = 0;
   cudaStream_t capture_stream = nullptr;
-  int32_t slab_cols_f32 = 32, slab_cols_bf16 = 64;
+  int32_t slab_cols_f32 = 128, slab_cols_bf16 = 256;
+  int32_t cache_hints = 1;
   struct GraphEntry {
     uint64_t key[16];
     cudaGraphExec_t exec;
@@ -188,6 +190,7 @@ struct isvd_operator {
 
 namespace isvd {
 void *op_alloc(isvd_operator *op, size_t bytes, cudaStream_t s);
+void free_heavy(isvd_operator *op, HeavyPlan *hp, cudaStream_t s);
 void op_free(isvd_operator *op, void *p, cudaStream_t s);
 isvd_status ensure_arena(isvd_operator *op, size_t bytes, cudaStream_t s);
 

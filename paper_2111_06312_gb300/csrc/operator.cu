@@ -203,6 +203,20 @@ void *owned_alloc(isvd_operator *op, size_t bytes, cudaStream_t s) {
   return p;
 }
 
+}  // namespace
+
+void free_heavy(isvd_operator *op, HeavyPlan *hp, cudaStream_t s) {
+  op_free(op, hp->chunks, s);
+  op_free(op, hp->chunk_end, s);
+  op_free(op, hp->rows, s);
+  hp->chunks = nullptr;
+  hp->chunk_end = nullptr;
+  hp->rows = nullptr;
+  hp->n_rows = hp->n_chunks = 0;
+}
+
+namespace {
+
 // Build the hub-row split plan from a host copy of rowptr.
 isvd_status build_heavy(isvd_operator *op, const int32_t *rowptr_dev, int64_t rows, HeavyPlan *hp,
                         cudaStream_t s) {
@@ -222,12 +236,13 @@ isvd_status build_heavy(isvd_operator *op, const int32_t *rowptr_dev, int64_t ro
     }
     hrows.push_back(make_int4((int)i, first, (int)chunks.size() - first, 0));
   }
+  free_heavy(op, hp, s);
   hp->n_rows = (int32_t)hrows.size();
   hp->n_chunks = (int32_t)chunks.size();
   if (hp->n_chunks == 0) return ISVD_OK;
-  hp->chunks = (int2 *)owned_alloc(op, sizeof(int2) * chunks.size(), s);
-  hp->chunk_end = (int32_t *)owned_alloc(op, sizeof(int32_t) * ends.size(), s);
-  hp->rows = (int4 *)owned_alloc(op, sizeof(int4) * hrows.size(), s);
+  hp->chunks = (int2 *)op_alloc(op, sizeof(int2) * chunks.size(), s);
+  hp->chunk_end = (int32_t *)op_alloc(op, sizeof(int32_t) * ends.size(), s);
+  hp->rows = (int4 *)op_alloc(op, sizeof(int4) * hrows.size(), s);
   if (!hp->chunks || !hp->chunk_end || !hp->rows) return fail(ISVD_ERR_WORKSPACE, "heavy-row plan allocation failed");
   ISVD_CUDA_TRY(cudaMemcpyAsync(hp->chunks, chunks.data(), sizeof(int2) * chunks.size(), cudaMemcpyHostToDevice, s));
   ISVD_CUDA_TRY(cudaMemcpyAsync(hp->chunk_end, ends.data(), sizeof(int32_t) * ends.size(), cudaMemcpyHostToDevice, s));
@@ -458,6 +473,7 @@ SpmmArgs base_args_A(const isvd_operator *op) {
   a.scalar = 1.f;
   a.ax_scalar = 1.f;
   a.heavy_threshold = op->heavy_A.n_chunks > 0 ? op->heavy_A.threshold : INT_MAX;
+  a.cache_hints = op->cache_hints;
   return a;
 }
 
@@ -647,6 +663,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
     ax.scalar = 1.f;
     ax.ax_scalar = 1.f;
     ax.heavy_threshold = op->heavy_X.n_chunks > 0 ? op->heavy_X.threshold : INT_MAX;
+    ax.cache_hints = op->cache_hints;
     for (int l = 0; l <= L; ++l) {
       const char *gin = (const char *)G + (size_t)l * d.d * ldg * es;
       if (L == 0) add_slabs(ax, dtype, b, scols, 0, gin, ldg, out, ldo, nullptr, 0);
@@ -705,6 +722,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
   at.scalar = 1.f;
   at.ax_scalar = 1.f;
   at.heavy_threshold = op->heavy_XT.n_chunks > 0 ? op->heavy_XT.threshold : INT_MAX;
+  at.cache_hints = op->cache_hints;
   for (int l = 0; l <= L; ++l) {
     const void *in = l == 0 ? G : (const void *)seg(l);
     const int64_t ldi = l == 0 ? ldg : ldp;
@@ -783,6 +801,9 @@ void isvd_destroy_operator(isvd_operator *op) {
   cudaStream_t s = nullptr;
   op_free(op, op->arena, s);
   for (void *p : op->owned) op_free(op, p, s);
+  free_heavy(op, &op->heavy_A, s);
+  free_heavy(op, &op->heavy_X, s);
+  free_heavy(op, &op->heavy_XT, s);
   if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
   cudaStreamSynchronize(s);
   delete op;
@@ -819,6 +840,41 @@ isvd_status isvd_apply(isvd_operator *op, const void *G, int64_t ldg, int32_t b,
 isvd_status isvd_apply_T(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
                          isvd_dtype dtype, void *stream) {
   return apply_entry(op, G, ldg, b, out, ldo, dtype, stream, true);
+}
+
+isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
+  if (!op || !out) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  out->slab_cols_f32 = op->slab_cols_f32;
+  out->slab_cols_bf16 = op->slab_cols_bf16;
+  out->heavy_threshold = op->heavy_A.threshold;
+  out->heavy_chunk = op->heavy_A.chunk;
+  out->flags = op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0;
+  return ISVD_OK;
+}
+
+isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *stream) {
+  if (!op || !t) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (t->slab_cols_f32 < 4 || t->slab_cols_f32 > 128 || t->slab_cols_f32 % 4 || t->slab_cols_bf16 < 8 ||
+      t->slab_cols_bf16 > 256 || t->slab_cols_bf16 % 8 || t->heavy_threshold < 32 || t->heavy_chunk < 32)
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "tuning field out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  for (auto &g : op->graphs) cudaGraphExecDestroy(g.exec);
+  op->graphs.clear();
+  op->slab_cols_f32 = t->slab_cols_f32;
+  op->slab_cols_bf16 = t->slab_cols_bf16;
+  op->cache_hints = (t->flags & ISVD_TUNE_CACHE_HINTS) ? 1 : 0;
+  HeavyPlan *plans[3] = {&op->heavy_A, &op->heavy_X, &op->heavy_XT};
+  for (HeavyPlan *hp : plans) {
+    hp->threshold = t->heavy_threshold;
+    hp->chunk = t->heavy_chunk;
+  }
+  ISVD_TRY(build_heavy(op, op->desc.A.rowptr, op->n, &op->heavy_A, s));
+  if (op->desc.form == ISVD_FORM_CONCAT) {
+    ISVD_TRY(build_heavy(op, op->x_rowptr, op->n, &op->heavy_X, s));
+    ISVD_TRY(build_heavy(op, op->xt_rowptr, op->desc.d, &op->heavy_XT, s));
+  }
+  return ISVD_OK;
 }
 
 }  // extern "C"

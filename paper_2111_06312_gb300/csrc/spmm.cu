@@ -22,6 +22,52 @@
 namespace isvd {
 namespace {
 
+// L2 eviction-priority policies (PTX createpolicy): gathered rows of the dense
+// block are kept (evict_last); the CSR stream and the output block pass
+// through (evict_first), so that the slab of the block stays in L2.
+__device__ __forceinline__ uint64_t policy_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_stream() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+template <bool HINT>
+__device__ __forceinline__ uint4 ld16(const void *p, uint64_t pol) {
+  uint4 v;
+  if (HINT)
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+  else
+    v = __ldg(reinterpret_cast<const uint4 *>(p));
+  return v;
+}
+
+template <bool HINT>
+__device__ __forceinline__ void st16(void *p, uint4 v, uint64_t pol) {
+  if (HINT)
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+  else
+    *reinterpret_cast<uint4 *>(p) = v;
+}
+
+template <bool HINT>
+__device__ __forceinline__ int32_t ld_idx(const int32_t *p, uint64_t pol) {
+  int32_t v;
+  if (HINT)
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  else
+    v = __ldg(p);
+  return v;
+}
+
 template <int DT>
 struct Vec;
 
@@ -29,21 +75,18 @@ template <>
 struct Vec<DT_F32> {
   static constexpr int N = 4;
   static constexpr int BYTES = 4;
-  __device__ __forceinline__ static void load(const void *p, float *v) {
-    const float4 x = __ldg(reinterpret_cast<const float4 *>(p));
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  __device__ __forceinline__ static void unpack(const uint4 x, float *v) {
+    v[0] = __uint_as_float(x.x);
+    v[1] = __uint_as_float(x.y);
+    v[2] = __uint_as_float(x.z);
+    v[3] = __uint_as_float(x.w);
   }
-  __device__ __forceinline__ static void load_plain(const void *p, float *v) {
-    const float4 x = *reinterpret_cast<const float4 *>(p);
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  __device__ __forceinline__ static uint4 pack(const float *v) {
+    return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
   }
-  __device__ __forceinline__ static void store(void *p, const float *v, int valid) {
+  __device__ __forceinline__ static void store_partial(void *p, const float *v, int valid) {
     float *q = reinterpret_cast<float *>(p);
-    if (valid >= 4) {
-      *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
-      for (int k = 0; k < valid; ++k) q[k] = v[k];
-    }
+    for (int k = 0; k < valid; ++k) q[k] = v[k];
   }
 };
 
@@ -60,25 +103,32 @@ struct Vec<DT_BF16> {
       v[2 * k + 1] = f.y;
     }
   }
-  __device__ __forceinline__ static void load(const void *p, float *v) {
-    unpack(__ldg(reinterpret_cast<const uint4 *>(p)), v);
-  }
-  __device__ __forceinline__ static void load_plain(const void *p, float *v) {
-    unpack(*reinterpret_cast<const uint4 *>(p), v);
-  }
-  __device__ __forceinline__ static void store(void *p, const float *v, int valid) {
-    if (valid >= 8) {
-      uint4 x;
-      __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&x);
+  __device__ __forceinline__ static uint4 pack(const float *v) {
+    uint4 x;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&x);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-      *reinterpret_cast<uint4 *>(p) = x;
-    } else {
-      __nv_bfloat16 *q = reinterpret_cast<__nv_bfloat16 *>(p);
-      for (int k = 0; k < valid; ++k) q[k] = __float2bfloat16_rn(v[k]);
-    }
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    return x;
+  }
+  __device__ __forceinline__ static void store_partial(void *p, const float *v, int valid) {
+    __nv_bfloat16 *q = reinterpret_cast<__nv_bfloat16 *>(p);
+    for (int k = 0; k < valid; ++k) q[k] = __float2bfloat16_rn(v[k]);
   }
 };
+
+struct Policies {
+  uint64_t keep, stream;
+};
+
+template <bool HINT>
+__device__ __forceinline__ Policies make_policies() {
+  Policies p{0, 0};
+  if (HINT) {
+    p.keep = policy_keep();
+    p.stream = policy_stream();
+  }
+  return p;
+}
 
 struct Lane {
   int G;          // lanes per row
@@ -103,9 +153,9 @@ __device__ __forceinline__ Lane make_lane(const SpmmSlab &sl) {
 }
 
 // acc += sum over nonzeros e in [e0, e1) of a_e w_j in_j (slab columns of this lane)
-template <int DT>
+template <int DT, bool HINT>
 __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int e0,
-                                             int e1, float *acc) {
+                                             int e1, const Policies &pol, float *acc) {
   using V = Vec<DT>;
   constexpr int VN = V::N;
   const char *inb = reinterpret_cast<const char *>(sl.in) + (size_t)L.col * V::BYTES;
@@ -115,7 +165,7 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
     int j = 0;
     float w = 0.f;
     if (me < e1) {
-      j = __ldg(a.colidx + me);
+      j = ld_idx<HINT>(a.colidx + me, pol.stream);
       w = a.values ? __ldg(a.values + me) : 1.f;
       if (a.colw) w *= __ldg(a.colw + j);
     }
@@ -132,10 +182,10 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
       const float w3 = __shfl_sync(L.mask, w, t + 3, L.G);
       if (L.active) {
         float v0[VN], v1[VN], v2[VN], v3[VN];
-        V::load(inb + (size_t)j0 * ldb, v0);
-        V::load(inb + (size_t)j1 * ldb, v1);
-        V::load(inb + (size_t)j2 * ldb, v2);
-        V::load(inb + (size_t)j3 * ldb, v3);
+        V::unpack(ld16<HINT>(inb + (size_t)j0 * ldb, pol.keep), v0);
+        V::unpack(ld16<HINT>(inb + (size_t)j1 * ldb, pol.keep), v1);
+        V::unpack(ld16<HINT>(inb + (size_t)j2 * ldb, pol.keep), v2);
+        V::unpack(ld16<HINT>(inb + (size_t)j3 * ldb, pol.keep), v3);
 #pragma unroll
         for (int k = 0; k < VN; ++k) {
           acc[k] = fmaf(w0, v0[k], acc[k]);
@@ -150,7 +200,7 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
       const float w0 = __shfl_sync(L.mask, w, t, L.G);
       if (L.active) {
         float v0[VN];
-        V::load(inb + (size_t)j0 * ldb, v0);
+        V::unpack(ld16<HINT>(inb + (size_t)j0 * ldb, pol.keep), v0);
 #pragma unroll
         for (int k = 0; k < VN; ++k) acc[k] = fmaf(w0, v0[k], acc[k]);
       }
@@ -158,15 +208,15 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
   }
 }
 
-template <int DT>
+template <int DT, bool HINT>
 __device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int64_t r,
-                                         float *acc) {
+                                         const Policies &pol, float *acc) {
   using V = Vec<DT>;
   constexpr int VN = V::N;
   if (!L.active) return;
   if (a.self_term) {
     float v[VN];
-    V::load(reinterpret_cast<const char *>(sl.in) + ((size_t)r * sl.ldi + L.col) * V::BYTES, v);
+    V::unpack(ld16<false>(reinterpret_cast<const char *>(sl.in) + ((size_t)r * sl.ldi + L.col) * V::BYTES, 0), v);
     const float w = a.colw ? __ldg(a.colw + r) : 1.f;
 #pragma unroll
     for (int k = 0; k < VN; ++k) acc[k] = fmaf(w, v[k], acc[k]);
@@ -177,7 +227,9 @@ __device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, 
   if (sl.axpy) {
     float v[VN];
     // plain load: the axpy block may be the output block (in-place accumulate)
-    V::load_plain(reinterpret_cast<const char *>(sl.axpy) + ((size_t)r * sl.lda + L.col) * V::BYTES, v);
+    V::unpack(*reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(sl.axpy) +
+                                               ((size_t)r * sl.lda + L.col) * V::BYTES),
+              v);
     const float as = a.ax_scalar * (a.ax_rowscale ? __ldg(a.ax_rowscale + r) : 1.f);
 #pragma unroll
     for (int k = 0; k < VN; ++k) acc[k] = fmaf(as, v[k], acc[k]);
@@ -191,31 +243,34 @@ __device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, 
     for (int k = 0; k < VN; ++k) acc[k] = fmaf(al, __ldg(c + k), acc[k]);
   }
   const int valid = min(VN, sl.width - L.col);
-  V::store(reinterpret_cast<char *>(sl.out) + ((size_t)r * sl.ldo + L.col) * V::BYTES, acc, valid);
+  char *o = reinterpret_cast<char *>(sl.out) + ((size_t)r * sl.ldo + L.col) * V::BYTES;
+  if (valid >= VN) st16<HINT>(o, V::pack(acc), pol.stream);
+  else V::store_partial(o, acc, valid);
 }
 
-template <int DT>
+template <int DT, bool HINT>
 __global__ void __launch_bounds__(256) spmm_rows_kernel(const __grid_constant__ SpmmArgs a) {
   constexpr int VN = Vec<DT>::N;
   const SpmmSlab &sl = a.slab[blockIdx.y];
   const Lane L = make_lane<DT>(sl);
+  const Policies pol = make_policies<HINT>();
   const int rpw = 32 / L.G;
   const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t base = warp * rpw; base < a.rows; base += nwarp * rpw) {
     const int64_t r = base + L.sub;
     if (r >= a.rows) continue;  // uniform within the group
-    const int e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
+    const int e0 = ld_idx<HINT>(a.rowptr + r, pol.stream), e1 = ld_idx<HINT>(a.rowptr + r + 1, pol.stream);
     if (e1 - e0 > a.heavy_threshold) continue;
     float acc[VN];
 #pragma unroll
     for (int k = 0; k < VN; ++k) acc[k] = 0.f;
-    gather_range<DT>(a, sl, L, e0, e1, acc);
-    epilogue<DT>(a, sl, L, r, acc);
+    gather_range<DT, HINT>(a, sl, L, e0, e1, pol, acc);
+    epilogue<DT, HINT>(a, sl, L, r, pol, acc);
   }
 }
 
-template <int DT>
+template <int DT, bool HINT>
 __global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant__ SpmmArgs a,
                                                           const int2 *__restrict__ chunks,
                                                           const int32_t *__restrict__ chunk_end, int32_t n,
@@ -223,6 +278,7 @@ __global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant_
   constexpr int VN = Vec<DT>::N;
   const SpmmSlab &sl = a.slab[blockIdx.y];
   const Lane L = make_lane<DT>(sl);
+  const Policies pol = make_policies<HINT>();
   const int rpw = 32 / L.G;
   const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -233,7 +289,7 @@ __global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant_
     float acc[VN];
 #pragma unroll
     for (int k = 0; k < VN; ++k) acc[k] = 0.f;
-    gather_range<DT>(a, sl, L, e0, e1, acc);
+    gather_range<DT, HINT>(a, sl, L, e0, e1, pol, acc);
     if (L.active) {
       float *p = partial + (size_t)c * pw + sl.col0 + L.col;
 #pragma unroll
@@ -242,13 +298,14 @@ __global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant_
   }
 }
 
-template <int DT>
+template <int DT, bool HINT>
 __global__ void __launch_bounds__(256) spmm_finish_kernel(const __grid_constant__ SpmmArgs a,
                                                           const int4 *__restrict__ hrows, int32_t n,
                                                           const float *__restrict__ partial, int64_t pw) {
   constexpr int VN = Vec<DT>::N;
   const SpmmSlab &sl = a.slab[blockIdx.y];
   const Lane L = make_lane<DT>(sl);
+  const Policies pol = make_policies<HINT>();
   const int rpw = 32 / L.G;
   const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -266,7 +323,7 @@ __global__ void __launch_bounds__(256) spmm_finish_kernel(const __grid_constant_
         for (int k = 0; k < VN; ++k) acc[k] += p[k];
       }
     }
-    epilogue<DT>(a, sl, L, hr.x, acc);
+    epilogue<DT, HINT>(a, sl, L, hr.x, pol, acc);
   }
 }
 
@@ -276,7 +333,7 @@ int pow2_ceil(int x) {
   return p;
 }
 
-template <int DT>
+template <int DT, bool HINT>
 cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s) {
   const int threads = 256;
   int gmin = 32;
@@ -287,15 +344,15 @@ cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, in
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
   dim3 grid((unsigned)bx, (unsigned)a.nslabs);
-  spmm_rows_kernel<DT><<<grid, threads, 0, s>>>(a);
+  spmm_rows_kernel<DT, HINT><<<grid, threads, 0, s>>>(a);
   if (hp.n_chunks > 0) {
     int64_t cx = ceil_div(hp.n_chunks, rows_per_block);
     if (cx > cap) cx = cap;
-    spmm_chunks_kernel<DT><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, s>>>(
+    spmm_chunks_kernel<DT, HINT><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, s>>>(
         a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
     int64_t fx = ceil_div(hp.n_rows, rows_per_block);
     if (fx > cap) fx = cap;
-    spmm_finish_kernel<DT><<<dim3((unsigned)fx, (unsigned)a.nslabs), threads, 0, s>>>(a, hp.rows, hp.n_rows,
+    spmm_finish_kernel<DT, HINT><<<dim3((unsigned)fx, (unsigned)a.nslabs), threads, 0, s>>>(a, hp.rows, hp.n_rows,
                                                                                       partial, pw);
   }
   return cudaGetLastError();
@@ -323,8 +380,11 @@ int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out) {
 cudaError_t spmm_launch(const SpmmArgs &a, int dtype, const HeavyPlan &hp, float *partial, int64_t pw,
                         cudaStream_t s) {
   if (a.rows == 0 || a.nslabs == 0) return cudaSuccess;
-  return dtype == DT_F32 ? launch_dt<DT_F32>(a, hp, partial, pw, s)
-                         : launch_dt<DT_BF16>(a, hp, partial, pw, s);
+  if (a.cache_hints)
+    return dtype == DT_F32 ? launch_dt<DT_F32, true>(a, hp, partial, pw, s)
+                           : launch_dt<DT_BF16, true>(a, hp, partial, pw, s);
+  return dtype == DT_F32 ? launch_dt<DT_F32, false>(a, hp, partial, pw, s)
+                         : launch_dt<DT_BF16, false>(a, hp, partial, pw, s);
 }
 
 }  // namespace isvd

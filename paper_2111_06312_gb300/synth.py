@@ -236,6 +236,26 @@ def workload_ne_large(n: int = 1_000_000, m: int = 20_000_000, max_degree: float
     return chung_lu(n, m, BASE_SEED + 2, max_degree=max_degree)
 
 
+def cached(name: str) -> Graph:
+    """``workload_<name>`` graph, cached as .npz in the temp directory (the
+    10^6-node graph takes ~20 s to draw)."""
+    import os
+    import tempfile
+
+    path = os.path.join(tempfile.gettempdir(), f"isvd_synth_{name}_v1.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return Graph(int(z["n"]), z["rowptr"], z["colidx"])
+    g = {"ne_large": workload_ne_large, "ne_small": workload_ne_small}[name]()
+    try:
+        tmp = path + f".{os.getpid()}.npz"
+        np.savez(tmp, n=g.n, rowptr=g.rowptr, colidx=g.colidx)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return g
+
+
 def workload_batched(count: int = 256, n_lo: int = 500, n_hi: int = 50_000, mean_degree: float = 8.0):
     """Many uneven graphs: n ~ U[n_lo, n_hi]; even index Erdos-Renyi, odd index
     Chung-Lu; rank drawn from {16, 32, 64}."""

@@ -213,7 +213,8 @@ def gapped_prefix(S_ritz, k, rel_gap=1e-3):
     """Largest j <= k with (s_j - s_{j+1}) >= rel_gap * s_j (1-based)."""
     best = 0
     for j in range(1, k + 1):
-        if S_ritz[j - 1] - S_ritz[j] >= rel_gap * S_ritz[j - 1]:
+        # j == len(S_ritz): the whole block is the subspace, no gap to check
+        if j == len(S_ritz) or S_ritz[j - 1] - S_ritz[j] >= rel_gap * S_ritz[j - 1]:
             best = j
     return best
 
