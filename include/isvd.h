@@ -200,6 +200,27 @@ ISVD_API isvd_status isvd_philox_words(uint64_t seed, int64_t rows, uint32_t *ou
 ISVD_API isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t rows, int32_t l, int64_t ldq,
                                 double *R_out, isvd_info *dev_info, void *stream);
 
+/* isvd_orthonormalize without any allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they need it (code running inside another framework's allocator or
+ * memory-pool callback, latency-bound services that forbid cudaMalloc on the
+ * hot path because it can synchronise the device).  Its scratch is one
+ * file-scope device array of about 5 MB that every GPU which loads the
+ * library holds until the process exits.
+ *   - Same arguments and results as isvd_orthonormalize (no operator), but
+ *     l <= ISVD_NOALLOC_MAX_BLOCK (64); larger l returns ISVD_ERR_UNSUPPORTED.
+ *   - The first call on a device sets up that device (looks up the array's
+ *     device address and kernel attributes): make it before any stream
+ *     capture on that device.
+ *   - Every call shares the one array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and corrupt each other's results.
+ *     Order them on one stream.  dev_info NULL uses a slot in the array that
+ *     is cleared at the start of each call.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define ISVD_NOALLOC_MAX_BLOCK 64
+ISVD_API isvd_status isvd_orthonormalize_noalloc(float *Q, int64_t rows, int32_t l, int64_t ldq, double *R_out,
+                                                 isvd_info *dev_info, void *stream);
+
 /* SVD of a small square upper-triangular-or-dense FP64 matrix by one-sided
  * Jacobi on its transpose (the Rayleigh-Ritz step of Alg. 1, done as
  * SVD(R^T) after a QR of B^T).  A (l x l, row-major, DEVICE) = Uo diag(S) Vo^T

@@ -152,6 +152,17 @@ cudaError_t small_svd_launch(const double *A, int32_t l, double *Uo, double *S, 
 cudaError_t small_kernels_init();
 cudaError_t dense_kernels_init();
 
+// Device buffers of one orthonormalisation (CholeskyQR2 with shift).
+struct OrthBufs {
+  float *gram_partial = nullptr;  // n_part x l x l FP32
+  double *W = nullptr, *tmp = nullptr;  // l x l FP64 each
+  float *Rinv = nullptr;          // l x l FP32
+  int32_t *state = nullptr;       // kOrthStateInts
+  int32_t n_part = 0;
+};
+isvd_status orth_enqueue(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, double *Racc, const OrthBufs &o,
+                         isvd_info *info, cudaStream_t s);
+
 }  // namespace isvd
 
 // ---- the operator ------------------------------------------------------------

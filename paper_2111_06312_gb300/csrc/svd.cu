@@ -8,6 +8,22 @@
 #include "internal.h"
 
 namespace isvd {
+
+// CholeskyQR2 with conditional extra passes after a shifted one (passes 3, 4
+// return at once unless a shift happened in the two passes before them).
+isvd_status orth_enqueue(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, double *Racc, const OrthBufs &o,
+                         isvd_info *info, cudaStream_t s) {
+  ISVD_CUDA_TRY(orth_reset_launch(o.state, s));
+  if (Racc) ISVD_CUDA_TRY(racc_init_launch(Racc, l, s));
+  for (int pass = 1; pass <= 4; ++pass) {
+    PassGate g{o.state, pass};
+    ISVD_CUDA_TRY(gram_launch(Q, ldq, dt, rows, l, o.gram_partial, o.n_part, o.W, g, s));
+    ISVD_CUDA_TRY(chol_inv_launch(o.W, l, rows, dt, o.Rinv, l, nullptr, Racc, o.tmp, o.state, info, pass, s));
+    ISVD_CUDA_TRY(gemm_small_launch(Q, ldq, dt, rows, l, o.Rinv, l, l, true, Q, ldq, dt, g, s));
+  }
+  return ISVD_OK;
+}
+
 namespace {
 
 __global__ void cast_kernel_bf16_f32(const __nv_bfloat16 *in, float *out, int64_t n) {
@@ -27,14 +43,6 @@ struct Carver {
   }
 };
 
-struct OrthBufs {
-  float *gram_partial = nullptr;
-  double *W = nullptr, *tmp = nullptr;
-  float *Rinv = nullptr;
-  int32_t *state = nullptr;
-  int32_t n_part = 0;
-};
-
 void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o) {
   o->n_part = gram_partials(rows);
   o->gram_partial = c.take<float>((size_t)o->n_part * l * l);
@@ -42,21 +50,6 @@ void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o) {
   o->tmp = c.take<double>((size_t)l * l);
   o->Rinv = c.take<float>((size_t)l * l);
   o->state = c.take<int32_t>(kOrthStateInts);
-}
-
-// CholeskyQR2 with conditional extra passes after a shifted one (passes 3, 4
-// return at once unless a shift happened in the two passes before them).
-isvd_status orth_enqueue(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, double *Racc, const OrthBufs &o,
-                         isvd_info *info, cudaStream_t s) {
-  ISVD_CUDA_TRY(orth_reset_launch(o.state, s));
-  if (Racc) ISVD_CUDA_TRY(racc_init_launch(Racc, l, s));
-  for (int pass = 1; pass <= 4; ++pass) {
-    PassGate g{o.state, pass};
-    ISVD_CUDA_TRY(gram_launch(Q, ldq, dt, rows, l, o.gram_partial, o.n_part, o.W, g, s));
-    ISVD_CUDA_TRY(chol_inv_launch(o.W, l, rows, dt, o.Rinv, l, nullptr, Racc, o.tmp, o.state, info, pass, s));
-    ISVD_CUDA_TRY(gemm_small_launch(Q, ldq, dt, rows, l, o.Rinv, l, l, true, Q, ldq, dt, g, s));
-  }
-  return ISVD_OK;
 }
 
 struct SvdPlan {
