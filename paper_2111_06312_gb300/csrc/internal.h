@@ -145,10 +145,11 @@ cudaError_t chol_inv_launch(const double *W, int32_t l, int64_t rows, int dtype,
 cudaError_t racc_init_launch(double *Racc, int32_t l, cudaStream_t s);
 // SVD A = Uo diag(S) Vo^T of an l x l FP64 matrix by one-sided Jacobi on the
 // columns of A^T.  Optional FP32 copies of the first k columns (Uk, Vk: l x k)
-// and of S (k).  work: l2 x l2 FP64 (l2 = l rounded up to even).
+// and of S (k).  work: small_svd_work_doubles(l) FP64.
 cudaError_t small_svd_launch(const double *A, int32_t l, double *Uo, double *S, double *Vo, double *work,
                              float *Uk, float *Vk, float *Sk, int32_t k, isvd_info *info, int32_t iters,
                              cudaStream_t s);
+size_t small_svd_work_doubles(int32_t l);
 cudaError_t small_kernels_init();
 cudaError_t dense_kernels_init();
 

@@ -1,0 +1,321 @@
+// Small SVD of the Rayleigh-Ritz step (Alg. 1): A = Uo diag(S) Vo^T for an
+// l x l FP64 matrix (A = R from the QR of B^T), by one-sided Jacobi on the
+// columns of G = A^T, spread over a thread-block cluster.
+//
+// GB300 runs FP64 at ~8 GFLOP/s per SM, so one CTA cannot do the ~5 l^3 flop
+// per sweep quickly; the columns are split into 2*CL blocks held in the
+// shared memory of the CL CTAs of one cluster.  A sweep rotates every column
+// pair once: the pairs inside each block first, then the pairs across blocks,
+// block pairs meeting in round-robin tournament order with the blocks
+// travelling between CTAs through distributed shared memory (one cluster
+// barrier per step).  Rotations are not accumulated: after convergence the
+// columns w_p of G J have norms sigma_p, Vo = W Sigma^-1 and
+// Uo = J = A W Sigma^-2 (A A^T j_p = sigma_p^2 j_p), one FP64 product.
+// Rotation: Rutishauser's formula; converged when every pair satisfies
+// |g_p.g_q| <= tol ||g_p|| ||g_q||, tol = max(1e-15, sqrt(l) eps).
+#include <cooperative_groups.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace isvd {
+namespace {
+
+constexpr int kJacThreads = 256;
+constexpr int kJacMaxCluster = 16;
+constexpr int kJacMaxSmem = 200 * 1024;
+
+__device__ __forceinline__ void warp_sum3(double &a, double &b, double &c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+}
+
+// One warp rotates columns gp, gq (length l) if they are not yet orthogonal.
+__device__ __forceinline__ int rotate_pair(double *gp, double *gq, int l, int lane, double tol, double tiny) {
+  double al = 0.0, be = 0.0, ga = 0.0;
+  for (int i = lane; i < l; i += 32) {
+    const double x = gp[i], y = gq[i];
+    al += x * x;
+    be += y * y;
+    ga += x * y;
+  }
+  warp_sum3(al, be, ga);
+  if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) return 0;
+  if (al <= tiny && be <= tiny) return 0;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+  for (int i = lane; i < l; i += 32) {
+    const double x = gp[i], y = gq[i];
+    gp[i] = cs * x - sn * y;
+    gq[i] = sn * x + cs * y;
+  }
+  return 1;
+}
+
+// round-robin tournament on m (even) players: round r, pair k
+__device__ __forceinline__ void tourney(int r, int k, int m, int &p, int &q) {
+  if (k == 0) {
+    p = r;
+    q = m - 1;
+  } else {
+    p = (r + k) % (m - 1);
+    q = (r - k + (m - 1)) % (m - 1);
+  }
+}
+
+__global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
+    const double *__restrict__ A, int32_t l, int32_t bs, double *__restrict__ Wg, double *__restrict__ nrm_g,
+    int32_t *__restrict__ perm_g, double *__restrict__ Uo, double *__restrict__ S, double *__restrict__ Vo,
+    float *__restrict__ Uk, float *__restrict__ Vk, float *__restrict__ Sk, int32_t k, isvd_info *info,
+    int32_t iters) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
+  const int c = (int)cluster.block_rank();
+  const int nb = 2 * CL;
+  const int l3 = nb * bs;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  extern __shared__ double sm[];  // [2 buffers][2 slots][bs][l]
+  __shared__ int ids[2][2];
+  __shared__ int any_flags[kJacMaxCluster];
+  __shared__ int stop;
+  __shared__ double red[kJacThreads / 32];
+  auto colp = [&](int buf, int slot, int j) { return sm + ((size_t)(buf * 2 + slot) * bs + j) * l; };
+
+  if (tid == 0) {
+    ids[0][0] = c;
+    ids[0][1] = nb - 1 - c;
+  }
+  __syncthreads();
+  for (int slot = 0; slot < 2; ++slot)
+    for (int idx = tid; idx < bs * l; idx += blockDim.x) {
+      const int j = idx / l, i = idx - j * l;
+      const int p = ids[0][slot] * bs + j;
+      colp(0, slot, j)[i] = (p < l) ? A[(size_t)p * l + i] : 0.0;
+    }
+  // ||A||_F^2 (every CTA computes it from A: same value everywhere)
+  double f = 0.0;
+  for (int idx = tid; idx < l * l; idx += blockDim.x) f += A[idx] * A[idx];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if (lane == 0) red[warp] = f;
+  __syncthreads();
+  double fro2 = 0.0;
+  for (int w = 0; w < nwarp; ++w) fro2 += red[w];
+  const double eps = 2.220446049250313e-16;
+  const double tol = fmax(1e-15, sqrt((double)l) * eps);
+  const double tiny = (double)l * eps * (double)l * eps * fro2;
+  const int bsp = (bs + 1) & ~1;  // players of the in-block tournament
+  int cur = 0;
+  cluster.sync();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    int rotated = 0;
+    // pairs inside each of the two blocks held here
+    for (int r = 0; r < bsp - 1; ++r) {
+      for (int pi = warp; pi < bsp; pi += nwarp) {  // bsp/2 pairs per slot, two slots
+        const int slot = pi / (bsp / 2), kk = pi - slot * (bsp / 2);
+        int p, q;
+        tourney(r, kk, bsp, p, q);
+        if (p < bs && q < bs) rotated |= rotate_pair(colp(cur, slot, p), colp(cur, slot, q), l, lane, tol, tiny);
+      }
+      __syncthreads();
+    }
+    // pairs across blocks: nb - 1 tournament steps
+    for (int step = 0; step < nb - 1; ++step) {
+      for (int r = 0; r < bs; ++r) {
+        for (int i = warp; i < bs; i += nwarp)
+          rotated |= rotate_pair(colp(cur, 0, i), colp(cur, 1, (i + r) % bs), l, lane, tol, tiny);
+        __syncthreads();
+      }
+      if (CL == 1) continue;  // two blocks only: they never move
+      cluster.sync();
+      // circle [t1 .. t_{CL-1}, b_{CL-1} .. b0] rotates by one; t0 stays
+      const int nxt = cur ^ 1;
+      int src_rank[2], src_slot[2];
+      if (c == 0) {
+        src_rank[0] = 0; src_slot[0] = 0;
+      } else if (c == 1) {
+        src_rank[0] = 0; src_slot[0] = 1;
+      } else {
+        src_rank[0] = c - 1; src_slot[0] = 0;
+      }
+      if (c == CL - 1) {
+        src_rank[1] = c; src_slot[1] = 0;
+      } else {
+        src_rank[1] = c + 1; src_slot[1] = 1;
+      }
+      for (int slot = 0; slot < 2; ++slot) {
+        double *src = cluster.map_shared_rank(colp(cur, src_slot[slot], 0), src_rank[slot]);
+        double *dst = colp(nxt, slot, 0);
+        for (int idx = tid; idx < bs * l; idx += blockDim.x) dst[idx] = src[idx];
+        if (tid == 0) {
+          int *rid = cluster.map_shared_rank(&ids[cur][src_slot[slot]], src_rank[slot]);
+          ids[nxt][slot] = *rid;
+        }
+      }
+      cur = nxt;
+      __syncthreads();
+    }
+    // convergence: any rotation anywhere in the cluster?
+    const int mine = __syncthreads_or(rotated);
+    if (tid == 0) *cluster.map_shared_rank(&any_flags[c], 0) = mine;
+    cluster.sync();
+    if (tid == 0) {
+      const int *fl = cluster.map_shared_rank(any_flags, 0);
+      int any = 0;
+      for (int r = 0; r < CL; ++r) any |= fl[r];
+      stop = !any;
+    }
+    cluster.sync();  // any_flags of CTA 0 are rewritten next sweep
+    if (stop) break;
+  }
+  // columns and norms to global memory, by original block position
+  for (int slot = 0; slot < 2; ++slot)
+    for (int j = warp; j < bs; j += nwarp) {
+      const int p = ids[cur][slot] * bs + j;
+      const double *g = colp(cur, slot, j);
+      double s2 = 0.0;
+      for (int i = lane; i < l; i += 32) {
+        const double x = g[i];
+        s2 += x * x;
+        Wg[(size_t)p * l + i] = x;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) nrm_g[p] = sqrt(s2);
+    }
+  __threadfence();
+  cluster.sync();
+  if (c == 0 && tid == 0) {
+    // descending order of the first l columns (the rest are zero padding); stable
+    for (int p = 0; p < l; ++p) perm_g[p] = p;
+    for (int a = 1; a < l; ++a) {
+      const int x = perm_g[a];
+      const double nx = nrm_g[x];
+      int b = a - 1;
+      while (b >= 0 && nrm_g[perm_g[b]] < nx) {
+        perm_g[b + 1] = perm_g[b];
+        --b;
+      }
+      perm_g[b + 1] = x;
+    }
+    if (info) info->iters_done = iters;
+  }
+  (void)l3;
+  __threadfence();
+  cluster.sync();
+  // outputs: column kk of Vo = w_p / sigma, of Uo = A w_p / sigma^2
+  for (int kk = c; kk < l; kk += CL) {
+    const int p = perm_g[kk];
+    const double sg = nrm_g[p];
+    const double *w = Wg + (size_t)p * l;
+    for (int i = tid; i < l; i += blockDim.x) {
+      double u = 0.0;
+      for (int t = 0; t < l; ++t) u += A[(size_t)i * l + t] * w[t];
+      const double v = sg > 0.0 ? w[i] / sg : 0.0;
+      u = sg > 0.0 ? u / (sg * sg) : 0.0;
+      if (Vo) Vo[(size_t)i * l + kk] = v;
+      if (Uo) Uo[(size_t)i * l + kk] = u;
+      if (kk < k) {
+        if (Vk) Vk[(size_t)i * k + kk] = (float)v;
+        if (Uk) Uk[(size_t)i * k + kk] = (float)u;
+      }
+    }
+    if (tid == 0) {
+      if (S) S[kk] = sg;
+      if (Sk && kk < k) Sk[kk] = (float)sg;
+    }
+  }
+}
+
+int g_cluster = 0;
+std::once_flag g_once;
+cudaError_t g_err = cudaSuccess;
+
+size_t jac_smem(int32_t l, int32_t bs) { return sizeof(double) * 4 * (size_t)bs * l; }
+
+int block_size_for(int32_t l, int cl) { return (int)((l + 2 * cl - 1) / (2 * cl)); }
+
+cudaError_t pick_cluster() {
+  std::call_once(g_once, [] {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) cudaGetLastError();
+    e = cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacMaxSmem);
+    if (e != cudaSuccess) {
+      g_err = e;
+      return;
+    }
+    g_cluster = 1;
+    for (int cl : {16, 8, 4, 2}) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(cl);
+      cfg.blockDim = dim3(kJacThreads);
+      cfg.dynamicSmemBytes = jac_smem(ISVD_MAX_BLOCK, block_size_for(ISVD_MAX_BLOCK, cl));
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, jacobi_cluster_kernel, &cfg) == cudaSuccess && nclusters > 0) {
+        g_cluster = cl;
+        break;
+      }
+      cudaGetLastError();
+    }
+  });
+  return g_err;
+}
+
+}  // namespace
+
+cudaError_t small_svd_launch(const double *A, int32_t l, double *Uo, double *S, double *Vo, double *work, float *Uk,
+                             float *Vk, float *Sk, int32_t k, isvd_info *info, int32_t iters, cudaStream_t s) {
+  cudaError_t e = pick_cluster();
+  if (e != cudaSuccess) return e;
+  // at least 4 columns per block (fewer CTAs for small l)
+  int cl = g_cluster;
+  while (cl > 1 && block_size_for(l, cl) < 4) cl >>= 1;
+  const int bs = block_size_for(l, cl);
+  const int l3 = 2 * cl * bs;
+  if (jac_smem(l, bs) > (size_t)kJacMaxSmem) return cudaErrorInvalidConfiguration;
+  double *Wg = work;                                   // l3 x l
+  double *nrm = work + (size_t)l3 * l;                 // l3
+  int32_t *perm = reinterpret_cast<int32_t *>(nrm + l3);  // l
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(kJacThreads);
+  cfg.dynamicSmemBytes = jac_smem(l, bs);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, A, l, bs, Wg, nrm, perm, Uo, S, Vo, Uk, Vk, Sk, k, info,
+                            iters);
+}
+
+size_t small_svd_work_doubles(int32_t l) {
+  // largest l3 over the cluster sizes this file may pick, plus norms and order
+  size_t best = 0;
+  for (int cl = 1; cl <= kJacMaxCluster; cl <<= 1) {
+    const size_t l3 = (size_t)2 * cl * block_size_for(l, cl);
+    const size_t need = l3 * l + l3 + (l + 1) / 2 + 1;
+    if (need > best) best = need;
+  }
+  return best;
+}
+
+}  // namespace isvd

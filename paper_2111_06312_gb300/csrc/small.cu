@@ -1,7 +1,6 @@
-// Small l x l FP64 steps of the randomized SVD, one CTA each (l <= 160):
-//  - Cholesky of the Gram matrix Q^T Q with an adaptive diagonal shift and
-//    the inverse of the triangular factor (CholeskyQR, Alg. 2, right);
-//  - one-sided Jacobi SVD for the Rayleigh-Ritz step of Alg. 1.
+// Small l x l FP64 step of CholeskyQR (Alg. 2, right), one CTA (l <= 160):
+// Cholesky of the Gram matrix Q^T Q with an adaptive diagonal shift and the
+// inverse of the triangular factor.  (The Rayleigh-Ritz SVD is in jacobi.cu.)
 #include <mutex>
 
 #include "internal.h"
@@ -142,132 +141,7 @@ __global__ void racc_init_kernel(double *Racc, int32_t l) {
     Racc[idx] = (idx / l == idx % l) ? 1.0 : 0.0;
 }
 
-// One-sided Jacobi on the columns of G = A^T (column p of G is row p of A,
-// kept contiguous in shared memory).  Pairs follow the round-robin
-// tournament order, l/2 disjoint pairs per round, one warp per pair.
-// Rotation: Rutishauser's formula; convergence when every pair satisfies
-// |g_p.g_q| <= tol ||g_p|| ||g_q|| with tol = max(1e-15, sqrt(l) eps).
-// Then A^T = (G J Sigma^-1) Sigma J^T, i.e. A = J Sigma (G J Sigma^-1)^T:
-// Uo = J, Vo = normalised rotated columns, S descending.
-__global__ void __launch_bounds__(kSmallThreads) jacobi_kernel(const double *__restrict__ A, int32_t l,
-                                                               double *__restrict__ Uo, double *__restrict__ S,
-                                                               double *__restrict__ Vo, double *__restrict__ Jt,
-                                                               float *__restrict__ Uk, float *__restrict__ Vk,
-                                                               float *__restrict__ Sk, int32_t k, isvd_info *info,
-                                                               int32_t iters) {
-  extern __shared__ double Gs[];  // [l2][l2]
-  __shared__ double nrm[ISVD_MAX_BLOCK + 2];
-  __shared__ int perm[ISVD_MAX_BLOCK + 2];
-  __shared__ double fro2;
-  const int l2 = (l + 1) & ~1;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
-  for (int idx = tid; idx < l2 * l2; idx += nt) {
-    const int p = idx / l2, i = idx - p * l2;
-    Gs[idx] = (p < l && i < l) ? A[(size_t)p * l + i] : 0.0;
-    Jt[idx] = (p == i) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double f = 0.0;
-    for (int idx = 0; idx < l2 * l2; ++idx) f += Gs[idx] * Gs[idx];
-    fro2 = f;
-  }
-  __syncthreads();
-  const double eps = 2.220446049250313e-16;
-  const double tol = fmax(1e-15, sqrt((double)l2) * eps);
-  const double tiny = (double)l2 * eps * (double)l2 * eps * fro2;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    int rotated = 0;
-    for (int round = 0; round < l2 - 1; ++round) {
-      for (int pi = warp; pi < l2 / 2; pi += nwarp) {
-        int p, q;
-        if (pi == 0) {
-          p = round;
-          q = l2 - 1;
-        } else {
-          p = (round + pi) % (l2 - 1);
-          q = (round - pi + (l2 - 1)) % (l2 - 1);
-        }
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int i = lane; i < l2; i += 32) {
-          const double gp = Gs[(size_t)p * l2 + i], gq = Gs[(size_t)q * l2 + i];
-          al += gp * gp;
-          be += gq * gq;
-          ga += gp * gq;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) continue;
-        if (al <= tiny && be <= tiny) continue;
-        rotated = 1;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-        for (int i = lane; i < l2; i += 32) {
-          const double gp = Gs[(size_t)p * l2 + i], gq = Gs[(size_t)q * l2 + i];
-          Gs[(size_t)p * l2 + i] = cs * gp - sn * gq;
-          Gs[(size_t)q * l2 + i] = sn * gp + cs * gq;
-          const double jp = Jt[(size_t)p * l2 + i], jq = Jt[(size_t)q * l2 + i];
-          Jt[(size_t)p * l2 + i] = cs * jp - sn * jq;
-          Jt[(size_t)q * l2 + i] = sn * jp + cs * jq;
-        }
-      }
-      __syncthreads();
-    }
-    if (!__syncthreads_or(rotated)) break;
-  }
-  // column norms and descending order
-  for (int p = warp; p < l2; p += nwarp) {
-    double s = 0.0;
-    for (int i = lane; i < l2; i += 32) s += Gs[(size_t)p * l2 + i] * Gs[(size_t)p * l2 + i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) nrm[p] = sqrt(s);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int p = 0; p < l2; ++p) perm[p] = p;
-    for (int a = 1; a < l2; ++a) {  // stable insertion sort, descending
-      const int x = perm[a];
-      int b = a - 1;
-      while (b >= 0 && nrm[perm[b]] < nrm[x]) {
-        perm[b + 1] = perm[b];
-        --b;
-      }
-      perm[b + 1] = x;
-    }
-    if (info) info->iters_done = iters;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < l * l; idx += nt) {
-    const int i = idx / l, c = idx - i * l;
-    const int p = perm[c];
-    const double sg = nrm[p];
-    const double v = sg > 0.0 ? Gs[(size_t)p * l2 + i] / sg : 0.0;
-    const double u = Jt[(size_t)p * l2 + i];
-    if (Vo) Vo[idx] = v;
-    if (Uo) Uo[idx] = u;
-    if (c < k) {
-      if (Vk) Vk[(size_t)i * k + c] = (float)v;
-      if (Uk) Uk[(size_t)i * k + c] = (float)u;
-    }
-  }
-  for (int c = tid; c < l; c += nt) {
-    if (S) S[c] = nrm[perm[c]];
-    if (Sk && c < k) Sk[c] = (float)nrm[perm[c]];
-  }
-}
-
 size_t chol_smem(int32_t l) { return sizeof(double) * ((size_t)l * l + l); }
-size_t jacobi_smem(int32_t l) {
-  const size_t l2 = (size_t)((l + 1) & ~1);
-  return sizeof(double) * l2 * l2;
-}
 
 }  // namespace
 
@@ -277,9 +151,6 @@ cudaError_t small_kernels_init() {
   std::call_once(once, [] {
     cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)chol_smem(ISVD_MAX_BLOCK));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)jacobi_smem(ISVD_MAX_BLOCK));
     err = e;
   });
   return err;
@@ -302,12 +173,6 @@ cudaError_t chol_inv_launch(const double *W, int32_t l, int64_t rows, int dtype,
   (void)dtype;  // the Gram is accumulated in FP32 for both storage types
   const double u = 5.9604644775390625e-08;
   chol_inv_kernel<<<1, kSmallThreads, chol_smem(l), s>>>(W, l, u, Rinv, ldr, R, Racc, tmp, state, info, pass);
-  return cudaGetLastError();
-}
-
-cudaError_t small_svd_launch(const double *A, int32_t l, double *Uo, double *S, double *Vo, double *work, float *Uk,
-                             float *Vk, float *Sk, int32_t k, isvd_info *info, int32_t iters, cudaStream_t s) {
-  jacobi_kernel<<<1, kSmallThreads, jacobi_smem(l), s>>>(A, l, Uo, S, Vo, work, Uk, Vk, Sk, k, info, iters);
   return cudaGetLastError();
 }
 

@@ -88,12 +88,11 @@ size_t carve_svd(const isvd_operator *op, const SvdPlan &P, char *base, SvdBufs 
   const size_t ab = std::max(apply_scratch_bytes(op, P.l, DT_F32, false), apply_scratch_bytes(op, P.l, DT_F32, true));
   b->apply_base = c.take<char>(ab);
   carve_orth(c, std::max(rows, cols), P.l, &b->orth);
-  const int32_t l2 = (P.l + 1) & ~1;
   b->Racc = c.take<double>((size_t)P.l * P.l);
   b->Uo = c.take<double>((size_t)P.l * P.l);
   b->Vo = c.take<double>((size_t)P.l * P.l);
   b->So = c.take<double>((size_t)P.l);
-  b->jwork = c.take<double>((size_t)l2 * l2);
+  b->jwork = c.take<double>(small_svd_work_doubles(P.l));
   b->Lk = c.take<float>((size_t)P.l * P.k);
   b->Rk = c.take<float>((size_t)P.l * P.k);
   b->info = c.take<isvd_info>(1);
@@ -280,9 +279,8 @@ isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double
   if (!op || !A || !Uo || !S || !Vo) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
   if (l < 1 || l > ISVD_MAX_BLOCK) return fail(ISVD_ERR_SHAPE, "need 1 <= l <= %d", ISVD_MAX_BLOCK);
   cudaStream_t s = (cudaStream_t)stream;
-  const int32_t l2 = (l + 1) & ~1;
   Carver c{nullptr};
-  c.take<double>((size_t)l2 * l2);
+  c.take<double>(small_svd_work_doubles(l));
   ISVD_TRY(ensure_arena(op, c.off, s));
   ISVD_CUDA_TRY(small_svd_launch(A, l, Uo, S, Vo, (double *)op->arena, nullptr, nullptr, nullptr, 0, dev_info, 0, s));
   return ISVD_OK;
