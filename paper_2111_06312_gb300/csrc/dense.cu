@@ -157,68 +157,9 @@ __global__ void project_final_kernel(const double *partial, int32_t n_part, int3
   c[(int64_t)t * ldc + col] = (float)s;
 }
 
-// ---- Gram  W = Q^T Q  (FP32 products, FP64 combination of row chunks) -----------
+// ---- conditional CholeskyQR passes ------------------------------------------------
 __device__ __forceinline__ bool pass_skipped(const PassGate &g) {
   return g.state != nullptr && g.pass > 2 && g.state[0] + 2 < g.pass;
-}
-
-constexpr int kGramTile = 32;   // rows staged per step
-constexpr int kGramMaxT = 10;   // (ISVD_MAX_BLOCK / 16)
-
-template <typename T>
-__global__ void __launch_bounds__(256) gram_partial_kernel(const T *Q, int64_t ldq, int64_t rows, int32_t l,
-                                                           float *partial, int64_t rows_per_part,
-                                                           PassGate g) {
-  if (pass_skipped(g)) return;
-  extern __shared__ float tile[];  // [kGramTile][lp]
-  const int lp = l | 1;            // odd stride: conflict-free column reads
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int TT = (l + 15) / 16;
-  float acc[kGramMaxT][kGramMaxT];
-#pragma unroll
-  for (int i = 0; i < kGramMaxT; ++i)
-#pragma unroll
-    for (int j = 0; j < kGramMaxT; ++j) acc[i][j] = 0.f;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_part;
-  const int64_t r1 = min(rows, r0 + rows_per_part);
-  for (int64_t rt = r0; rt < r1; rt += kGramTile) {
-    for (int idx = threadIdx.x; idx < kGramTile * l; idx += blockDim.x) {
-      const int rr = idx / l, c = idx - rr * l;
-      tile[rr * lp + c] = (rt + rr < r1) ? to_float(Q[(rt + rr) * ldq + c]) : 0.f;
-    }
-    __syncthreads();
-    for (int rr = 0; rr < kGramTile; ++rr) {
-      float av[kGramMaxT], bv[kGramMaxT];
-#pragma unroll
-      for (int i = 0; i < kGramMaxT; ++i) {
-        const int ca = ty * TT + i, cb = tx * TT + i;
-        av[i] = (i < TT && ca < l) ? tile[rr * lp + ca] : 0.f;
-        bv[i] = (i < TT && cb < l) ? tile[rr * lp + cb] : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < kGramMaxT; ++i)
-#pragma unroll
-        for (int j = 0; j < kGramMaxT; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  float *P = partial + (int64_t)blockIdx.x * l * l;
-#pragma unroll
-  for (int i = 0; i < kGramMaxT; ++i)
-#pragma unroll
-    for (int j = 0; j < kGramMaxT; ++j) {
-      const int a = ty * TT + i, b = tx * TT + j;
-      if (i < TT && j < TT && a < l && b < l) P[a * l + b] = acc[i][j];
-    }
-}
-
-__global__ void gram_reduce_kernel(const float *partial, int32_t n_part, int32_t l, double *W, PassGate g) {
-  if (pass_skipped(g)) return;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)l * l) return;
-  double s = 0.0;
-  for (int p = 0; p < n_part; ++p) s += (double)partial[(int64_t)p * l * l + idx];
-  W[idx] = s;
 }
 
 // ---- out = Q B  (B small, staged in shared memory) -------------------------------
@@ -357,26 +298,6 @@ cudaError_t lowrank_project_launch(const void *G, int64_t ldg, int dtype, int64_
                                                                   r, ones_first, partial, pb);
   const int64_t tot = (int64_t)r * b;
   project_final_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, s>>>(partial, n_part, r, b, pb, c, ldc);
-  return cudaGetLastError();
-}
-
-int32_t gram_partials(int64_t rows) {
-  int64_t p = ceil_div(rows, 256);
-  if (p > 2 * kNumSMs) p = 2 * kNumSMs;
-  if (p < 1) p = 1;
-  return (int32_t)p;
-}
-
-cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, float *partial,
-                        int32_t n_part, double *W, PassGate g, cudaStream_t s) {
-  const int64_t rpp = round_up(ceil_div(rows, n_part), kGramTile);
-  const size_t smem = sizeof(float) * kGramTile * (size_t)(l | 1);
-  if (dtype == DT_F32)
-    gram_partial_kernel<float><<<n_part, 256, smem, s>>>((const float *)Q, ldq, rows, l, partial, rpp, g);
-  else
-    gram_partial_kernel<__nv_bfloat16><<<n_part, 256, smem, s>>>((const __nv_bfloat16 *)Q, ldq, rows, l, partial,
-                                                                  rpp, g);
-  gram_reduce_kernel<<<(unsigned)ceil_div((int64_t)l * l, 256), 256, 0, s>>>(partial, n_part, l, W, g);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,328 @@
+// Q <- Q B on tcgen05 with B upper triangular (B = R^-1 of CholeskyQR,
+// Alg. 2: Q_hat = Q (L^-1)^T, L^T = R), in place, Q n x l row-major, l <= 160.
+//
+// B stays in shared memory for the whole kernel as K-major panels (128-byte
+// swizzle) of 32 (FP32) or 64 (BF16) rows of K; because B is upper
+// triangular, panel p only multiplies output columns n >= first k of the
+// panel, so it is stored and multiplied for those columns only (MMA N shrinks
+// panel by panel, and its accumulator starts at that column).  Q is streamed in
+// 128-row tiles, panel by panel, by cp.async straight into the swizzled
+// layout (row r of the tile = 128 bytes of row r of Q).  FP32 blocks use
+// 3xTF32 (A and B split into TF32 hi + lo); BF16 blocks one BF16 MMA.  The
+// FP32 accumulator (128 x round16(l)) is double-buffered in tensor memory so
+// the epilogue warps write tile t while tile t+1 is multiplied.
+#include <mutex>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace isvd {
+namespace {
+
+using namespace tc;
+
+constexpr int kProdWarps = 8;
+constexpr int kProd = kProdWarps * 32;
+constexpr int kMmaWarp = kProdWarps;       // warp 8
+constexpr int kEpiWarp0 = kProdWarps + 1;  // warps 9..12
+constexpr int kThreads = (kProdWarps + 1 + 4) * 32;
+constexpr int kStages = 3;
+constexpr int kTmemCols = 512;
+constexpr int kDBufCol = 256;  // column offset of accumulator buffer 1
+
+__device__ __forceinline__ void cp_async16_zfill(uint32_t saddr, const void *g, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void producer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kProd) : "memory"); }
+
+template <int DT>
+struct GemmCfg {
+  static constexpr bool F32 = DT == DT_F32;
+  static constexpr int ES = F32 ? 4 : 2;
+  static constexpr int KE = F32 ? 32 : 64;  // K elements per panel (128 bytes)
+  static constexpr int NT = F32 ? 2 : 1;
+  static constexpr int STAGE = NT * 128 * 128;  // bytes per A stage
+};
+
+// Panel p of B holds K rows [p*KE, p*KE + KE) and output columns n in
+// [p*KE, N1): np(p) = N1 - p*KE rows of 128 bytes, at byte offset
+// bo(p) = 128 * sum_{q<p} np(q).
+struct Layout {
+  int KE, KP, N1, bbytes;
+  __host__ __device__ int np(int p) const { return N1 - p * KE; }
+  __host__ __device__ int bo(int p) const { return 128 * (p * N1 - KE * p * (p - 1) / 2); }
+};
+
+template <int DT>
+__host__ __device__ Layout make_layout(int l) {
+  using C = GemmCfg<DT>;
+  Layout L{};
+  L.KE = C::KE;
+  L.KP = (l + C::KE - 1) / C::KE;
+  L.N1 = (l + 15) & ~15;
+  L.bbytes = L.bo(L.KP);
+  return L;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tc_kernel(void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, const float *__restrict__ B,
+                   int64_t ldb, const int32_t *gate_state, int32_t gate_pass, int32_t *err_state) {
+  using C = GemmCfg<DT>;
+  if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
+  const Layout L = make_layout<DT>(l);
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], dfull[2], dfree[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  unsigned char *sm = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
+  unsigned char *bhi = sm;
+  unsigned char *blo = sm + L.bbytes;                         // F32 only
+  unsigned char *astage = sm + C::NT * L.bbytes;              // [kStages][NT][16 KB]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (rows + 127) / 128;
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t G = my_tiles * L.KP;
+
+  // B panels: element (k, n) of B, k in panel p, n >= p*KE, stored K-major
+  for (int p = 0; p < L.KP; ++p) {
+    const int k0 = p * C::KE;
+    for (int idx = tid; idx < L.np(p) * C::KE; idx += blockDim.x) {
+      const int nn = idx / C::KE, kk = idx - nn * C::KE;
+      const int n = k0 + nn, k = k0 + kk;
+      const float x = (k < l && n < l && k <= n) ? B[(size_t)k * ldb + n] : 0.f;
+      const uint32_t off = L.bo(p) + sw128(nn, kk * C::ES);
+      if (C::F32) {
+        float hi, lo;
+        split_tf32(x, hi, lo);
+        *reinterpret_cast<float *>(bhi + off) = hi;
+        *reinterpret_cast<float *>(blo + off) = lo;
+      } else {
+        *reinterpret_cast<__nv_bfloat16 *>(bhi + off) = __float2bfloat16_rn(x);
+      }
+    }
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], kProd);
+      mbar_init(&empty[s], 1);
+    }
+    for (int d = 0; d < 2; ++d) {
+      mbar_init(&dfull[d], 1);
+      mbar_init(&dfree[d], 128);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  fence_async_shared();
+  __syncthreads();
+  if (warp == 0) tmem_alloc(&tmem_slot, kTmemCols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  char *Q = reinterpret_cast<char *>(Qv);
+
+  if (warp < kProdWarps) {
+    // ---------------- producers: stream A panels ----------------
+    auto tile_row0 = [&](int64_t lt) { return ((int64_t)blockIdx.x + lt * gridDim.x) * 128; };
+    auto issue = [&](int64_t g) {
+      const int s = (int)(g % kStages);
+      const int64_t lt = g / L.KP;
+      const int p = (int)(g - lt * L.KP);
+      unsigned char *ahi = astage + (size_t)s * C::STAGE;
+      const int64_t rb = tile_row0(lt);
+      for (int t = tid; t < 128 * 8; t += kProd) {  // 128 rows x 8 pieces of 16 bytes
+        const int r = t >> 3, q = t & 7;
+        const int64_t row = rb + r;
+        const int64_t colb = (int64_t)p * 128 + q * 16;   // byte offset in the row
+        const bool ok = row < rows && colb < ldq * C::ES;
+        const char *src = ok ? Q + ((size_t)row * ldq) * C::ES + colb : Q;
+        cp_async16_zfill(smem_u32(ahi + sw128(r, q * 16)), src, ok ? 16u : 0u);
+      }
+    };
+    auto transform = [&](int64_t g) {
+      const int s = (int)(g % kStages);
+      const int p = (int)(g % L.KP);
+      unsigned char *ahi = astage + (size_t)s * C::STAGE;
+      unsigned char *alo = ahi + 128 * 128;
+      for (int t = tid; t < 128 * 8; t += kProd) {
+        const int r = t >> 3, q = t & 7;
+        const uint32_t off = sw128(r, q * 16);
+        const int k0 = p * C::KE + q * (16 / C::ES);  // first column of this piece
+        if (C::F32) {
+          float4 v = *reinterpret_cast<float4 *>(ahi + off);
+          float x[4] = {v.x, v.y, v.z, v.w}, hi[4], lo[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (k0 + j >= l) x[j] = 0.f;  // padding columns never enter the product
+            split_tf32(x[j], hi[j], lo[j]);
+          }
+          *reinterpret_cast<float4 *>(ahi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<float4 *>(alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        } else if (k0 + 8 > l) {
+          unsigned short *h = reinterpret_cast<unsigned short *>(ahi + off);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (k0 + j >= l) h[j] = 0;
+        }
+      }
+    };
+    int64_t next_issue = 0;
+    for (int64_t g = 0; g < G; ++g) {
+      // keep two panels in flight ahead of the one being transformed
+      while (next_issue < G && next_issue <= g + 2) {
+        const int s = (int)(next_issue % kStages);
+        if (tid == 0 && next_issue >= kStages &&
+            !mbar_wait(&empty[s], (uint32_t)(((next_issue / kStages) & 1) ^ 1))) {
+          abort_flag = 1;
+          if (err_state) atomicExch(&err_state[2], 1);
+        }
+        producer_bar();
+        if (abort_flag) break;
+        issue(next_issue);
+        cp_async_commit();
+        ++next_issue;
+      }
+      if (abort_flag) break;
+      // wait until panel g has landed: at most (next_issue - 1 - g) younger groups pending
+      const int64_t younger = next_issue - 1 - g;
+      if (younger >= 2) cp_async_wait<2>();
+      else if (younger == 1) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      producer_bar();
+      transform(g);
+      fence_async_shared();
+      mbar_arrive(&full[g % kStages]);
+    }
+    cp_async_wait<0>();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t fmt = C::F32 ? 2u : 1u;
+      for (int64_t lt = 0; lt < my_tiles && !abort_flag; ++lt) {
+        const int d = (int)(lt & 1);
+        if (lt >= 2 && !mbar_wait(&dfree[d], (uint32_t)(((lt >> 1) & 1) ^ 1))) {
+          if (err_state) atomicExch(&err_state[2], 1);
+          abort_flag = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t dcol = tmem + (d ? kDBufCol : 0);
+        for (int p = 0; p < L.KP; ++p) {
+          const int64_t g = lt * L.KP + p;
+          const int s = (int)(g % kStages);
+          if (!mbar_wait(&full[s], (uint32_t)((g / kStages) & 1))) {
+            if (err_state) atomicExch(&err_state[2], 1);
+            abort_flag = 1;
+            break;
+          }
+          fence_after();
+          const uint32_t id = idesc(fmt, 128, L.np(p));
+          const uint32_t ahi = smem_u32(astage + (size_t)s * C::STAGE), alo = ahi + 128 * 128;
+          const uint32_t b_hi = smem_u32(bhi + L.bo(p)), b_lo = smem_u32(blo + L.bo(p));
+          const uint32_t dp = dcol + p * C::KE;  // accumulator columns n >= p*KE
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t acc = (p > 0 || kk > 0) ? 1u : 0u;
+            const uint64_t da = desc_sw128(ahi + kk * 32, 1024), db = desc_sw128(b_hi + kk * 32, 1024);
+            if (C::F32) {
+              mma_tf32(dp, da, db, id, acc);
+              mma_tf32(dp, da, desc_sw128(b_lo + kk * 32, 1024), id, 1u);
+              mma_tf32(dp, desc_sw128(alo + kk * 32, 1024), db, id, 1u);
+            } else {
+              mma_bf16(dp, da, db, id, acc);
+            }
+          }
+          commit(&empty[s]);
+        }
+        commit(&dfull[d]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: TMEM -> Q rows ----------------
+    const int sub = warp & 3;  // TMEM lane quarter of this warp
+    const int r = sub * 32 + lane;
+    for (int64_t lt = 0; lt < my_tiles; ++lt) {
+      const int d = (int)(lt & 1);
+      if (!mbar_wait(&dfull[d], (uint32_t)((lt >> 1) & 1))) {
+        if (err_state && lane == 0) atomicExch(&err_state[2], 1);
+        break;
+      }
+      fence_after();
+      const int64_t row = ((int64_t)blockIdx.x + lt * gridDim.x) * 128 + r;
+      uint32_t v[32];
+      for (int cb = 0; cb < L.N1; cb += 32) {
+        tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (d ? kDBufCol : 0) + cb, v);
+        if (row < rows) {
+          char *dst = Q + ((size_t)row * ldq + cb) * C::ES;
+          if (C::F32) {
+            const int n = min(32, l - cb);
+            if (n == 32) {
+#pragma unroll
+              for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<uint4 *>(dst + j * 4) = make_uint4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            } else {
+              for (int j = 0; j < n; ++j) reinterpret_cast<float *>(dst)[j] = __uint_as_float(v[j]);
+            }
+          } else {
+            const int n = min(32, l - cb);
+            __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(dst);
+            for (int j = 0; j < n; ++j) o[j] = __float2bfloat16_rn(__uint_as_float(v[j]));
+          }
+        }
+      }
+      fence_before();
+      mbar_arrive(&dfree[d]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int DT>
+size_t gemm_tc_smem(int32_t l) {
+  using C = GemmCfg<DT>;
+  const Layout L = make_layout<DT>(l);
+  return (size_t)C::NT * L.bbytes + (size_t)kStages * C::STAGE + 1024;
+}
+
+std::once_flag g_once;
+cudaError_t g_err = cudaSuccess;
+
+}  // namespace
+
+cudaError_t gemm_tc_init() {
+  std::call_once(g_once, [] {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<DT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_tc_smem<DT_F32>(ISVD_MAX_BLOCK));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_tc_kernel<DT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)gemm_tc_smem<DT_BF16>(ISVD_MAX_BLOCK));
+    g_err = e;
+  });
+  return g_err;
+}
+
+cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, const float *B,
+                                    int64_t ldb, PassGate g, cudaStream_t s) {
+  cudaError_t e = gemm_tc_init();
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (rows + 127) / 128;
+  const int grid = (int)std::min<int64_t>(ntiles, kNumSMs);
+  int32_t *err = const_cast<int32_t *>(g.state);
+  if (dtype == DT_F32)
+    gemm_tc_kernel<DT_F32><<<grid, kThreads, gemm_tc_smem<DT_F32>(l), s>>>(Q, ldq, rows, l, B, ldb, g.state, g.pass, err);
+  else
+    gemm_tc_kernel<DT_BF16><<<grid, kThreads, gemm_tc_smem<DT_BF16>(l), s>>>(Q, ldq, rows, l, B, ldb, g.state, g.pass,
+                                                                            err);
+  return cudaGetLastError();
+}
+
+}  // namespace isvd

@@ -103,6 +103,24 @@ cudaError_t spmm_launch(const SpmmArgs &a, int dtype, const HeavyPlan &hp, float
 // Column slabs for a block of width b (row-major, 16-byte aligned).
 int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out);
 
+// Nonzero-balanced form: warps take chunks of CH consecutive nonzeros; rows
+// crossing chunk boundaries (split) and rows without nonzeros (empty) are
+// finished by two small passes.  row_of[e] is the row of nonzero e.
+struct ChunkPlan {
+  int64_t nnz = 0;
+  int32_t CH = 512;
+  int64_t nchunks = 0;
+  int32_t *row_of = nullptr;
+  int4 *split = nullptr;  // (row, first chunk, last chunk, 0)
+  int32_t nsplit = 0;
+  int32_t *empty = nullptr;
+  int32_t nempty = 0;
+};
+// part: nchunks x 2 x pw FP32 partial sums (head / tail row of each chunk).
+cudaError_t spmm_chunk_launch(const SpmmArgs &a, int dtype, const ChunkPlan &cp, float *part, int64_t pw,
+                              cudaStream_t s);
+int chunk_slab_cols(int dtype);
+
 // ---- dense helpers -----------------------------------------------------------
 cudaError_t gaussian_launch(uint64_t seed, int64_t rows, int32_t cols, void *out, int64_t ld, int dtype,
                             cudaStream_t s);
@@ -125,6 +143,10 @@ struct PassGate {
 int32_t gram_partials(int64_t rows);
 cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, float *partial,
                         int32_t n_part, double *W, PassGate g, cudaStream_t s);
+
+// Q <- Q B in place on the tensor cores, B (l x l, FP32) upper triangular.
+cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, const float *B,
+                                    int64_t ldb, PassGate g, cudaStream_t s);
 
 // out (rows x w) = Q (rows x l) B (l x w, FP32, ld ldb); upper: B upper
 // triangular.  out may equal Q (in place) when w == l and out dtype == in dtype.
@@ -184,6 +206,9 @@ struct isvd_operator {
   const float *x_values = nullptr;
   int64_t x_nnz = 0;
   isvd::HeavyPlan heavy_A, heavy_X, heavy_XT;
+  isvd::ChunkPlan chunk_A, chunk_X, chunk_XT;
+  int32_t spmm_algo = 0;    // 1: nonzero-balanced chunks, 0: row groups with hub splitting
+  int32_t chunk_nnz = 512;
   std::vector<void *> owned;  // allocations released at destroy
   // workspace arena (grow only)
   void *arena = nullptr;
@@ -203,6 +228,7 @@ struct isvd_operator {
 namespace isvd {
 void *op_alloc(isvd_operator *op, size_t bytes, cudaStream_t s);
 void free_heavy(isvd_operator *op, HeavyPlan *hp, cudaStream_t s);
+void free_chunks(isvd_operator *op, ChunkPlan *cp, cudaStream_t s);
 void op_free(isvd_operator *op, void *p, cudaStream_t s);
 isvd_status ensure_arena(isvd_operator *op, size_t bytes, cudaStream_t s);
 

@@ -215,6 +215,16 @@ void free_heavy(isvd_operator *op, HeavyPlan *hp, cudaStream_t s) {
   hp->n_rows = hp->n_chunks = 0;
 }
 
+void free_chunks(isvd_operator *op, ChunkPlan *cp, cudaStream_t s) {
+  op_free(op, cp->row_of, s);
+  op_free(op, cp->split, s);
+  op_free(op, cp->empty, s);
+  cp->row_of = nullptr;
+  cp->split = nullptr;
+  cp->empty = nullptr;
+  cp->nchunks = cp->nsplit = cp->nempty = 0;
+}
+
 namespace {
 
 // Build the hub-row split plan from a host copy of rowptr.
@@ -247,6 +257,50 @@ isvd_status build_heavy(isvd_operator *op, const int32_t *rowptr_dev, int64_t ro
   ISVD_CUDA_TRY(cudaMemcpyAsync(hp->chunks, chunks.data(), sizeof(int2) * chunks.size(), cudaMemcpyHostToDevice, s));
   ISVD_CUDA_TRY(cudaMemcpyAsync(hp->chunk_end, ends.data(), sizeof(int32_t) * ends.size(), cudaMemcpyHostToDevice, s));
   ISVD_CUDA_TRY(cudaMemcpyAsync(hp->rows, hrows.data(), sizeof(int4) * hrows.size(), cudaMemcpyHostToDevice, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  return ISVD_OK;
+}
+
+// Nonzero-chunk plan: row of every nonzero (device), rows that cross a chunk
+// boundary and rows without nonzeros (host lists, uploaded).
+isvd_status build_chunks(isvd_operator *op, const int32_t *rowptr_dev, int64_t rows, int64_t nnz, ChunkPlan *cp,
+                         cudaStream_t s) {
+  free_chunks(op, cp, s);
+  cp->nnz = nnz;
+  cp->CH = op->chunk_nnz;
+  cp->nchunks = nnz > 0 ? ceil_div(nnz, cp->CH) : 0;
+  if (nnz > 0) {
+    cp->row_of = (int32_t *)op_alloc(op, sizeof(int32_t) * nnz, s);
+    if (!cp->row_of) return fail(ISVD_ERR_WORKSPACE, "row index allocation failed");
+    row_of_entry_kernel<<<grid_for(rows), 256, 0, s>>>(rows, rowptr_dev, cp->row_of);
+    ISVD_CUDA_TRY(cudaGetLastError());
+  }
+  std::vector<int32_t> rp((size_t)rows + 1);
+  ISVD_CUDA_TRY(cudaMemcpyAsync(rp.data(), rowptr_dev, sizeof(int32_t) * (rows + 1), cudaMemcpyDeviceToHost, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int4> split;
+  std::vector<int32_t> empty;
+  for (int64_t i = 0; i < rows; ++i) {
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    if (e0 == e1) {
+      empty.push_back((int32_t)i);
+      continue;
+    }
+    const int64_t cf = e0 / cp->CH, cl = (e1 - 1) / cp->CH;
+    if (cf != cl) split.push_back(make_int4((int)i, (int)cf, (int)cl, 0));
+  }
+  cp->nsplit = (int32_t)split.size();
+  cp->nempty = (int32_t)empty.size();
+  if (cp->nsplit) {
+    cp->split = (int4 *)op_alloc(op, sizeof(int4) * split.size(), s);
+    if (!cp->split) return fail(ISVD_ERR_WORKSPACE, "split-row list allocation failed");
+    ISVD_CUDA_TRY(cudaMemcpyAsync(cp->split, split.data(), sizeof(int4) * split.size(), cudaMemcpyHostToDevice, s));
+  }
+  if (cp->nempty) {
+    cp->empty = (int32_t *)op_alloc(op, sizeof(int32_t) * empty.size(), s);
+    if (!cp->empty) return fail(ISVD_ERR_WORKSPACE, "empty-row list allocation failed");
+    ISVD_CUDA_TRY(cudaMemcpyAsync(cp->empty, empty.data(), sizeof(int32_t) * empty.size(), cudaMemcpyHostToDevice, s));
+  }
   ISVD_CUDA_TRY(cudaStreamSynchronize(s));
   return ISVD_OK;
 }
@@ -424,6 +478,7 @@ isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaS
   }
   if (!(d.flags & ISVD_FLAG_SKIP_SYMMETRY_CHECK)) ISVD_TRY(check_symmetry(op, d.A, flags, s));
   ISVD_TRY(build_heavy(op, d.A.rowptr, n, &op->heavy_A, s));
+  ISVD_TRY(build_chunks(op, d.A.rowptr, n, d.A.nnz, &op->chunk_A, s));
 
   if (d.form == ISVD_FORM_CONCAT) {
     if (d.X.rowptr) {
@@ -448,6 +503,8 @@ isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaS
                            &op->xt_colidx, &op->xt_values, s));
     ISVD_TRY(build_heavy(op, op->x_rowptr, n, &op->heavy_X, s));
     ISVD_TRY(build_heavy(op, op->xt_rowptr, d.d, &op->heavy_XT, s));
+    ISVD_TRY(build_chunks(op, op->x_rowptr, n, op->x_nnz, &op->chunk_X, s));
+    ISVD_TRY(build_chunks(op, op->xt_rowptr, d.d, op->x_nnz, &op->chunk_XT, s));
   }
   ISVD_CUDA_TRY(cudaStreamSynchronize(s));
   return ISVD_OK;
@@ -462,7 +519,10 @@ struct Chain {
   const ApplyScratch *sc;
 };
 
-int slab_cols(const isvd_operator *op, int dtype) { return dtype == DT_F32 ? op->slab_cols_f32 : op->slab_cols_bf16; }
+int slab_cols(const isvd_operator *op, int dtype) {
+  if (op->spmm_algo == 1) return chunk_slab_cols(dtype);
+  return dtype == DT_F32 ? op->slab_cols_f32 : op->slab_cols_bf16;
+}
 
 SpmmArgs base_args_A(const isvd_operator *op) {
   SpmmArgs a{};
@@ -502,8 +562,14 @@ int slabs_needed(int dtype, int32_t b, int32_t scols) {
   return (int)ceil_div(b, sc);
 }
 
-cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, int64_t pw) {
+cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, const ChunkPlan &cp, int64_t pw) {
+  if (c.op->spmm_algo == 1) return spmm_chunk_launch(a, c.dtype, cp, c.sc->heavy_partial, pw, c.s);
   return spmm_launch(a, c.dtype, hp, c.sc->heavy_partial, pw, c.s);
+}
+
+int64_t partial_rows(const isvd_operator *op) {
+  return std::max<int64_t>({op->heavy_A.n_chunks, op->heavy_X.n_chunks, op->heavy_XT.n_chunks,
+                            2 * op->chunk_A.nchunks, 2 * op->chunk_X.nchunks, 2 * op->chunk_XT.nchunks, 1});
 }
 
 }  // namespace
@@ -524,7 +590,7 @@ size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool t
   const int r = (op->desc.ones_coeff != 0.0 ? 1 : 0) + op->desc.lr_rank;
   add(sizeof(float) * (size_t)std::max(r, 1) * bseg);
   add(sizeof(double) * (size_t)lowrank_partials(op->n) * std::max(r, 1) * bseg);
-  int64_t chunks = std::max<int64_t>({op->heavy_A.n_chunks, op->heavy_X.n_chunks, op->heavy_XT.n_chunks, 1});
+  const int64_t chunks = partial_rows(op);
   add(sizeof(float) * (size_t)chunks * pw);
   return total;
 }
@@ -547,7 +613,7 @@ void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool tra
   sc->lr_c = (float *)take(sizeof(float) * (size_t)std::max(r, 1) * bseg);
   sc->lr_partial = (double *)take(sizeof(double) * (size_t)lowrank_partials(op->n) * std::max(r, 1) * bseg);
   int64_t pw = op->desc.form == ISVD_FORM_CONCAT ? bseg * (op->desc.L + 1) : bseg;
-  int64_t chunks = std::max<int64_t>({op->heavy_A.n_chunks, op->heavy_X.n_chunks, op->heavy_XT.n_chunks, 1});
+  const int64_t chunks = partial_rows(op);
   sc->heavy_partial = (float *)take(sizeof(float) * (size_t)chunks * pw);
 }
 
@@ -618,7 +684,7 @@ static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int
     }
     if (last) set_lowrank(a);
     add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, axp, ldg);
-    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, bseg));
+    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
     cur = dst;
     ldcur = lddst;
     which ^= 1;
@@ -629,7 +695,7 @@ static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int
     a.scalar = (float)d.adj_coeff;
     a.ax_scalar = 1.f;
     add_slabs(a, dtype, b, scols, 0, G, ldg, out, ldo, out, ldo);
-    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, bseg));
+    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
   }
   return ISVD_OK;
 }
@@ -669,7 +735,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
       if (L == 0) add_slabs(ax, dtype, b, scols, 0, gin, ldg, out, ldo, nullptr, 0);
       else add_slabs(ax, dtype, b, scols, (int32_t)(l * bseg), gin, ldg, seg(l), ldp, nullptr, 0);
     }
-    ISVD_CUDA_TRY(run(ch, ax, op->heavy_X, ldp));
+    ISVD_CUDA_TRY(run(ch, ax, op->heavy_X, op->chunk_X, ldp));
     if (L == 0) return ISVD_OK;
     // Horner over N
     const void *cur = seg(L);
@@ -690,7 +756,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
         a.ax_rowscale = last ? nullptr : op->s;
       }
       add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, seg(l), ldp);
-      ISVD_CUDA_TRY(run(ch, a, op->heavy_A, bseg));
+      ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
       cur = dst;
       ldcur = lddst;
       which ^= 1;
@@ -710,7 +776,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
       a.rowscale = op->s;
     }
     add_slabs(a, dtype, b, scols, 0, cur, ldcur, seg(l), ldp, nullptr, 0);
-    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, bseg));
+    ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
     cur = seg(l);
     ldcur = ldp;
   }
@@ -729,7 +795,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
     char *o = (char *)out + (size_t)l * d.d * ldo * es;
     add_slabs(at, dtype, b, scols, (int32_t)(l * bseg), in, ldi, o, ldo, nullptr, 0);
   }
-  ISVD_CUDA_TRY(run(ch, at, op->heavy_XT, ldp));
+  ISVD_CUDA_TRY(run(ch, at, op->heavy_XT, op->chunk_XT, ldp));
   return ISVD_OK;
 }
 
@@ -804,6 +870,9 @@ void isvd_destroy_operator(isvd_operator *op) {
   free_heavy(op, &op->heavy_A, s);
   free_heavy(op, &op->heavy_X, s);
   free_heavy(op, &op->heavy_XT, s);
+  free_chunks(op, &op->chunk_A, s);
+  free_chunks(op, &op->chunk_X, s);
+  free_chunks(op, &op->chunk_XT, s);
   if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
   cudaStreamSynchronize(s);
   delete op;
@@ -848,14 +917,16 @@ isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
   out->slab_cols_bf16 = op->slab_cols_bf16;
   out->heavy_threshold = op->heavy_A.threshold;
   out->heavy_chunk = op->heavy_A.chunk;
-  out->flags = op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0;
+  out->flags = (op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0) | (op->spmm_algo == 0 ? ISVD_TUNE_ROW_KERNEL : 0);
+  out->chunk_nnz = op->chunk_nnz;
   return ISVD_OK;
 }
 
 isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *stream) {
   if (!op || !t) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
   if (t->slab_cols_f32 < 4 || t->slab_cols_f32 > 128 || t->slab_cols_f32 % 4 || t->slab_cols_bf16 < 8 ||
-      t->slab_cols_bf16 > 256 || t->slab_cols_bf16 % 8 || t->heavy_threshold < 32 || t->heavy_chunk < 32)
+      t->slab_cols_bf16 > 256 || t->slab_cols_bf16 % 8 || t->heavy_threshold < 32 || t->heavy_chunk < 32 ||
+      t->chunk_nnz < 32 || t->chunk_nnz > (1 << 20))
     return fail(ISVD_ERR_INVALID_ARGUMENT, "tuning field out of range");
   cudaStream_t s = (cudaStream_t)stream;
   ISVD_CUDA_TRY(cudaStreamSynchronize(s));
@@ -864,15 +935,20 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
   op->slab_cols_f32 = t->slab_cols_f32;
   op->slab_cols_bf16 = t->slab_cols_bf16;
   op->cache_hints = (t->flags & ISVD_TUNE_CACHE_HINTS) ? 1 : 0;
+  op->spmm_algo = (t->flags & ISVD_TUNE_ROW_KERNEL) ? 0 : 1;
+  op->chunk_nnz = t->chunk_nnz;
   HeavyPlan *plans[3] = {&op->heavy_A, &op->heavy_X, &op->heavy_XT};
   for (HeavyPlan *hp : plans) {
     hp->threshold = t->heavy_threshold;
     hp->chunk = t->heavy_chunk;
   }
   ISVD_TRY(build_heavy(op, op->desc.A.rowptr, op->n, &op->heavy_A, s));
+  ISVD_TRY(build_chunks(op, op->desc.A.rowptr, op->n, op->desc.A.nnz, &op->chunk_A, s));
   if (op->desc.form == ISVD_FORM_CONCAT) {
     ISVD_TRY(build_heavy(op, op->x_rowptr, op->n, &op->heavy_X, s));
     ISVD_TRY(build_heavy(op, op->xt_rowptr, op->desc.d, &op->heavy_XT, s));
+    ISVD_TRY(build_chunks(op, op->x_rowptr, op->n, op->x_nnz, &op->chunk_X, s));
+    ISVD_TRY(build_chunks(op, op->xt_rowptr, op->desc.d, op->x_nnz, &op->chunk_XT, s));
   }
   return ISVD_OK;
 }

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kSmallThreads) chol_inv_kernel(const double *_
   __shared__ int fail;
   __shared__ double trace;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0 && state[2]) atomicExch(&info->status, (int)ISVD_ERR_TIMEOUT);  // a Gram wait gave up
   if (tid == 0) {
     double t = 0.0;
     for (int i = 0; i < l; ++i) t += W[(size_t)i * l + i];

@@ -19,7 +19,7 @@ isvd_status orth_enqueue(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, 
     PassGate g{o.state, pass};
     ISVD_CUDA_TRY(gram_launch(Q, ldq, dt, rows, l, o.gram_partial, o.n_part, o.W, g, s));
     ISVD_CUDA_TRY(chol_inv_launch(o.W, l, rows, dt, o.Rinv, l, nullptr, Racc, o.tmp, o.state, info, pass, s));
-    ISVD_CUDA_TRY(gemm_small_launch(Q, ldq, dt, rows, l, o.Rinv, l, l, true, Q, ldq, dt, g, s));
+    ISVD_CUDA_TRY(gemm_tri_inplace_launch(Q, ldq, dt, rows, l, o.Rinv, l, g, s));
   }
   return ISVD_OK;
 }

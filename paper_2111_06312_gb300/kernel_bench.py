@@ -39,8 +39,10 @@ def _time(fn, reps, flush):
     return [a.elapsed_time(b) for a, b in out]
 
 
-def set_tuning(op, slab32=None, slab16=None, heavy=None, chunk=None, hints=None):
-    t = (C.c_int32 * 5)()
+def set_tuning(op, slab32=None, slab16=None, heavy=None, chunk=None, hints=None, row_kernel=None, chunk_nnz=None):
+    """Read-modify-write of isvd_tuning: [slab_f32, slab_bf16, heavy_threshold,
+    heavy_chunk, flags (1 = L2 hints, 2 = row-group kernel), chunk_nnz]."""
+    t = (C.c_int32 * 6)()
     isvd.lib().isvd_get_tuning.argtypes = [C.c_void_p, C.c_void_p]
     isvd.lib().isvd_set_tuning.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     isvd.lib().isvd_get_tuning(op._handle, t)
@@ -53,7 +55,11 @@ def set_tuning(op, slab32=None, slab16=None, heavy=None, chunk=None, hints=None)
     if chunk:
         t[3] = chunk
     if hints is not None:
-        t[4] = 1 if hints else 0
+        t[4] = (t[4] & ~1) | (1 if hints else 0)
+    if row_kernel is not None:
+        t[4] = (t[4] & ~2) | (2 if row_kernel else 0)
+    if chunk_nnz:
+        t[5] = chunk_nnz
     isvd._check(isvd.lib().isvd_set_tuning(op._handle, t, isvd._stream()), "isvd_set_tuning")
     return list(t)
 
@@ -81,6 +87,8 @@ def main():
     ap.add_argument("--slab", type=int, default=0)
     ap.add_argument("--heavy", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--chunk-nnz", type=int, default=0)
+    ap.add_argument("--row-kernel", action="store_true")
     ap.add_argument("--rows", type=int, default=1_000_000)
     ap.add_argument("--k", type=int, default=128)
     ap.add_argument("--p", type=int, default=16)
@@ -94,21 +102,20 @@ def main():
         op = isvd.graph_operator(g, coeffs=[1.0], check_symmetry=False)
         if a.what == "spmm":
             tun = set_tuning(op, slab32=a.slab or None, slab16=a.slab or None, heavy=a.heavy or None,
-                             chunk=a.chunk or None)
+                             chunk=a.chunk or None, row_kernel=True if a.row_kernel else None,
+                             chunk_nnz=a.chunk_nnz or None)
             r = spmm_case(g, op, a.width, a.dtype, a.reps, flush)
             print(json.dumps({"what": "spmm", "workload": a.workload, "width": a.width, "dtype": a.dtype,
                               "tuning": tun, **r}), flush=True)
         else:
-            slabs = [16, 32, 64, 128] if a.dtype == "f32" else [32, 64, 128, 256]
-            for slab, heavy, hints in [(s_, h_, k_) for s_ in slabs for h_ in (64, 128) for k_ in (0, 1)]:
-                if True:
-                    tun = set_tuning(op, slab32=slab if a.dtype == "f32" else None,
-                                     slab16=slab if a.dtype == "bf16" else None, heavy=heavy, chunk=heavy,
-                                     hints=hints)
-                    r = spmm_case(g, op, a.width, a.dtype, a.reps, flush)
-                    r.pop("all_ms")
-                    print(json.dumps({"what": "spmm", "width": a.width, "dtype": a.dtype, "tuning": tun, **r}),
-                          flush=True)
+            cases = [dict(row_kernel=True, slab32=128, slab16=256, heavy=64, chunk=64, hints=h) for h in (0, 1)]
+            cases += [dict(row_kernel=False, chunk_nnz=cn, hints=h) for cn in (256, 512, 1024, 2048) for h in (0, 1)]
+            for kw in cases:
+                tun = set_tuning(op, **kw)
+                r = spmm_case(g, op, a.width, a.dtype, a.reps, flush)
+                r.pop("all_ms")
+                print(json.dumps({"what": "spmm", "width": a.width, "dtype": a.dtype, "tuning": tun, **r}),
+                      flush=True)
         op.close()
     elif a.what == "orth":
         g = synth.cycle(64)
