@@ -269,6 +269,34 @@ class Operator:
                 raise IsvdError(st, "isvd_svd (device)", "reported by the GPU")
         return U, S, V, info
 
+    # ---- launch shapes of the sparse products ----
+    _TUNING_FIELDS = ("slab_cols_f32", "slab_cols_bf16", "heavy_threshold", "heavy_chunk", "flags", "chunk_nnz")
+
+    def tuning(self) -> dict:
+        t = (C.c_int32 * 6)()
+        lib().isvd_get_tuning.argtypes = [C.c_void_p, C.c_void_p]
+        lib().isvd_get_tuning.restype = C.c_int
+        _check(lib().isvd_get_tuning(self._handle, t), "isvd_get_tuning")
+        d = dict(zip(self._TUNING_FIELDS, list(t)))
+        d["cache_hints"] = bool(d["flags"] & 1)
+        d["kernel"] = "rows" if d["flags"] & 2 else "chunks"
+        return d
+
+    def set_tuning(self, kernel=None, cache_hints=None, **fields):
+        """kernel: 'chunks' (nonzero-balanced) or 'rows' (row groups with hub
+        splitting); other keys as in isvd_tuning."""
+        cur = self.tuning()
+        vals = [int(fields.get(k, cur[k])) for k in self._TUNING_FIELDS]
+        if cache_hints is not None:
+            vals[4] = (vals[4] & ~1) | (1 if cache_hints else 0)
+        if kernel is not None:
+            vals[4] = (vals[4] & ~2) | (2 if kernel == "rows" else 0)
+        t = (C.c_int32 * 6)(*vals)
+        lib().isvd_set_tuning.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib().isvd_set_tuning.restype = C.c_int
+        _check(lib().isvd_set_tuning(self._handle, t, _stream()), "isvd_set_tuning")
+        return self.tuning()
+
     def graph_kernel_nodes(self) -> int:
         """Kernel launches in the graph replayed by the last svd() call."""
         return int(lib().isvd_graph_kernel_nodes(self._handle))

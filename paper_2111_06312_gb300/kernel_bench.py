@@ -130,10 +130,11 @@ def main():
         g = synth.cached(a.workload)
         c5 = (6 - np.arange(1, 6)) / 15.0
         with isvd.graph_operator(g, coeffs=c5, ones_coeff=-0.05) as op:
+            op.set_tuning(kernel="rows" if a.row_kernel else "chunks", chunk_nnz=a.chunk_nnz or 512)
             op.svd(a.k, a.p, a.q, 1, precision=a.precision)
             ts = _time(lambda: op.svd(a.k, a.p, a.q, 1, precision=a.precision, check=False), a.reps, flush)
             print(json.dumps({"what": "svd", "workload": a.workload, "k": a.k, "p": a.p, "q": a.q,
-                              "precision": a.precision, "ms": float(np.median(ts)),
+                              "precision": a.precision, "ms": float(np.median(ts)), "tuning": op.tuning(),
                               "kernels": op.graph_kernel_nodes()}))
 
 

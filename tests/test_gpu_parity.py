@@ -104,13 +104,18 @@ def make_ops(g, norm, K, ones, adj, weighted, lowrank, seed=5):
     return gpu, oracle.graph_operator(g, **kw)
 
 
+KERNELS = ["chunks", "rows"]
+
+
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("b", [1, 3, 42, 144, 200])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_poly_apply_fp32(hub_graph, case, b, transpose):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_poly_apply_fp32(hub_graph, case, b, transpose, kernel):
     g = hub_graph
     gpu, ref = make_ops(g, *case)
     with gpu:
+        gpu.set_tuning(kernel=kernel, chunk_nnz=256)
         G = isvd.gaussian(3, g.n, b)
         Y = gpu.apply(G, transpose=transpose)
         Yr = ref.apply(npy(G), transpose=transpose)
@@ -119,14 +124,32 @@ def test_poly_apply_fp32(hub_graph, case, b, transpose):
 
 
 @pytest.mark.parametrize("case", CASES[:5])
-def test_poly_apply_bf16(hub_graph, case):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_poly_apply_bf16(hub_graph, case, kernel):
     g = hub_graph
     gpu, ref = make_ops(g, *case)
     with gpu:
+        gpu.set_tuning(kernel=kernel)
         G = isvd.gaussian(4, g.n, 72, dtype=torch.bfloat16)
         Y = gpu.apply(G)
         Yr = ref.apply(npy(G))
     assert np.abs(npy(Y) - Yr).max() <= 3e-2 * np.abs(Yr).max()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_apply_empty_rows_and_hubs(kernel):
+    # isolated nodes (no nonzeros) under Â, one hub spanning many chunks
+    g = synth.chung_lu(2000, 9000, 91, max_degree=1200, isolated_self_loops=False)
+    assert (g.degrees() == 0).any() and g.degrees().max() > 600
+    gpu, ref = make_ops(g, "sym", 5, True, False, False, False)
+    with gpu:
+        gpu.set_tuning(kernel=kernel, chunk_nnz=64)
+        for b in (5, 40, 130):
+            for tr in (False, True):
+                G = isvd.gaussian(8, g.n, b)
+                Y = gpu.apply(G, transpose=tr)
+                Yr = ref.apply(npy(G), transpose=tr)
+                assert np.abs(npy(Y) - Yr).max() <= 1e-5 * np.abs(Yr).max()
 
 
 def test_apply_leaves_padding_and_is_deterministic(hub_graph):
@@ -146,7 +169,8 @@ def test_apply_leaves_padding_and_is_deterministic(hub_graph):
 @pytest.mark.parametrize("norm", ["sym", "row"])
 @pytest.mark.parametrize("dense", [False, True])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_concat_apply(hub_graph, L, norm, dense, transpose):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_concat_apply(hub_graph, L, norm, dense, transpose, kernel):
     g = hub_graph
     d = 37
     if dense:
@@ -157,6 +181,7 @@ def test_concat_apply(hub_graph, L, norm, dense, transpose):
         Xg = (d, x.rowptr, x.colidx, x.values)
         Xo = (d, x.rowptr, x.colidx, x.values.astype(np.float64))
     with isvd.graph_operator(g, form="concat", norm=norm, X=Xg, L=L) as gpu:
+        gpu.set_tuning(kernel=kernel, chunk_nnz=128)
         ref = oracle.graph_operator(g, form="concat", norm=norm, X=Xo, L=L)
         r, c = gpu.shape
         assert (r, c) == ref.shape
@@ -245,10 +270,12 @@ def check_svd(gpu_op, ref_op, k, p, q, seed, tol_s=1e-5, tol_angle=1e-3, precisi
     return out
 
 
-def test_svd_ne_small_parity(ne_small):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_svd_ne_small_parity(ne_small, kernel):
     """Cora-sized NE operator: k = 32, oversample 10, 4 power iterations."""
     g = ne_small
     with isvd.graph_operator(g, coeffs=C5, ones_coeff=-LAM) as gpu:
+        gpu.set_tuning(kernel=kernel)
         ref = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
         out = check_svd(gpu, ref, 32, 10, 4, synth.BASE_SEED)
     print(out)
@@ -271,11 +298,13 @@ def test_svd_concat_sparse(hub_graph):
         check_svd(gpu, ref, 16, 10, 4, 23)
 
 
-def test_svd_concat_pubmed_sized():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_svd_concat_pubmed_sized(kernel):
     """Feature-concatenation operator [X | ÂX | Â²X] at n = 19,717, d = 500, k = 64."""
     g, x = synth.workload_concat_graph()
     X = (x.d, x.rowptr, x.colidx, x.values)
     with isvd.graph_operator(g, form="concat", norm="sym", X=X, L=2) as gpu:
+        gpu.set_tuning(kernel=kernel)
         ref = oracle.graph_operator(g, form="concat", norm="sym",
                                     X=(x.d, x.rowptr, x.colidx, x.values.astype(np.float64)), L=2)
         out = check_svd(gpu, ref, 64, 10, 4, synth.BASE_SEED + 1)
