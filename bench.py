@@ -65,19 +65,26 @@ def measured_peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-def recorded_traffic(kernel_src):
-    """dram read+write bytes per launch of the SpMM step, from the committed
-    ncu summary, valid only while the kernel source is unchanged."""
+def kernel_sources_sha1():
+    h = hashlib.sha1()
+    for f in ("spmm.cu", "dense.cu"):
+        with open(os.path.join(ROOT, "paper_2111_06312_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(storage):
+    """dram read+write bytes of one M.Q apply (all its kernels), from the
+    committed ncu summary; valid only while the kernel sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "spmm_ne_large.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(r"traffic_bytes_per_apply_%s:\s*([0-9.eE+]+)" % storage, text)
     h = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
     if not m or not h:
         return None
-    cur = hashlib.sha1(open(kernel_src, "rb").read()).hexdigest()
-    return float(m.group(1)) if cur == h.group(1) else None
+    return float(m.group(1)) if kernel_sources_sha1() == h.group(1) else None
 
 
 class ClockSampler:
@@ -248,6 +255,7 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     evs = []
+    torch.cuda.nvtx.range_push("timed_steps")
     for _ in range(args.steps):
         flush.zero_()  # untimed: leaves no operand of the next step in L2
         e0 = torch.cuda.Event(enable_timing=True)
@@ -256,6 +264,7 @@ def run_ours(args):
         step()
         e1.record(stream)
         evs.append((e0, e1))
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -268,29 +277,36 @@ def run_ours(args):
         ms = float(t.item())
     kernels_per_step = op.graph_kernel_nodes()
 
-    # ---- SpMM step roofline: one sparse product T.Q at the SVD's block width ----
+    # ---- SpMM step roofline: one M.Q apply of this operator at the SVD's block width ----
+    # (K Horner SpMMs with fused epilogues plus the V^T G projection of the all-ones term),
+    # in the storage type of the power iterations
     hbm, _, peak_src = measured_peaks()
-    spmm_op = isvd.graph_operator(g, coeffs=[1.0], device=dev, check_symmetry=False)
-    Q = isvd.gaussian(1, g.n, l, device=dev)
-    Y = isvd.new_block(g.n, l, device=dev)
+    apply_dtype = torch.float32 if args.precision == "fp32" else torch.bfloat16
+    es = 4 if apply_dtype == torch.float32 else 2
+    Q = isvd.gaussian(1, g.n, l, device=dev).to(apply_dtype)
+    Y = torch.empty_like(Q)
     for _ in range(3):
-        spmm_op.apply(Q, out=Y)
+        op.apply(Q, out=Y)
     spmm_t = []
     for _ in range(10):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("roofline_apply")
         a.record(stream)
-        spmm_op.apply(Q, out=Y)
+        op.apply(Q, out=Y)
         b.record(stream)
+        torch.cuda.nvtx.range_pop()
         spmm_t.append((a, b))
     torch.cuda.synchronize()
-    spmm_ms = float(np.mean([a.elapsed_time(b) for a, b in spmm_t]))
-    es = 4
-    alg_bytes = 4 * (g.n + 1) + 4 * g.nnz + 2 * es * g.n * l  # CSR once, block in once, block out once
-    achieved = alg_bytes / (spmm_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(os.path.join(ROOT, "paper_2111_06312_gb300", "csrc", "spmm.cu"))
-    spmm_op.close()
-
+    apply_ms = float(np.mean([a.elapsed_time(b) for a, b in spmm_t]))
+    K = len(c5)
+    csr_bytes = 4 * (g.n + 1) + 4 * g.nnz
+    blk = es * g.n * l
+    # per SpMM: CSR once, input block once, output block once; axpy operand in K-1 of K
+    # steps; plus one read of Q for the projection c = 1^T Q
+    alg_bytes = K * (csr_bytes + 2 * blk) + (K - 1) * blk + blk
+    achieved = alg_bytes / (apply_ms * 1e-3) / 1e9
+    traffic = recorded_traffic("f32" if es == 4 else "bf16")
     # ---- end to end through the public API, host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -336,10 +352,12 @@ def run_ours(args):
                        "l2": "256 MB buffer written between steps (untimed); per-step working set > 3 GB",
                        "construct_ms": construct_ms},
             "step_ms": step_ms,
-            "spmm": {"ms_per_launch": spmm_ms, "algorithmic_bytes": alg_bytes, "gbs": achieved, "width": l},
+            "spmm": {"ms_per_apply": apply_ms, "algorithmic_bytes": alg_bytes, "gbs": achieved, "width": l,
+                     "spmm_per_apply": K, "storage": "f32" if es == 4 else "bf16"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
-                         "kernel": "SpMM step T.Q (spmm_rows + split hub rows), FP32, width %d" % l},
+                         "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " (copy, burst)",
+                         "kernel": "SpMM: one M.Q apply = %d Horner SpMMs (spmm_rows_kernel + split hub rows) "
+                                   "+ projection, width %d" % (K, l)},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(kernels_per_step * args.steps) if kernels_per_step > 0 else None,
             "device_status": st,

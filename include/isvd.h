@@ -175,6 +175,30 @@ ISVD_API isvd_status isvd_svd(isvd_operator *op, int32_t k, int32_t oversample, 
                      isvd_precision precision, float *U, int64_t ldu, float *S, float *V, int64_t ldv,
                      isvd_info *dev_info, void *stream);
 
+/* Many independent rank-k SVDs (Alg. 1 on each problem) in one call: one
+ * CUDA graph whose parallel branches run the problems side by side, so that
+ * small problems together fill the GPU.  The paper has no batched form; each
+ * problem's result equals that of isvd_svd with the same arguments.
+ *   ops[i]   : distinct operators (each owns the workspace its problem uses);
+ *   k[i]     : rank of problem i (HOST array); oversample and iters shared;
+ *   seed + i : start-block seed of problem i;
+ *   U[i], S[i], V[i] : HOST arrays of DEVICE pointers; U[i] is rows_i x k[i]
+ *              and V[i] cols_i x k[i], dense (ld = k[i]); S[i] has k[i] values;
+ *   dev_info : NULL or a DEVICE array of `count` isvd_info, one per problem.
+ * The graph is captured on the first call with a given argument set and
+ * replayed afterwards (the same operators, pointers and sizes).  Inside a
+ * caller's stream capture the branches are forked into that capture.
+ * Errors: INVALID_ARGUMENT (null, repeated operator, k < 1), SHAPE,
+ * UNSUPPORTED (k + oversample > ISVD_MAX_BLOCK), WORKSPACE, CUDA. */
+ISVD_API isvd_status isvd_svd_batched(isvd_operator *const *ops, const int32_t *k, int32_t count,
+                                      int32_t oversample, int32_t iters, uint64_t seed, isvd_precision precision,
+                                      float *const *U, float *const *S, float *const *V, isvd_info *dev_info,
+                                      void *stream);
+
+/* Kernel launches in the graph replayed by this thread's last
+ * isvd_svd_batched call (-1 if none).  Introspection for benchmarks. */
+ISVD_API int64_t isvd_batched_kernel_nodes(void);
+
 /* --- individual steps, exported for verification and reuse --------------- */
 
 /* out[i][j] (rows x cols) = standard normal from Philox4x32-10 (Salmon et al.
@@ -220,6 +244,21 @@ ISVD_API isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t ro
 #define ISVD_NOALLOC_MAX_BLOCK 64
 ISVD_API isvd_status isvd_orthonormalize_noalloc(float *Q, int64_t rows, int32_t l, int64_t ldq, double *R_out,
                                                  isvd_info *dev_info, void *stream);
+
+/* Closed-form weights from a rank-k SVD of M (Sec. 3, Thm. 1): the least-norm
+ * minimiser of ||M W - Y||_F is M^+ Y; with M ~ U diag(S) V^T it is
+ *     W = V diag(S)^+ U^T Y.
+ * All pointers DEVICE, FP32, row-major: U (r x k, ld ldu), S (k), V (c x k,
+ * ld ldv), Y (r x m, ld ldy), W (c x m, ld ldw, written).  r x c is the
+ * operator's shape.  Label matrices with zero rows outside the training set
+ * fit zero targets there; a fit on the training rows alone takes the SVD of
+ * the row-gathered operator instead.  diag(S)^+ inverts S_i > rcond * max(S) and zeroes
+ * the rest.  U^T Y is summed in FP64 across row parts.  1 <= k, m <=
+ * ISVD_MAX_BLOCK.  Workspace from the operator's allocator; asynchronous on
+ * `stream`. */
+ISVD_API isvd_status isvd_closed_form(isvd_operator *op, const float *U, int64_t ldu, const float *S, const float *V,
+                                      int64_t ldv, int32_t k, const float *Y, int64_t ldy, int32_t m, double rcond,
+                                      float *W, int64_t ldw, void *stream);
 
 /* SVD of a small square upper-triangular-or-dense FP64 matrix by one-sided
  * Jacobi on its transpose (the Rayleigh-Ritz step of Alg. 1, done as

@@ -251,6 +251,19 @@ def num_threads() -> int:
     return int(C.CDLL(_LIB_PATH).orc_num_threads())
 
 
+# ---- closed-form training outputs ------------------------------------------
+
+def closed_form(U, S, V, Y, rcond=1e-6):
+    """Thm. 1 (Sec. 3): the least-norm minimiser of ||M W - Y||_F is M^+ Y;
+    with M = U diag(S) V^T (rank k) it is W = V diag(S)^+ U^T Y, where
+    diag(S)^+ inverts S_i > rcond * max(S) and zeroes the rest.  FP64; the
+    two products are numpy matmuls used as library primitives."""
+    U, S, V, Y = (np.asarray(a, dtype=np.float64) for a in (U, S, V, Y))
+    smax = S.max() if S.size else 0.0
+    inv = np.where((S > 0) & (S > rcond * smax), 1.0 / np.where(S > 0, S, 1.0), 0.0)
+    return V @ (inv[:, None] * (U.T @ Y))
+
+
 # ---- metrics ----------------------------------------------------------------
 
 def sin_principal_angles(U_ref, U):

@@ -154,6 +154,12 @@ cudaError_t gemm_small_launch(const void *Q, int64_t ldq, int in_dtype, int64_t 
                               const float *B, int64_t ldb, int32_t w, bool upper, void *out,
                               int64_t ldo, int out_dtype, PassGate g, cudaStream_t s);
 
+// W (c x m) = V S^+ (U^T Y) (Thm. 1).  partial: nparts x k x m FP64; Z: k x m FP32.
+int32_t closed_form_parts(int64_t rows, int32_t k, int32_t m);
+cudaError_t closed_form_launch(const float *U, int64_t ldu, const float *S, const float *V, int64_t ldv, int64_t r,
+                               int64_t c, int32_t k, const float *Y, int64_t ldy, int32_t m, double rcond,
+                               float *W, int64_t ldw, double *partial, int32_t nparts, float *Z, cudaStream_t s);
+
 // ---- small FP64 kernels -------------------------------------------------------
 // Orthonormalisation state block (device, int32[8]):
 //  [0] last pass that needed a shift (0 = none)   [1] breakdown flag
@@ -223,6 +229,8 @@ struct isvd_operator {
   };
   std::vector<GraphEntry> graphs;
   int64_t last_kernel_nodes = -1;
+  uint64_t serial = 0;      // unique per operator in the process
+  uint64_t generation = 0;  // bumped whenever captured graphs become stale
 };
 
 namespace isvd {
@@ -231,6 +239,10 @@ void free_heavy(isvd_operator *op, HeavyPlan *hp, cudaStream_t s);
 void free_chunks(isvd_operator *op, ChunkPlan *cp, cudaStream_t s);
 void op_free(isvd_operator *op, void *p, cudaStream_t s);
 isvd_status ensure_arena(isvd_operator *op, size_t bytes, cudaStream_t s);
+// Drop the operator's captured graphs (workspace moved or launch shapes changed).
+void invalidate_graphs(isvd_operator *op);
+// Drop batched graphs that include the operator with this serial.
+void batched_forget(uint64_t serial);
 
 // Scratch layout for one apply (offsets into a region of the arena).
 struct ApplyScratch {

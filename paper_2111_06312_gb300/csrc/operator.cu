@@ -10,6 +10,8 @@
 #include <cstring>
 #include <string>
 
+#include <atomic>
+
 #include "internal.h"
 
 namespace isvd {
@@ -55,11 +57,15 @@ void op_free(isvd_operator *op, void *p, cudaStream_t s) {
   else cudaFreeAsync(p, s);
 }
 
-isvd_status ensure_arena(isvd_operator *op, size_t bytes, cudaStream_t s) {
-  if (bytes <= op->arena_bytes) return ISVD_OK;
-  // captured graphs point into the old arena
+void invalidate_graphs(isvd_operator *op) {
   for (auto &g : op->graphs) cudaGraphExecDestroy(g.exec);
   op->graphs.clear();
+  ++op->generation;
+}
+
+isvd_status ensure_arena(isvd_operator *op, size_t bytes, cudaStream_t s) {
+  if (bytes <= op->arena_bytes) return ISVD_OK;
+  invalidate_graphs(op);  // captured graphs point into the old arena
   op_free(op, op->arena, s);
   op->arena = nullptr;
   op->arena_bytes = 0;
@@ -833,6 +839,8 @@ isvd_status isvd_create_operator(const isvd_operator_desc *desc, const isvd_allo
   if (!desc || !out) return fail(ISVD_ERR_INVALID_ARGUMENT, "null descriptor or output");
   *out = nullptr;
   isvd_operator *op = new isvd_operator();
+  static std::atomic<uint64_t> next_serial{1};
+  op->serial = next_serial.fetch_add(1);
   op->desc = *desc;
   if (alloc) {
     if (!alloc->alloc || !alloc->free) {
@@ -862,8 +870,8 @@ isvd_status isvd_create_operator(const isvd_operator_desc *desc, const isvd_allo
 void isvd_destroy_operator(isvd_operator *op) {
   if (!op) return;
   cudaDeviceSynchronize();
-  for (auto &g : op->graphs) cudaGraphExecDestroy(g.exec);
-  op->graphs.clear();
+  invalidate_graphs(op);
+  batched_forget(op->serial);
   cudaStream_t s = nullptr;
   op_free(op, op->arena, s);
   for (void *p : op->owned) op_free(op, p, s);
@@ -930,8 +938,7 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
     return fail(ISVD_ERR_INVALID_ARGUMENT, "tuning field out of range");
   cudaStream_t s = (cudaStream_t)stream;
   ISVD_CUDA_TRY(cudaStreamSynchronize(s));
-  for (auto &g : op->graphs) cudaGraphExecDestroy(g.exec);
-  op->graphs.clear();
+  invalidate_graphs(op);
   op->slab_cols_f32 = t->slab_cols_f32;
   op->slab_cols_bf16 = t->slab_cols_bf16;
   op->cache_hints = (t->flags & ISVD_TUNE_CACHE_HINTS) ? 1 : 0;

@@ -3,6 +3,8 @@
 // stream-ordered sequence that is captured once into a CUDA graph.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <vector>
 
 #include "internal.h"
@@ -143,7 +145,106 @@ isvd_status svd_enqueue(isvd_operator *op, const SvdPlan &P, const SvdBufs &b, c
   return ISVD_OK;
 }
 
+int64_t count_kernel_nodes(cudaGraph_t graph) {
+  int64_t kernels = 0;
+  size_t nn = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
+  }
+  return kernels;
+}
+
+// ---- many independent problems in one graph ----------------------------------
+// The problems are spread over kBatchBranches parallel branches of one graph
+// (longest first onto the least-loaded branch), so that small problems,
+// whose kernels fill a fraction of the GPU each, run side by side.
+constexpr int kBatchBranches = 16;
+constexpr size_t kMaxBatchedGraphs = 4;
+
+struct BatchedGraph {
+  std::vector<uint64_t> key;
+  std::vector<uint64_t> serials;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernel_nodes = 0;
+};
+std::mutex g_batched_mu;
+std::vector<BatchedGraph> g_batched;
+thread_local int64_t t_batched_kernel_nodes = -1;
+
+// Side streams and events of one fork/join; released after the capture ends.
+struct Fork {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  ~Fork() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaStream_t t : streams) cudaStreamDestroy(t);
+  }
+};
+
+double problem_cost(const isvd_operator *op, const SvdPlan &P) {
+  const double nnz = (double)op->desc.A.nnz + (double)op->x_nnz;
+  const double deg = op->desc.form == ISVD_FORM_POLY ? std::max(1, op->desc.degree) : op->desc.L + 1;
+  const double dim = (double)(op->rows + op->cols);
+  return (2.0 * P.iters + 2.0) * ((nnz * deg + dim) * P.l + dim * (double)P.l * P.l);
+}
+
+isvd_status batched_enqueue(isvd_operator *const *ops, const std::vector<SvdPlan> &plans,
+                            const std::vector<SvdBufs> &bufs, Fork &fork, cudaStream_t s) {
+  const int count = (int)plans.size();
+  const int B = std::min(count, kBatchBranches);
+  std::vector<int> order(count);
+  std::vector<double> cost(count);
+  for (int i = 0; i < count; ++i) {
+    order[i] = i;
+    cost[i] = problem_cost(ops[i], plans[i]);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<int>> lanes(B);
+  std::vector<double> load(B, 0.0);
+  for (int i : order) {
+    const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lanes[b].push_back(i);
+    load[b] += cost[i];
+  }
+  fork.streams.assign(B, nullptr);
+  fork.events.assign(B + 1, nullptr);
+  for (int b = 0; b <= B; ++b) ISVD_CUDA_TRY(cudaEventCreateWithFlags(&fork.events[b], cudaEventDisableTiming));
+  for (int b = 0; b < B; ++b) ISVD_CUDA_TRY(cudaStreamCreateWithFlags(&fork.streams[b], cudaStreamNonBlocking));
+  ISVD_CUDA_TRY(cudaEventRecord(fork.events[B], s));
+  isvd_status first = ISVD_OK;
+  for (int b = 0; b < B; ++b) {
+    ISVD_CUDA_TRY(cudaStreamWaitEvent(fork.streams[b], fork.events[B], 0));
+    for (int i : lanes[b]) {
+      if (first != ISVD_OK) break;
+      first = svd_enqueue(ops[i], plans[i], bufs[i], fork.streams[b]);
+    }
+    // join every branch, also after a failure, so that a capture can end
+    ISVD_CUDA_TRY(cudaEventRecord(fork.events[b], fork.streams[b]));
+    ISVD_CUDA_TRY(cudaStreamWaitEvent(s, fork.events[b], 0));
+  }
+  return first;
+}
+
 }  // namespace
+
+void batched_forget(uint64_t serial) {
+  std::lock_guard<std::mutex> lk(g_batched_mu);
+  for (size_t i = 0; i < g_batched.size();) {
+    BatchedGraph &e = g_batched[i];
+    if (std::find(e.serials.begin(), e.serials.end(), serial) != e.serials.end()) {
+      cudaGraphExecDestroy(e.exec);
+      g_batched.erase(g_batched.begin() + (std::ptrdiff_t)i);
+    } else {
+      ++i;
+    }
+  }
+}
+
 }  // namespace isvd
 
 using namespace isvd;
@@ -209,18 +310,7 @@ isvd_status isvd_svd(isvd_operator *op, int32_t k, int32_t oversample, int32_t i
     if (graph) cudaGraphDestroy(graph);
     return fail(ISVD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
   }
-  int64_t kernels = 0;
-  {
-    size_t nn = 0;
-    if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
-      std::vector<cudaGraphNode_t> nodes(nn);
-      if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
-        for (size_t i = 0; i < nn; ++i) {
-          cudaGraphNodeType t;
-          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
-        }
-    }
-  }
+  const int64_t kernels = count_kernel_nodes(graph);
   cudaGraphExec_t exec = nullptr;
   const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
@@ -240,6 +330,108 @@ isvd_status isvd_svd(isvd_operator *op, int32_t k, int32_t oversample, int32_t i
 }
 
 int64_t isvd_graph_kernel_nodes(const isvd_operator *op) { return op ? op->last_kernel_nodes : -1; }
+
+isvd_status isvd_svd_batched(isvd_operator *const *ops, const int32_t *k, int32_t count, int32_t oversample,
+                             int32_t iters, uint64_t seed, isvd_precision precision, float *const *U,
+                             float *const *S, float *const *V, isvd_info *dev_info, void *stream) {
+  if (!ops || !k || !U || !S || !V || count < 1) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument or count < 1");
+  if (oversample < 0 || iters < 0) return fail(ISVD_ERR_INVALID_ARGUMENT, "need oversample >= 0, iters >= 0");
+  if (precision != ISVD_PREC_FP32 && precision != ISVD_PREC_MIXED)
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown precision");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::set<const isvd_operator *> seen;
+  std::vector<SvdPlan> plans(count);
+  std::vector<SvdBufs> bufs(count);
+  std::vector<uint64_t> key = {(uint64_t)count, (uint64_t)oversample, (uint64_t)iters, seed, (uint64_t)precision,
+                               (uint64_t)(uintptr_t)dev_info};
+  std::vector<uint64_t> serials(count);
+  for (int i = 0; i < count; ++i) {
+    isvd_operator *op = ops[i];
+    if (!op || !U[i] || !S[i] || !V[i]) return fail(ISVD_ERR_INVALID_ARGUMENT, "null pointer for problem %d", i);
+    if (!seen.insert(op).second)
+      return fail(ISVD_ERR_INVALID_ARGUMENT, "problem %d repeats an operator (each needs its own workspace)", i);
+    const int64_t l = (int64_t)k[i] + oversample;
+    if (k[i] < 1) return fail(ISVD_ERR_INVALID_ARGUMENT, "problem %d: k < 1", i);
+    if (l > ISVD_MAX_BLOCK) return fail(ISVD_ERR_UNSUPPORTED, "problem %d: k + oversample > %d", i, ISVD_MAX_BLOCK);
+    if (l > std::min(op->rows, op->cols))
+      return fail(ISVD_ERR_SHAPE, "problem %d: k + oversample exceeds min(rows, cols)", i);
+    SvdPlan &P = plans[i];
+    P.k = k[i];
+    P.p = oversample;
+    P.l = (int32_t)l;
+    P.ld = (int32_t)round_up(l, 8);
+    P.iters = iters;
+    P.seed = seed + (uint64_t)i;
+    P.prec = precision;
+    P.U = U[i];
+    P.S = S[i];
+    P.V = V[i];
+    P.ldu = k[i];
+    P.ldv = k[i];
+    P.info = dev_info ? dev_info + i : nullptr;
+    const size_t bytes = carve_svd(op, P, nullptr, &bufs[i]);
+    ISVD_TRY(ensure_arena(op, bytes, s));
+    carve_svd(op, P, (char *)op->arena, &bufs[i]);
+  }
+  for (int i = 0; i < count; ++i) {
+    const isvd_operator *op = ops[i];
+    serials[i] = op->serial;
+    const uint64_t e[7] = {op->serial, op->generation, (uint64_t)k[i], (uint64_t)(uintptr_t)U[i],
+                           (uint64_t)(uintptr_t)S[i], (uint64_t)(uintptr_t)V[i], (uint64_t)(uintptr_t)op->arena};
+    key.insert(key.end(), e, e + 7);
+  }
+
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  ISVD_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) {  // the caller is capturing: fork inside its graph
+    Fork fork;
+    return batched_enqueue(ops, plans, bufs, fork, s);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_batched_mu);
+    for (BatchedGraph &g : g_batched)
+      if (g.key == key) {
+        t_batched_kernel_nodes = g.kernel_nodes;
+        ISVD_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+        return ISVD_OK;
+      }
+  }
+  cudaStream_t cs = ops[0]->capture_stream;
+  cudaGraph_t graph = nullptr;
+  isvd_status st;
+  cudaError_t ce;
+  {
+    Fork fork;
+    ISVD_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    st = batched_enqueue(ops, plans, bufs, fork, cs);
+    ce = cudaStreamEndCapture(cs, &graph);
+  }
+  if (st != ISVD_OK || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (st != ISVD_OK) return st;
+    return fail(ISVD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+  }
+  BatchedGraph e;
+  e.key = key;
+  e.serials = serials;
+  e.kernel_nodes = count_kernel_nodes(graph);
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return fail(ISVD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+  t_batched_kernel_nodes = e.kernel_nodes;
+  ISVD_CUDA_TRY(cudaGraphLaunch(e.exec, s));
+  std::lock_guard<std::mutex> lk(g_batched_mu);
+  if (g_batched.size() >= kMaxBatchedGraphs) {
+    cudaGraphExecDestroy(g_batched.front().exec);
+    g_batched.erase(g_batched.begin());
+  }
+  g_batched.push_back(std::move(e));
+  return ISVD_OK;
+}
+
+int64_t isvd_batched_kernel_nodes(void) { return t_batched_kernel_nodes; }
+
+
 
 isvd_status isvd_gaussian(uint64_t seed, int64_t rows, int32_t cols, void *out, int64_t ld, isvd_dtype dtype,
                           void *stream) {
@@ -272,6 +464,29 @@ isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t rows, int32
   isvd_info *info = dev_info ? dev_info : own;
   if (!dev_info) ISVD_CUDA_TRY(cudaMemsetAsync(own, 0, sizeof(isvd_info), s));
   return orth_enqueue(Q, ldq, DT_F32, rows, l, R_out, o, info, s);
+}
+
+isvd_status isvd_closed_form(isvd_operator *op, const float *U, int64_t ldu, const float *S, const float *V,
+                             int64_t ldv, int32_t k, const float *Y, int64_t ldy, int32_t m, double rcond, float *W,
+                             int64_t ldw, void *stream) {
+  if (!op || !U || !S || !V || !Y || !W) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (k < 1 || k > ISVD_MAX_BLOCK || m < 1 || m > ISVD_MAX_BLOCK)
+    return fail(ISVD_ERR_SHAPE, "need 1 <= k, m <= %d", ISVD_MAX_BLOCK);
+  if (k > std::min(op->rows, op->cols)) return fail(ISVD_ERR_SHAPE, "k exceeds min(rows, cols)");
+  if (ldu < k || ldv < k || ldy < m || ldw < m) return fail(ISVD_ERR_INVALID_ARGUMENT, "leading dimension too small");
+  if (!(rcond >= 0.0)) return fail(ISVD_ERR_INVALID_ARGUMENT, "rcond must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t parts = closed_form_parts(op->rows, k, m);
+  Carver c{nullptr};
+  c.take<double>((size_t)parts * k * m);
+  c.take<float>((size_t)k * m);
+  ISVD_TRY(ensure_arena(op, c.off, s));
+  Carver c2{(char *)op->arena};
+  double *partial = c2.take<double>((size_t)parts * k * m);
+  float *Z = c2.take<float>((size_t)k * m);
+  ISVD_CUDA_TRY(closed_form_launch(U, ldu, S, V, ldv, op->rows, op->cols, k, Y, ldy, m, rcond, W, ldw, partial, parts,
+                                   Z, s));
+  return ISVD_OK;
 }
 
 isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double *Uo, double *S, double *Vo,

@@ -105,6 +105,10 @@ def lib():
             L.isvd_philox_words.argtypes = [U64, I64, P, P]
             L.isvd_orthonormalize.argtypes = [P, P, I64, I32, I64, P, P, P]
             L.isvd_small_svd.argtypes = [P, P, I32, P, P, P, P, P]
+            L.isvd_closed_form.argtypes = [P, P, I64, P, P, I64, I32, P, I64, I32, C.c_double, P, I64, P]
+            L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
+            L.isvd_batched_kernel_nodes.argtypes = []
+            L.isvd_batched_kernel_nodes.restype = C.c_int64
             L.isvd_graph_kernel_nodes.argtypes = [P]
             L.isvd_graph_kernel_nodes.restype = C.c_int64
             L.isvd_status_string.argtypes = [C.c_int]
@@ -112,7 +116,8 @@ def lib():
             L.isvd_last_error.argtypes = []
             L.isvd_last_error.restype = C.c_char_p
             for name in ("isvd_create_operator", "isvd_operator_shape", "isvd_apply", "isvd_apply_T", "isvd_svd",
-                         "isvd_gaussian", "isvd_philox_words", "isvd_orthonormalize", "isvd_small_svd"):
+                         "isvd_gaussian", "isvd_philox_words", "isvd_orthonormalize", "isvd_small_svd",
+                         "isvd_closed_form", "isvd_svd_batched"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -368,3 +373,63 @@ def small_svd(op: Operator, A: torch.Tensor):
     _check(lib().isvd_small_svd(op._handle, _ptr(A), l, _ptr(U), _ptr(S), _ptr(V), None, _stream()),
            "isvd_small_svd")
     return U, S, V
+
+
+def closed_form(op: Operator, U: torch.Tensor, S: torch.Tensor, V: torch.Tensor, Y: torch.Tensor,
+                rcond: float = 1e-6, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Least-norm weights W = V diag(S)^+ U^T Y from a rank-k SVD of M
+    (Thm. 1)."""
+    for t in (U, S, V, Y):
+        if t.dtype != torch.float32 or not t.is_cuda:
+            raise TypeError("closed_form takes FP32 CUDA tensors")
+    r, c = op.shape
+    k = S.numel()
+    m = Y.shape[1]
+    if U.shape != (r, k) or V.shape != (c, k) or Y.shape[0] != r:
+        raise ValueError("U, S, V, Y do not match the operator's shape")
+    U, V, Y = _as_block(U), _as_block(V), _as_block(Y)
+    S = S.contiguous()
+    W = new_block(c, m, device=U.device) if out is None else out
+    _check(lib().isvd_closed_form(op._handle, _ptr(U), U.stride(0), _ptr(S), _ptr(V), V.stride(0), k, _ptr(Y),
+                                  Y.stride(0), m, float(rcond), _ptr(W), W.stride(0), _stream()), "isvd_closed_form")
+    return W
+
+
+class Batch:
+    """Many independent rank-k SVDs in one call (isvd_svd_batched).  Output
+    buffers are allocated once and reused, so that repeated calls replay one
+    captured graph."""
+
+    def __init__(self, ops, ks, oversample: int = 10, iters: int = 4, seed: int = 0, precision: str = "fp32"):
+        if len(ops) != len(ks) or not ops:
+            raise ValueError("need one rank per operator")
+        self.ops = list(ops)
+        self.ks = [int(k) for k in ks]
+        self.oversample, self.iters, self.seed, self.precision = int(oversample), int(iters), int(seed), precision
+        dev = self.ops[0].device
+        self.U = [torch.zeros((op.shape[0], k), dtype=torch.float32, device=dev) for op, k in zip(self.ops, self.ks)]
+        self.V = [torch.zeros((op.shape[1], k), dtype=torch.float32, device=dev) for op, k in zip(self.ops, self.ks)]
+        self.S = [torch.zeros(k, dtype=torch.float32, device=dev) for k in self.ks]
+        self.info = torch.zeros((len(self.ops), 4), dtype=torch.int32, device=dev)
+        n = len(self.ops)
+        self._h_ops = (C.c_void_p * n)(*[op._handle.value for op in self.ops])
+        self._h_k = (C.c_int32 * n)(*self.ks)
+        self._h_U = (C.c_void_p * n)(*[t.data_ptr() for t in self.U])
+        self._h_S = (C.c_void_p * n)(*[t.data_ptr() for t in self.S])
+        self._h_V = (C.c_void_p * n)(*[t.data_ptr() for t in self.V])
+
+    def run(self, check: bool = True):
+        _check(lib().isvd_svd_batched(self._h_ops, self._h_k, len(self.ops), self.oversample, self.iters,
+                                      C.c_uint64(self.seed), PREC[self.precision], self._h_U, self._h_S, self._h_V,
+                                      _ptr(self.info), _stream()), "isvd_svd_batched")
+        if check:
+            torch.cuda.current_stream().synchronize()
+            bad = torch.nonzero(self.info[:, 0]).reshape(-1).tolist()
+            if bad:
+                st = int(self.info[bad[0], 0])
+                raise IsvdError(st, f"isvd_svd_batched (device, problem {bad[0]})", "reported by the GPU")
+        return self.U, self.S, self.V
+
+    @staticmethod
+    def kernel_nodes() -> int:
+        return int(lib().isvd_batched_kernel_nodes())

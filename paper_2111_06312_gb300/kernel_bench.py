@@ -5,6 +5,10 @@
   python -m paper_2111_06312_gb300.kernel_bench sweep [--workload ne_large] [--width 144] [--dtype f32]
   python -m paper_2111_06312_gb300.kernel_bench orth  [--rows 1000000] [--width 144] [--reps 5]
   python -m paper_2111_06312_gb300.kernel_bench svd   [--workload ne_large] [--k 128 --p 16 --q 6]
+                                                      [--kernel rows|chunks] [--precision fp32|mixed]
+  python -m paper_2111_06312_gb300.kernel_bench equal_error [--workload ne_large] [--k 128 --p 16 --q 6]
+  python -m paper_2111_06312_gb300.kernel_bench batched [--count 256]
+  python -m paper_2111_06312_gb300.kernel_bench finetune [--epochs 20]
 
 Each prints one JSON line per measured configuration (CUDA events on the
 launching stream, L2 written over between repetitions).
@@ -18,7 +22,7 @@ import json
 import numpy as np
 import torch
 
-from . import build, isvd, synth
+from . import adjoint, build, isvd, synth
 
 
 def _flush(buf):
@@ -79,7 +83,7 @@ def spmm_case(g, op, width, dtype, reps, flush):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["spmm", "sweep", "orth", "svd"])
+    ap.add_argument("what", choices=["spmm", "sweep", "orth", "svd", "equal_error", "batched", "finetune"])
     ap.add_argument("--workload", default="ne_large")
     ap.add_argument("--width", type=int, default=144)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
@@ -94,6 +98,11 @@ def main():
     ap.add_argument("--p", type=int, default=16)
     ap.add_argument("--q", type=int, default=6)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--kernel", default=None, choices=["rows", "chunks"])
+    ap.add_argument("--count", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--q-ref", type=int, default=0)
+    ap.add_argument("--q-extra", type=int, default=4)
     a = ap.parse_args()
     build.build()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -126,16 +135,152 @@ def main():
         ts = _time(lambda: (Q.copy_(Q0), isvd.orthonormalize(op, Q, want_r=False)), a.reps, flush)
         print(json.dumps({"what": "orth", "rows": a.rows, "width": a.width, "ms_incl_copy": float(np.median(ts))}))
         op.close()
-    else:
+    elif a.what == "svd":
         g = synth.cached(a.workload)
-        c5 = (6 - np.arange(1, 6)) / 15.0
-        with isvd.graph_operator(g, coeffs=c5, ones_coeff=-0.05) as op:
-            op.set_tuning(kernel="rows" if a.row_kernel else "chunks", chunk_nnz=a.chunk_nnz or 512)
+        with isvd.graph_operator(g, coeffs=C5, ones_coeff=-LAM) as op:
+            if a.kernel:
+                op.set_tuning(kernel=a.kernel, chunk_nnz=a.chunk_nnz or 512)
             op.svd(a.k, a.p, a.q, 1, precision=a.precision)
             ts = _time(lambda: op.svd(a.k, a.p, a.q, 1, precision=a.precision, check=False), a.reps, flush)
             print(json.dumps({"what": "svd", "workload": a.workload, "k": a.k, "p": a.p, "q": a.q,
                               "precision": a.precision, "ms": float(np.median(ts)), "tuning": op.tuning(),
                               "kernels": op.graph_kernel_nodes()}))
+    elif a.what == "equal_error":
+        equal_error(a, flush)
+    elif a.what == "batched":
+        batched(a, flush)
+    else:
+        finetune(a, flush)
+
+
+C5 = (6 - np.arange(1, 6)) / 15.0
+LAM = 0.05
+
+
+def _gapped_prefix(S_ref, k, rel_gap=1e-3):
+    """Largest k' <= k with sigma_k' - sigma_k'+1 > rel_gap * sigma_1 (0 if none)."""
+    s = S_ref.double().cpu().numpy()
+    best = 0
+    for j in range(1, min(k, len(s) - 1) + 1):
+        if s[j - 1] - s[j] > rel_gap * s[0]:
+            best = j
+    return best
+
+
+def _max_angle(U_ref, U, kp):
+    """Largest principal angle between the spans of the first kp columns."""
+    if kp == 0:
+        return 0.0
+    A = U_ref[:, :kp].double()
+    B = U[:, :kp].double()
+    P = B - A @ (A.T @ B)
+    ev = torch.linalg.eigvalsh(P.T @ P).clamp_min(0)
+    return float(torch.asin(torch.sqrt(ev.max()).clamp(max=1.0)))
+
+
+def equal_error(a, flush):
+    """Mixed vs FP32 at equal error: the FP32 run at q sets the target error
+    (max principal angle of the gapped top-k left subspace and max relative
+    singular-value error, both against an FP32 run with many more power
+    iterations); the mixed run takes the smallest q' >= q that meets it."""
+    g = synth.cached(a.workload)
+    q_ref = a.q_ref or 4 * a.q
+    with isvd.graph_operator(g, coeffs=C5, ones_coeff=-LAM) as op:
+        U_ref, S_ref, _, _ = op.svd(a.k, a.p, q_ref, 7)
+        U_ref, S_ref = U_ref.clone(), S_ref.clone()
+        kp = _gapped_prefix(S_ref, a.k)
+
+        def run(prec, q):
+            U, S, V, info = op.svd(a.k, a.p, q, 1, precision=prec)
+            ang = _max_angle(U_ref, U, kp)
+            serr = float(((S.double() - S_ref.double()).abs() / S_ref.double()[0]).max())
+            ts = _time(lambda: op.svd(a.k, a.p, q, 1, precision=prec, check=False), a.reps, flush)
+            return {"precision": prec, "q": q, "angle": ang, "sigma_err": serr, "ms": float(np.median(ts))}
+
+        base = run("fp32", a.q)
+        rows = [base]
+        chosen = None
+        for q in range(a.q, a.q + a.q_extra + 1):
+            r = run("mixed", q)
+            rows.append(r)
+            if chosen is None and r["angle"] <= base["angle"] * 1.0001 and r["sigma_err"] <= base["sigma_err"] * 1.0001:
+                chosen = r
+                break
+        out = {"what": "equal_error", "workload": a.workload, "k": a.k, "p": a.p, "q": a.q, "q_ref": q_ref,
+               "gapped_prefix": kp, "runs": rows, "fp32": base, "mixed_at_equal_error": chosen,
+               "speedup": (base["ms"] / chosen["ms"]) if chosen else None}
+        print(json.dumps(out), flush=True)
+
+
+def batched(a, flush):
+    """Many small problems: one isvd_svd_batched call vs one isvd_svd call each."""
+    graphs, ranks = synth.workload_batched(count=a.count)
+    ops = [isvd.graph_operator(gr, coeffs=C5, ones_coeff=-LAM) for gr in graphs]
+    try:
+        batch = isvd.Batch(ops, ranks, oversample=10, iters=4, seed=20211106315)
+        batch.run()
+        t_batch = _time(lambda: batch.run(check=False), a.reps, flush)
+        outs = [(isvd.new_block(op.shape[0], k), isvd.new_block(op.shape[1], k), torch.empty(k, device="cuda"))
+                for op, k in zip(ops, ranks)]
+        info = torch.zeros(4, dtype=torch.int32, device="cuda")
+
+        def singles():
+            for i, (op, k) in enumerate(zip(ops, ranks)):
+                U, V, S = outs[i]
+                op.svd(k, 10, 4, seed=20211106315 + i, U=U, S=S, V=V, info=info, check=False)
+
+        singles()
+        torch.cuda.synchronize()
+        t_single = _time(singles, a.reps, flush)
+        print(json.dumps({"what": "batched", "count": len(ops), "sum_n": int(sum(gr.n for gr in graphs)),
+                          "sum_nnz": int(sum(gr.nnz for gr in graphs)), "ranks": np.bincount(ranks).tolist(),
+                          "batched_ms": float(np.median(t_batch)), "single_calls_ms": float(np.median(t_single)),
+                          "kernels": isvd.Batch.kernel_nodes()}), flush=True)
+    finally:
+        for op in ops:
+            op.close()
+
+
+def finetune(a, flush):
+    """Linear model Y = M W on M = [X | ÂX | Â^2 X] (ogbn-arxiv-sized shapes):
+    closed-form start from a rank-40 iSVD, then epochs of forward, cross-entropy
+    on the training rows, backward (M^T dY) and an Adam step."""
+    g, x, y, train = synth.workload_finetune()
+    with isvd.Operator(g.n, g.rowptr, g.colidx, form="concat", norm="sym", X=x, L=2) as op:
+        labels = torch.as_tensor(y).cuda()
+        mask = torch.as_tensor(train).cuda()
+        idx = torch.nonzero(mask).reshape(-1)
+        Ylab = adjoint.one_hot_train(labels, mask, 40)
+        adjoint.closed_form_init(op, Ylab, k=40, oversample=10, iters=4, seed=4)
+        t_init = _time(lambda: adjoint.closed_form_init(op, Ylab, k=40, oversample=10, iters=4, seed=4), a.reps,
+                       flush)
+        W0, _ = adjoint.closed_form_init(op, Ylab, k=40, oversample=10, iters=4, seed=4)
+        model = adjoint.ImplicitLinear(op, W0)
+        opt = torch.optim.Adam(model.parameters(), lr=1e-3)
+        f = torch.nn.functional.cross_entropy
+
+        def epoch():
+            opt.zero_grad()
+            loss = f(model()[idx], labels[idx])
+            loss.backward()
+            opt.step()
+            return loss
+
+        acc0 = float((model().argmax(1)[idx] == labels[idx]).float().mean())
+        for _ in range(3):
+            epoch()
+        t_epoch = _time(epoch, a.epochs, flush)
+        r, c = op.shape
+        W = W0.clone()
+        dY = torch.randn((r, 40), device="cuda")
+        Yb = isvd.new_block(r, 40)
+        dWb = isvd.new_block(c, 40)
+        t_fwd = _time(lambda: op.apply(W, out=Yb), a.reps, flush)
+        t_bwd = _time(lambda: op.apply(dY, out=dWb, transpose=True), a.reps, flush)
+        print(json.dumps({"what": "finetune", "n": g.n, "nnz": g.nnz, "d": x.shape[1], "outputs": 40,
+                          "init_ms": float(np.median(t_init)), "epoch_ms": float(np.median(t_epoch)),
+                          "forward_ms": float(np.median(t_fwd)), "backward_ms": float(np.median(t_bwd)),
+                          "train_acc_at_init": acc0}), flush=True)
 
 
 if __name__ == "__main__":

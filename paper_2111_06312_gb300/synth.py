@@ -217,6 +217,36 @@ def induced_subgraph(g: Graph, nodes: np.ndarray, isolated_self_loops: bool = Tr
     return _pairs_to_csr(len(nodes), a, b, loops)
 
 
+def bfs_ball(g: Graph, size: int, root: int | None = None) -> np.ndarray:
+    """The first ``size`` nodes reached by breadth-first search from ``root``
+    (default: a node of median degree), continuing from the next unvisited
+    node when a component is exhausted."""
+    deg = np.diff(g.rowptr)
+    start = int(np.argsort(deg, kind="stable")[g.n // 2]) if root is None else int(root)
+    seen = np.zeros(g.n, dtype=bool)
+    order = []
+    nxt = 0
+    frontier = [start]
+    seen[start] = True
+    while len(order) < size:
+        if not frontier:
+            while seen[nxt]:
+                nxt += 1
+            seen[nxt] = True
+            frontier = [nxt]
+        new = []
+        for v in frontier:
+            order.append(v)
+            if len(order) == size:
+                break
+            nb = g.colidx[g.rowptr[v]:g.rowptr[v + 1]]
+            nb = nb[~seen[nb]]
+            seen[nb] = True
+            new.extend(nb.tolist())
+        frontier = new
+    return np.asarray(order[:size], dtype=np.int64)
+
+
 # ---- the five workload recipes ------------------------------------------------
 
 def workload_ne_small(seed_offset: int = 0) -> Graph:
@@ -279,3 +309,11 @@ def workload_finetune(n: int = 169_343, m: int = 1_166_243, d: int = 128, classe
     x = dense_features(n, d, BASE_SEED + 4 + 1000)
     y, train = labels(n, classes, 0.10, BASE_SEED + 4 + 2000)
     return g, x, y, train
+
+
+def workload_finetune_sub(size: int = 2000):
+    """Induced subgraph of the ogbn-arxiv-sized graph on a ``size``-node BFS
+    ball, with the matching feature rows and labels."""
+    g, x, y, train = workload_finetune()
+    nodes = bfs_ball(g, size)
+    return induced_subgraph(g, nodes, isolated_self_loops=False), x[nodes], y[nodes], train[nodes]
