@@ -65,26 +65,34 @@ def measured_peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-def kernel_sources_sha1():
+KERNEL_SOURCES = {
+    "rows": ("spmm.cu", "dense.cu"),
+    "ring": ("spmm_ring.cu", "dense.cu"),
+    "chunks": ("spmm_chunk.cu", "dense.cu"),
+}
+
+
+def kernel_sources_sha1(kernel):
     h = hashlib.sha1()
-    for f in ("spmm.cu", "dense.cu"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2111_06312_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def recorded_traffic(storage):
-    """dram read+write bytes of one M.Q apply (all its kernels), from the
-    committed ncu summary; valid only while the kernel sources are unchanged."""
+def recorded_traffic(storage, kernel):
+    """dram read+write bytes of one M.Q apply (all its kernels) with the given
+    SpMM kernel, from the committed ncu summary; valid only while the sources
+    of those kernels are unchanged."""
     path = os.path.join(ROOT, "profiles", "spmm_ne_large.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_apply_%s:\s*([0-9.eE+]+)" % storage, text)
-    h = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
+    m = re.search(r"traffic_bytes_per_apply_%s_%s:\s*([0-9.eE+]+)" % (storage, kernel), text)
+    h = re.search(r"source_sha1_%s:\s*([0-9a-f]{40})" % kernel, text)
     if not m or not h:
         return None
-    return float(m.group(1)) if kernel_sources_sha1() == h.group(1) else None
+    return float(m.group(1)) if kernel_sources_sha1(kernel) == h.group(1) else None
 
 
 class ClockSampler:
@@ -146,7 +154,7 @@ class ClockSampler:
 # CPU oracle sample (the reference arm and the cpu_baseline of our arm)
 # ---------------------------------------------------------------------------------------------
 
-def oracle_sample(g, k, p, q, b_sample=16):
+def oracle_sample(g, k, p, q, b_sample=32):
     """Time the FP64 oracle on a bounded sample of the same workload and scale
     to one whole SVD: one forward and one transposed product M G, M^T G at
     block width b_sample (cost proportional to the width) and one CholeskyQR2
@@ -306,7 +314,8 @@ def run_ours(args):
     # steps; plus one read of Q for the projection c = 1^T Q
     alg_bytes = K * (csr_bytes + 2 * blk) + (K - 1) * blk + blk
     achieved = alg_bytes / (apply_ms * 1e-3) / 1e9
-    traffic = recorded_traffic("f32" if es == 4 else "bf16")
+    kernel = op.tuning()["kernel"]
+    traffic = recorded_traffic("f32" if es == 4 else "bf16", kernel)
     # ---- end to end through the public API, host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -356,8 +365,8 @@ def run_ours(args):
                      "spmm_per_apply": K, "storage": "f32" if es == 4 else "bf16"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " (copy, burst)",
-                         "kernel": "SpMM: one M.Q apply = %d Horner SpMMs (spmm_rows_kernel + split hub rows) "
-                                   "+ projection, width %d" % (K, l)},
+                         "kernel": "SpMM: one M.Q apply = %d Horner SpMMs (%s kernel) + projection, width %d"
+                                   % (K, kernel, l)},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(kernels_per_step * args.steps) if kernels_per_step > 0 else None,
             "device_status": st,

@@ -278,12 +278,17 @@ typedef struct {
   int32_t heavy_threshold; /* >= 32 */
   int32_t heavy_chunk;     /* >= 32 */
   int32_t flags;           /* ISVD_TUNE_* */
-  int32_t chunk_nnz;       /* nonzeros per warp chunk of the balanced kernel, 32..2^20 */
+  int32_t chunk_nnz;       /* nonzeros per warp chunk of the balanced kernels, 32..2^20 */
 } isvd_tuning;
 
+/* The sparse-product kernel: ISVD_TUNE_ROW_KERNEL (row groups with hub
+ * splitting), ISVD_TUNE_RING_KERNEL (nonzero chunks, full-width gathers
+ * streamed through shared memory; takes precedence), neither: nonzero chunks
+ * over narrow column slabs. */
 enum {
-  ISVD_TUNE_CACHE_HINTS = 1, /* L2 eviction priorities: keep gathered rows, stream the rest */
-  ISVD_TUNE_ROW_KERNEL = 2   /* row groups with hub splitting instead of nonzero chunks */
+  ISVD_TUNE_CACHE_HINTS = 1, /* L2 eviction priorities: keep gathered (hub) rows, stream the rest */
+  ISVD_TUNE_ROW_KERNEL = 2,
+  ISVD_TUNE_RING_KERNEL = 4
 };
 
 /* Read / replace the operator's launch shapes.  isvd_set_tuning rebuilds the

@@ -121,6 +121,23 @@ cudaError_t spmm_chunk_launch(const SpmmArgs &a, int dtype, const ChunkPlan &cp,
                               cudaStream_t s);
 int chunk_slab_cols(int dtype);
 
+// Ring form (spmm_ring.cu): the same chunk plan, full-width gathers streamed
+// through shared memory with cp.async.  One slab per launch (a.nslabs == 1)
+// of at most ring_max_cols(dtype) columns.  Column tags: colidx with the
+// column's degree bucket floor(log2 deg) in bits 26..30 (n < 2^26), and the
+// number of columns per bucket; gathers of the hottest buckets whose rows fit
+// l2_budget bytes get the L2 evict_last policy.
+constexpr size_t kRingSmemBudget = 200 * 1024;
+constexpr int64_t kRingL2Budget = 96ll << 20;
+struct RingTags {
+  const int32_t *tagged = nullptr;
+  int64_t hist[32] = {};
+  int64_t l2_budget = 0;
+};
+int ring_max_cols(int dtype);
+cudaError_t spmm_ring_launch(const SpmmArgs &a, int dtype, const ChunkPlan &cp, const RingTags &tags, float *part,
+                             int64_t pw, cudaStream_t s);
+
 // ---- dense helpers -----------------------------------------------------------
 cudaError_t gaussian_launch(uint64_t seed, int64_t rows, int32_t cols, void *out, int64_t ld, int dtype,
                             cudaStream_t s);
@@ -213,7 +230,8 @@ struct isvd_operator {
   int64_t x_nnz = 0;
   isvd::HeavyPlan heavy_A, heavy_X, heavy_XT;
   isvd::ChunkPlan chunk_A, chunk_X, chunk_XT;
-  int32_t spmm_algo = 0;    // 1: nonzero-balanced chunks, 0: row groups with hub splitting
+  isvd::RingTags tags_A;    // degree-bucket tags of A's columns (ring form)
+  int32_t spmm_algo = 0;    // 0: row groups with hub splitting, 1: nonzero chunks, 2: ring
   int32_t chunk_nnz = 512;
   std::vector<void *> owned;  // allocations released at destroy
   // workspace arena (grow only)

@@ -267,6 +267,41 @@ isvd_status build_heavy(isvd_operator *op, const int32_t *rowptr_dev, int64_t ro
   return ISVD_OK;
 }
 
+// Column tags for the ring form: colidx with floor(log2 deg_j) of the column's
+// row degree in bits 26..30 (a column is re-read once per nonzero of it, so
+// for symmetric A its degree is how often its row of the block is gathered).
+__global__ void tag_columns_kernel(int64_t nnz, const int32_t *colidx, const int32_t *rowptr, int32_t *tagged) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const int32_t j = colidx[e];
+    const int32_t d = rowptr[j + 1] - rowptr[j];
+    const int32_t b = d > 0 ? 31 - __clz(d) : 0;
+    tagged[e] = j | (b << 26);
+  }
+}
+
+isvd_status build_tags(isvd_operator *op, cudaStream_t s) {
+  const isvd_csr &A = op->desc.A;
+  op->tags_A = RingTags{};
+  if (op->n >= ((int64_t)1 << 26) || A.nnz == 0) return ISVD_OK;
+  std::vector<int32_t> rp((size_t)op->n + 1);
+  ISVD_CUDA_TRY(cudaMemcpyAsync(rp.data(), A.rowptr, sizeof(int32_t) * (op->n + 1), cudaMemcpyDeviceToHost, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  int32_t *t = (int32_t *)owned_alloc(op, sizeof(int32_t) * A.nnz, s);
+  if (!t) return fail(ISVD_ERR_WORKSPACE, "column tag allocation failed");
+  tag_columns_kernel<<<grid_for(A.nnz), 256, 0, s>>>(A.nnz, A.colidx, A.rowptr, t);
+  ISVD_CUDA_TRY(cudaGetLastError());
+  for (int64_t i = 0; i < op->n; ++i) {
+    const int32_t d = rp[i + 1] - rp[i];
+    int b = 0;
+    while (b < 31 && (d >> (b + 1)) > 0) ++b;
+    op->tags_A.hist[d > 0 ? b : 0] += 1;
+  }
+  op->tags_A.tagged = t;
+  op->tags_A.l2_budget = kRingL2Budget;
+  return ISVD_OK;
+}
+
 // Nonzero-chunk plan: row of every nonzero (device), rows that cross a chunk
 // boundary and rows without nonzeros (host lists, uploaded).
 isvd_status build_chunks(isvd_operator *op, const int32_t *rowptr_dev, int64_t rows, int64_t nnz, ChunkPlan *cp,
@@ -485,6 +520,7 @@ isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaS
   if (!(d.flags & ISVD_FLAG_SKIP_SYMMETRY_CHECK)) ISVD_TRY(check_symmetry(op, d.A, flags, s));
   ISVD_TRY(build_heavy(op, d.A.rowptr, n, &op->heavy_A, s));
   ISVD_TRY(build_chunks(op, d.A.rowptr, n, d.A.nnz, &op->chunk_A, s));
+  ISVD_TRY(build_tags(op, s));
 
   if (d.form == ISVD_FORM_CONCAT) {
     if (d.X.rowptr) {
@@ -527,6 +563,7 @@ struct Chain {
 
 int slab_cols(const isvd_operator *op, int dtype) {
   if (op->spmm_algo == 1) return chunk_slab_cols(dtype);
+  if (op->spmm_algo == 2) return ring_max_cols(dtype);
   return dtype == DT_F32 ? op->slab_cols_f32 : op->slab_cols_bf16;
 }
 
@@ -543,13 +580,28 @@ SpmmArgs base_args_A(const isvd_operator *op) {
   return a;
 }
 
-// fill slabs for one segment of width b
-void add_slabs(SpmmArgs &a, int dtype, int32_t b, int32_t scols, int32_t col_base, const void *in, int64_t ldi,
+int slabs_needed(int dtype, int32_t b, int32_t scols);
+
+// fill slabs for one segment of width b; false when they do not fit kMaxSlabs
+bool add_slabs(SpmmArgs &a, int dtype, int32_t b, int32_t scols, int32_t col_base, const void *in, int64_t ldi,
                void *out, int64_t ldo, const void *axpy, int64_t lda) {
-  SpmmSlab tmp[kMaxSlabs];
-  const int ns = make_slabs(dtype, b, scols, tmp);
+  SpmmSlab tmp[256];
+  int ns = 0;
+  if (scols == ring_max_cols(dtype)) {  // ring form: full-width slabs
+    for (int32_t c0 = 0; c0 < b && ns < 256; c0 += scols) {
+      SpmmSlab sl{};
+      sl.col0 = c0;
+      sl.width = (b - c0) < scols ? (b - c0) : scols;
+      sl.group = 32;
+      tmp[ns++] = sl;
+    }
+  } else {
+    if (slabs_needed(dtype, b, scols) > 256) return false;
+    ns = make_slabs(dtype, b, scols, tmp);
+  }
+  if (a.nslabs + ns > kMaxSlabs) return false;
   const size_t es = dtype_size(dtype);
-  for (int i = 0; i < ns && a.nslabs < kMaxSlabs; ++i) {
+  for (int i = 0; i < ns; ++i) {
     SpmmSlab sl = tmp[i];
     sl.in = (const char *)in + (size_t)sl.col0 * es;
     sl.ldi = ldi;
@@ -560,15 +612,34 @@ void add_slabs(SpmmArgs &a, int dtype, int32_t b, int32_t scols, int32_t col_bas
     sl.col0 += col_base;
     a.slab[a.nslabs++] = sl;
   }
+  return true;
 }
+
+#define ISVD_SLABS(call) \
+  do {                                                                                      \
+    if (!(call)) return fail(ISVD_ERR_UNSUPPORTED, "block too wide for the sparse-product kernel"); \
+  } while (0)
 
 int slabs_needed(int dtype, int32_t b, int32_t scols) {
   const int vn = dtype == DT_F32 ? 4 : 8;
-  int sc = scols > 32 * vn ? 32 * vn : scols;
+  const int cap = scols == ring_max_cols(dtype) ? scols : 32 * vn;  // ring slabs span the full width
+  int sc = scols > cap ? cap : scols;
   return (int)ceil_div(b, sc);
 }
 
 cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, const ChunkPlan &cp, int64_t pw) {
+  if (c.op->spmm_algo == 2) {
+    static const RingTags none;
+    const RingTags &tags = a.colidx == c.op->desc.A.colidx ? c.op->tags_A : none;
+    for (int i = 0; i < a.nslabs; ++i) {
+      SpmmArgs one = a;
+      one.slab[0] = a.slab[i];
+      one.nslabs = 1;
+      const cudaError_t e = spmm_ring_launch(one, c.dtype, cp, tags, c.sc->heavy_partial, pw, c.s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   if (c.op->spmm_algo == 1) return spmm_chunk_launch(a, c.dtype, cp, c.sc->heavy_partial, pw, c.s);
   return spmm_launch(a, c.dtype, hp, c.sc->heavy_partial, pw, c.s);
 }
@@ -689,7 +760,7 @@ static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int
       a.ax_rowscale = op->s;
     }
     if (last) set_lowrank(a);
-    add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, axp, ldg);
+    ISVD_SLABS(add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, axp, ldg));
     ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
     cur = dst;
     ldcur = lddst;
@@ -700,7 +771,7 @@ static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int
     SpmmArgs a = base_args_A(op);
     a.scalar = (float)d.adj_coeff;
     a.ax_scalar = 1.f;
-    add_slabs(a, dtype, b, scols, 0, G, ldg, out, ldo, out, ldo);
+    ISVD_SLABS(add_slabs(a, dtype, b, scols, 0, G, ldg, out, ldo, out, ldo));
     ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
   }
   return ISVD_OK;
@@ -738,8 +809,8 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
     ax.cache_hints = op->cache_hints;
     for (int l = 0; l <= L; ++l) {
       const char *gin = (const char *)G + (size_t)l * d.d * ldg * es;
-      if (L == 0) add_slabs(ax, dtype, b, scols, 0, gin, ldg, out, ldo, nullptr, 0);
-      else add_slabs(ax, dtype, b, scols, (int32_t)(l * bseg), gin, ldg, seg(l), ldp, nullptr, 0);
+      if (L == 0) ISVD_SLABS(add_slabs(ax, dtype, b, scols, 0, gin, ldg, out, ldo, nullptr, 0));
+      else ISVD_SLABS(add_slabs(ax, dtype, b, scols, (int32_t)(l * bseg), gin, ldg, seg(l), ldp, nullptr, 0));
     }
     ISVD_CUDA_TRY(run(ch, ax, op->heavy_X, op->chunk_X, ldp));
     if (L == 0) return ISVD_OK;
@@ -761,7 +832,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
         a.rowscale = last ? op->s : op->s2;
         a.ax_rowscale = last ? nullptr : op->s;
       }
-      add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, seg(l), ldp);
+      ISVD_SLABS(add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, seg(l), ldp));
       ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
       cur = dst;
       ldcur = lddst;
@@ -781,7 +852,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
       a.self_term = 1;
       a.rowscale = op->s;
     }
-    add_slabs(a, dtype, b, scols, 0, cur, ldcur, seg(l), ldp, nullptr, 0);
+    ISVD_SLABS(add_slabs(a, dtype, b, scols, 0, cur, ldcur, seg(l), ldp, nullptr, 0));
     ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
     cur = seg(l);
     ldcur = ldp;
@@ -799,7 +870,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
     const void *in = l == 0 ? G : (const void *)seg(l);
     const int64_t ldi = l == 0 ? ldg : ldp;
     char *o = (char *)out + (size_t)l * d.d * ldo * es;
-    add_slabs(at, dtype, b, scols, (int32_t)(l * bseg), in, ldi, o, ldo, nullptr, 0);
+    ISVD_SLABS(add_slabs(at, dtype, b, scols, (int32_t)(l * bseg), in, ldi, o, ldo, nullptr, 0));
   }
   ISVD_CUDA_TRY(run(ch, at, op->heavy_XT, op->chunk_XT, ldp));
   return ISVD_OK;
@@ -925,7 +996,8 @@ isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
   out->slab_cols_bf16 = op->slab_cols_bf16;
   out->heavy_threshold = op->heavy_A.threshold;
   out->heavy_chunk = op->heavy_A.chunk;
-  out->flags = (op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0) | (op->spmm_algo == 0 ? ISVD_TUNE_ROW_KERNEL : 0);
+  out->flags = (op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0) | (op->spmm_algo == 0 ? ISVD_TUNE_ROW_KERNEL : 0) |
+               (op->spmm_algo == 2 ? ISVD_TUNE_RING_KERNEL : 0);
   out->chunk_nnz = op->chunk_nnz;
   return ISVD_OK;
 }
@@ -942,7 +1014,7 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
   op->slab_cols_f32 = t->slab_cols_f32;
   op->slab_cols_bf16 = t->slab_cols_bf16;
   op->cache_hints = (t->flags & ISVD_TUNE_CACHE_HINTS) ? 1 : 0;
-  op->spmm_algo = (t->flags & ISVD_TUNE_ROW_KERNEL) ? 0 : 1;
+  op->spmm_algo = (t->flags & ISVD_TUNE_RING_KERNEL) ? 2 : (t->flags & ISVD_TUNE_ROW_KERNEL) ? 0 : 1;
   op->chunk_nnz = t->chunk_nnz;
   HeavyPlan *plans[3] = {&op->heavy_A, &op->heavy_X, &op->heavy_XT};
   for (HeavyPlan *hp : plans) {

@@ -284,18 +284,21 @@ class Operator:
         _check(lib().isvd_get_tuning(self._handle, t), "isvd_get_tuning")
         d = dict(zip(self._TUNING_FIELDS, list(t)))
         d["cache_hints"] = bool(d["flags"] & 1)
-        d["kernel"] = "rows" if d["flags"] & 2 else "chunks"
+        d["kernel"] = "ring" if d["flags"] & 4 else "rows" if d["flags"] & 2 else "chunks"
         return d
 
     def set_tuning(self, kernel=None, cache_hints=None, **fields):
-        """kernel: 'chunks' (nonzero-balanced) or 'rows' (row groups with hub
-        splitting); other keys as in isvd_tuning."""
+        """kernel: 'ring' (nonzero chunks, full-width gathers through shared
+        memory), 'rows' (row groups with hub splitting) or 'chunks' (nonzero
+        chunks over narrow column slabs); other keys as in isvd_tuning."""
         cur = self.tuning()
         vals = [int(fields.get(k, cur[k])) for k in self._TUNING_FIELDS]
         if cache_hints is not None:
             vals[4] = (vals[4] & ~1) | (1 if cache_hints else 0)
         if kernel is not None:
-            vals[4] = (vals[4] & ~2) | (2 if kernel == "rows" else 0)
+            if kernel not in ("ring", "rows", "chunks"):
+                raise ValueError(f"unknown kernel {kernel!r}")
+            vals[4] = (vals[4] & ~6) | {"ring": 4, "rows": 2, "chunks": 0}[kernel]
         t = (C.c_int32 * 6)(*vals)
         lib().isvd_set_tuning.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib().isvd_set_tuning.restype = C.c_int

@@ -117,10 +117,10 @@ def main():
             print(json.dumps({"what": "spmm", "workload": a.workload, "width": a.width, "dtype": a.dtype,
                               "tuning": tun, **r}), flush=True)
         else:
-            cases = [dict(row_kernel=True, slab32=128, slab16=256, heavy=64, chunk=64, hints=h) for h in (0, 1)]
-            cases += [dict(row_kernel=False, chunk_nnz=cn, hints=h) for cn in (256, 512, 1024, 2048) for h in (0, 1)]
+            cases = [dict(kernel="rows", slab_cols_f32=128, slab_cols_bf16=256, cache_hints=h) for h in (0, 1)]
+            cases += [dict(kernel="ring", chunk_nnz=cn, cache_hints=h) for cn in (512, 2048, 8192) for h in (0, 1)]
             for kw in cases:
-                tun = set_tuning(op, **kw)
+                tun = op.set_tuning(**kw)
                 r = spmm_case(g, op, a.width, a.dtype, a.reps, flush)
                 r.pop("all_ms")
                 print(json.dumps({"what": "spmm", "width": a.width, "dtype": a.dtype, "tuning": tun, **r}),

@@ -104,7 +104,7 @@ def make_ops(g, norm, K, ones, adj, weighted, lowrank, seed=5):
     return gpu, oracle.graph_operator(g, **kw)
 
 
-KERNELS = ["chunks", "rows"]
+KERNELS = ["ring", "chunks", "rows"]
 
 
 @pytest.mark.parametrize("case", CASES)
