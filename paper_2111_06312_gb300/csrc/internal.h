@@ -54,7 +54,7 @@ struct SpmmSlab {
   int32_t col0;      // first column of the slab in the low-rank coefficient block
   int32_t width;     // valid columns in this slab
   int32_t group;     // lanes per row
-  int32_t pad_;
+  int32_t hot_bucket;  // with column tags: gathers of columns in degree buckets >= this keep L2 priority
 };
 
 constexpr int kMaxSlabs = 24;
@@ -79,6 +79,7 @@ struct SpmmArgs {
   float lr_alpha[ISVD_MAX_LOWRANK];
   int32_t heavy_threshold;  // rows with more nonzeros go through the split path
   int32_t cache_hints;      // L2 eviction-priority hints on gathers and streams
+  const int32_t *tagged;    // nullable: colidx with degree buckets (RingTags), for the hints
   int32_t nslabs;
   SpmmSlab slab[kMaxSlabs];
 };
@@ -188,6 +189,12 @@ cudaError_t chol_inv_launch(const double *W, int32_t l, int64_t rows, int dtype,
                             double *R, double *Racc, double *tmp, int32_t *state, isvd_info *info, int32_t pass,
                             cudaStream_t s);
 cudaError_t racc_init_launch(double *Racc, int32_t l, cudaStream_t s);
+// The same step spread over a thread-block cluster (chol_cluster.cu); the
+// cluster size it can use (16, 8, or 1 when none fits).
+int chol_cluster_size();
+cudaError_t chol_cluster_launch(const double *W, int32_t l, double u, float *Rinv, int64_t ldr, double *R,
+                                double *Racc, double *tmp, int32_t *state, isvd_info *info, int32_t pass,
+                                cudaStream_t s);
 // SVD A = Uo diag(S) Vo^T of an l x l FP64 matrix by one-sided Jacobi on the
 // columns of A^T.  Optional FP32 copies of the first k columns (Uk, Vk: l x k)
 // and of S (k).  work: small_svd_work_doubles(l) FP64.
@@ -240,6 +247,7 @@ struct isvd_operator {
   cudaStream_t capture_stream = nullptr;
   int32_t slab_cols_f32 = 128, slab_cols_bf16 = 256;
   int32_t cache_hints = 1;
+  int32_t hot_tags = 1;     // row kernel: L2 priority only for gathers of hub columns
   struct GraphEntry {
     uint64_t key[16];
     cudaGraphExec_t exec;

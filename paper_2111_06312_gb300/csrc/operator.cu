@@ -641,6 +641,21 @@ cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, const ChunkPla
     return cudaSuccess;
   }
   if (c.op->spmm_algo == 1) return spmm_chunk_launch(a, c.dtype, cp, c.sc->heavy_partial, pw, c.s);
+  if (a.cache_hints && c.op->hot_tags && a.colidx == c.op->desc.A.colidx && c.op->tags_A.tagged) {
+    // per slab: the hottest degree buckets whose gathered rows fit the L2 budget keep priority
+    const RingTags &t = c.op->tags_A;
+    a.tagged = t.tagged;
+    for (int i = 0; i < a.nslabs; ++i) {
+      const double row_bytes = (double)round_up((int64_t)a.slab[i].width * (int64_t)dtype_size(c.dtype), 32);
+      double bytes = 0.0;
+      int hb = 32;
+      while (hb > 0 && bytes + (double)t.hist[hb - 1] * row_bytes <= (double)t.l2_budget) {
+        bytes += (double)t.hist[hb - 1] * row_bytes;
+        --hb;
+      }
+      a.slab[i].hot_bucket = hb;
+    }
+  }
   return spmm_launch(a, c.dtype, hp, c.sc->heavy_partial, pw, c.s);
 }
 
@@ -997,7 +1012,7 @@ isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
   out->heavy_threshold = op->heavy_A.threshold;
   out->heavy_chunk = op->heavy_A.chunk;
   out->flags = (op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0) | (op->spmm_algo == 0 ? ISVD_TUNE_ROW_KERNEL : 0) |
-               (op->spmm_algo == 2 ? ISVD_TUNE_RING_KERNEL : 0);
+               (op->spmm_algo == 2 ? ISVD_TUNE_RING_KERNEL : 0) | (op->hot_tags ? ISVD_TUNE_HOT_TAGS : 0);
   out->chunk_nnz = op->chunk_nnz;
   return ISVD_OK;
 }
@@ -1015,6 +1030,7 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
   op->slab_cols_bf16 = t->slab_cols_bf16;
   op->cache_hints = (t->flags & ISVD_TUNE_CACHE_HINTS) ? 1 : 0;
   op->spmm_algo = (t->flags & ISVD_TUNE_RING_KERNEL) ? 2 : (t->flags & ISVD_TUNE_ROW_KERNEL) ? 0 : 1;
+  op->hot_tags = (t->flags & ISVD_TUNE_HOT_TAGS) ? 1 : 0;
   op->chunk_nnz = t->chunk_nnz;
   HeavyPlan *plans[3] = {&op->heavy_A, &op->heavy_X, &op->heavy_XT};
   for (HeavyPlan *hp : plans) {

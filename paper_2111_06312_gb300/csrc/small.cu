@@ -152,6 +152,7 @@ cudaError_t small_kernels_init() {
   std::call_once(once, [] {
     cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)chol_smem(ISVD_MAX_BLOCK));
+    chol_cluster_size();  // attributes and the cluster size of the distributed form
     err = e;
   });
   return err;
@@ -173,6 +174,9 @@ cudaError_t chol_inv_launch(const double *W, int32_t l, int64_t rows, int dtype,
   (void)rows;
   (void)dtype;  // the Gram is accumulated in FP32 for both storage types
   const double u = 5.9604644775390625e-08;
+  // blocks of at least 32 columns go to the cluster form when the GPU can host it
+  if (l >= 32 && chol_cluster_size() >= 8)
+    return chol_cluster_launch(W, l, u, Rinv, ldr, R, Racc, tmp, state, info, pass, s);
   chol_inv_kernel<<<1, kSmallThreads, chol_smem(l), s>>>(W, l, u, Rinv, ldr, R, Racc, tmp, state, info, pass);
   return cudaGetLastError();
 }

@@ -165,9 +165,16 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
     int j = 0;
     float w = 0.f;
     if (me < e1) {
-      j = ld_idx<HINT>(a.colidx + me, pol.stream);
+      if (HINT && a.tagged) {
+        // column index in bits 0..25, degree bucket above: cold columns stream through L2
+        const int32_t t = ld_idx<HINT>(a.tagged + me, pol.stream);
+        j = t & ((1 << 26) - 1);
+        if ((t >> 26) < sl.hot_bucket) j |= (int)0x80000000;
+      } else {
+        j = ld_idx<HINT>(a.colidx + me, pol.stream);
+      }
       w = a.values ? __ldg(a.values + me) : 1.f;
-      if (a.colw) w *= __ldg(a.colw + j);
+      if (a.colw) w *= __ldg(a.colw + (j & 0x7fffffff));
     }
     const int cnt = min(L.G, e1 - e);
     int t = 0;
@@ -182,10 +189,10 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
       const float w3 = __shfl_sync(L.mask, w, t + 3, L.G);
       if (L.active) {
         float v0[VN], v1[VN], v2[VN], v3[VN];
-        V::unpack(ld16<HINT>(inb + (size_t)j0 * ldb, pol.keep), v0);
-        V::unpack(ld16<HINT>(inb + (size_t)j1 * ldb, pol.keep), v1);
-        V::unpack(ld16<HINT>(inb + (size_t)j2 * ldb, pol.keep), v2);
-        V::unpack(ld16<HINT>(inb + (size_t)j3 * ldb, pol.keep), v3);
+        V::unpack(ld16<HINT>(inb + (size_t)(j0 & 0x7fffffff) * ldb, j0 < 0 ? pol.stream : pol.keep), v0);
+        V::unpack(ld16<HINT>(inb + (size_t)(j1 & 0x7fffffff) * ldb, j1 < 0 ? pol.stream : pol.keep), v1);
+        V::unpack(ld16<HINT>(inb + (size_t)(j2 & 0x7fffffff) * ldb, j2 < 0 ? pol.stream : pol.keep), v2);
+        V::unpack(ld16<HINT>(inb + (size_t)(j3 & 0x7fffffff) * ldb, j3 < 0 ? pol.stream : pol.keep), v3);
 #pragma unroll
         for (int k = 0; k < VN; ++k) {
           acc[k] = fmaf(w0, v0[k], acc[k]);
@@ -200,7 +207,7 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
       const float w0 = __shfl_sync(L.mask, w, t, L.G);
       if (L.active) {
         float v0[VN];
-        V::unpack(ld16<HINT>(inb + (size_t)j0 * ldb, pol.keep), v0);
+        V::unpack(ld16<HINT>(inb + (size_t)(j0 & 0x7fffffff) * ldb, j0 < 0 ? pol.stream : pol.keep), v0);
 #pragma unroll
         for (int k = 0; k < VN; ++k) acc[k] = fmaf(w0, v0[k], acc[k]);
       }

@@ -98,7 +98,7 @@ def main():
     ap.add_argument("--p", type=int, default=16)
     ap.add_argument("--q", type=int, default=6)
     ap.add_argument("--precision", default="fp32")
-    ap.add_argument("--kernel", default=None, choices=["rows", "chunks"])
+    ap.add_argument("--kernel", default=None, choices=["rows", "chunks", "ring"])
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--q-ref", type=int, default=0)
@@ -113,12 +113,17 @@ def main():
             tun = set_tuning(op, slab32=a.slab or None, slab16=a.slab or None, heavy=a.heavy or None,
                              chunk=a.chunk or None, row_kernel=True if a.row_kernel else None,
                              chunk_nnz=a.chunk_nnz or None)
+            if a.kernel:
+                tun = op.set_tuning(kernel=a.kernel)
             r = spmm_case(g, op, a.width, a.dtype, a.reps, flush)
             print(json.dumps({"what": "spmm", "workload": a.workload, "width": a.width, "dtype": a.dtype,
                               "tuning": tun, **r}), flush=True)
         else:
-            cases = [dict(kernel="rows", slab_cols_f32=128, slab_cols_bf16=256, cache_hints=h) for h in (0, 1)]
-            cases += [dict(kernel="ring", chunk_nnz=cn, cache_hints=h) for cn in (512, 2048, 8192) for h in (0, 1)]
+            cases = [dict(kernel="rows", slab_cols_f32=128, slab_cols_bf16=256, cache_hints=h, hot_tags=t)
+                     for h, t in ((0, 0), (1, 0), (1, 1))]
+            cases += [dict(kernel="rows", slab_cols_f32=sc, slab_cols_bf16=2 * sc, cache_hints=1, hot_tags=1)
+                      for sc in (64, 96)]
+            cases += [dict(kernel="ring", chunk_nnz=cn, cache_hints=1) for cn in (512, 2048)]
             for kw in cases:
                 tun = op.set_tuning(**kw)
                 r = spmm_case(g, op, a.width, a.dtype, a.reps, flush)

@@ -200,7 +200,8 @@ def cond_block(r, c, cond, seed):
     return (Ua * np.geomspace(1, 1 / cond, c)) @ Va.T
 
 
-@pytest.mark.parametrize("rows,l,cond", [(5000, 42, 1e2), (20011, 144, 1e3), (3001, 19, 1e5), (70000, 74, 1e6)])
+@pytest.mark.parametrize("rows,l,cond", [(5000, 42, 1e2), (20011, 144, 1e3), (3001, 19, 1e5), (70000, 74, 1e6),
+                                         (9000, 160, 1e5), (4000, 33, 1e4), (2500, 31, 1e2)])
 def test_orthonormalize(ne_small, rows, l, cond):
     Q0 = cond_block(rows, l, cond, 8)
     with isvd.graph_operator(ne_small, coeffs=C5) as op:
