@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(kCholThreads) chol_cluster_kernel(const double
         D[r * (kNB + 1) + c] = v;
       }
       __syncthreads();
-      // (b) factor it (one warp, lane = column)
+      // (b) factor it (one warp): row j scaled by 1/sqrt(d_jj), then the
+      // trailing triangle updated with one lane per element
       if (warp == 0) {
         for (int j = 0; j < nb; ++j) {
           const double d = D[j * (kNB + 1) + j];
@@ -108,17 +109,21 @@ __global__ void __launch_bounds__(kCholThreads) chol_cluster_kernel(const double
             if (lane == 0) s_fail = 1;
             break;
           }
-          const double r = sqrt(d), inv = 1.0 / r;
+          const double inv = rsqrt(d);
           __syncwarp();
           if (lane == j) {
-            D[j * (kNB + 1) + j] = r;
+            D[j * (kNB + 1) + j] = d * inv;
             invD[j] = inv;
           }
           if (lane > j && lane < nb) D[j * (kNB + 1) + lane] *= inv;
           __syncwarp();
-          if (lane > j && lane < nb) {
-            const double rjc = D[j * (kNB + 1) + lane];
-            for (int i = j + 1; i <= lane; ++i) D[i * (kNB + 1) + lane] -= D[j * (kNB + 1) + i] * rjc;
+          const int m = nb - j - 1;  // trailing order
+          for (int idx = lane; idx < m * m; idx += 32) {
+            const int ii = idx / m, cc = idx - ii * m;
+            if (cc >= ii) {
+              const int i = j + 1 + ii, c = j + 1 + cc;
+              D[i * (kNB + 1) + c] -= D[j * (kNB + 1) + i] * D[j * (kNB + 1) + c];
+            }
           }
           __syncwarp();
         }

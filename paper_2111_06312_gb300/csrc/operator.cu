@@ -577,6 +577,7 @@ SpmmArgs base_args_A(const isvd_operator *op) {
   a.ax_scalar = 1.f;
   a.heavy_threshold = op->heavy_A.n_chunks > 0 ? op->heavy_A.threshold : INT_MAX;
   a.cache_hints = op->cache_hints;
+  a.rows_occupancy = op->rows_occupancy;
   return a;
 }
 
@@ -822,6 +823,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
     ax.ax_scalar = 1.f;
     ax.heavy_threshold = op->heavy_X.n_chunks > 0 ? op->heavy_X.threshold : INT_MAX;
     ax.cache_hints = op->cache_hints;
+    ax.rows_occupancy = op->rows_occupancy;
     for (int l = 0; l <= L; ++l) {
       const char *gin = (const char *)G + (size_t)l * d.d * ldg * es;
       if (L == 0) ISVD_SLABS(add_slabs(ax, dtype, b, scols, 0, gin, ldg, out, ldo, nullptr, 0));
@@ -881,6 +883,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
   at.ax_scalar = 1.f;
   at.heavy_threshold = op->heavy_XT.n_chunks > 0 ? op->heavy_XT.threshold : INT_MAX;
   at.cache_hints = op->cache_hints;
+  at.rows_occupancy = op->rows_occupancy;
   for (int l = 0; l <= L; ++l) {
     const void *in = l == 0 ? G : (const void *)seg(l);
     const int64_t ldi = l == 0 ? ldg : ldp;
@@ -1012,7 +1015,8 @@ isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
   out->heavy_threshold = op->heavy_A.threshold;
   out->heavy_chunk = op->heavy_A.chunk;
   out->flags = (op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0) | (op->spmm_algo == 0 ? ISVD_TUNE_ROW_KERNEL : 0) |
-               (op->spmm_algo == 2 ? ISVD_TUNE_RING_KERNEL : 0) | (op->hot_tags ? ISVD_TUNE_HOT_TAGS : 0);
+               (op->spmm_algo == 2 ? ISVD_TUNE_RING_KERNEL : 0) | (op->hot_tags ? ISVD_TUNE_HOT_TAGS : 0) |
+               (op->rows_occupancy >= 3 ? ISVD_TUNE_ROWS_OCC3 : 0);
   out->chunk_nnz = op->chunk_nnz;
   return ISVD_OK;
 }
@@ -1031,6 +1035,7 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
   op->cache_hints = (t->flags & ISVD_TUNE_CACHE_HINTS) ? 1 : 0;
   op->spmm_algo = (t->flags & ISVD_TUNE_RING_KERNEL) ? 2 : (t->flags & ISVD_TUNE_ROW_KERNEL) ? 0 : 1;
   op->hot_tags = (t->flags & ISVD_TUNE_HOT_TAGS) ? 1 : 0;
+  op->rows_occupancy = (t->flags & ISVD_TUNE_ROWS_OCC3) ? 3 : 2;
   op->chunk_nnz = t->chunk_nnz;
   HeavyPlan *plans[3] = {&op->heavy_A, &op->heavy_X, &op->heavy_XT};
   for (HeavyPlan *hp : plans) {

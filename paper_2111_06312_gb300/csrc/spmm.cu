@@ -255,8 +255,8 @@ __device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, 
   else V::store_partial(o, acc, valid);
 }
 
-template <int DT, bool HINT>
-__global__ void __launch_bounds__(256) spmm_rows_kernel(const __grid_constant__ SpmmArgs a) {
+template <int DT, bool HINT, int MINB>
+__global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_constant__ SpmmArgs a) {
   constexpr int VN = Vec<DT>::N;
   const SpmmSlab &sl = a.slab[blockIdx.y];
   const Lane L = make_lane<DT>(sl);
@@ -351,7 +351,10 @@ cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, in
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
   dim3 grid((unsigned)bx, (unsigned)a.nslabs);
-  spmm_rows_kernel<DT, HINT><<<grid, threads, 0, s>>>(a);
+  if (a.rows_occupancy >= 3)
+    spmm_rows_kernel<DT, HINT, 6><<<grid, threads, 0, s>>>(a);
+  else
+    spmm_rows_kernel<DT, HINT, 1><<<grid, threads, 0, s>>>(a);
   if (hp.n_chunks > 0) {
     int64_t cx = ceil_div(hp.n_chunks, rows_per_block);
     if (cx > cap) cx = cap;

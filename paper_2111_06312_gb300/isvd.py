@@ -285,10 +285,11 @@ class Operator:
         d = dict(zip(self._TUNING_FIELDS, list(t)))
         d["cache_hints"] = bool(d["flags"] & 1)
         d["hot_tags"] = bool(d["flags"] & 8)
+        d["rows_occupancy"] = 3 if d["flags"] & 16 else 2
         d["kernel"] = "ring" if d["flags"] & 4 else "rows" if d["flags"] & 2 else "chunks"
         return d
 
-    def set_tuning(self, kernel=None, cache_hints=None, hot_tags=None, **fields):
+    def set_tuning(self, kernel=None, cache_hints=None, hot_tags=None, rows_occupancy=None, **fields):
         """kernel: 'ring' (nonzero chunks, full-width gathers through shared
         memory), 'rows' (row groups with hub splitting) or 'chunks' (nonzero
         chunks over narrow column slabs); other keys as in isvd_tuning."""
@@ -298,6 +299,8 @@ class Operator:
             vals[4] = (vals[4] & ~1) | (1 if cache_hints else 0)
         if hot_tags is not None:
             vals[4] = (vals[4] & ~8) | (8 if hot_tags else 0)
+        if rows_occupancy is not None:
+            vals[4] = (vals[4] & ~16) | (16 if rows_occupancy >= 3 else 0)
         if kernel is not None:
             if kernel not in ("ring", "rows", "chunks"):
                 raise ValueError(f"unknown kernel {kernel!r}")
