@@ -273,12 +273,13 @@ ISVD_API isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t 
  * heavy_threshold: rows with more nonzeros are split into chunks of
  * heavy_chunk nonzeros whose partial sums are combined in order. */
 typedef struct {
-  int32_t slab_cols_f32;   /* 4..128, multiple of 4 */
-  int32_t slab_cols_bf16;  /* 8..256, multiple of 8 */
+  int32_t slab_cols_f32;   /* 4..256, multiple of 4 (above 128: two 16-byte chunks per lane) */
+  int32_t slab_cols_bf16;  /* 8..512, multiple of 8 (above 256: two chunks per lane) */
   int32_t heavy_threshold; /* >= 32 */
   int32_t heavy_chunk;     /* >= 32 */
   int32_t flags;           /* ISVD_TUNE_* */
   int32_t chunk_nnz;       /* nonzeros per warp chunk of the balanced kernels, 32..2^20 */
+  int32_t l2_budget_mb;    /* L2 megabytes granted to gathered hub rows (HOT_TAGS), 1..1024 */
 } isvd_tuning;
 
 /* The sparse-product kernel: ISVD_TUNE_ROW_KERNEL (row groups with hub
@@ -298,6 +299,27 @@ enum {
  * Errors: INVALID_ARGUMENT (out-of-range field), WORKSPACE, CUDA. */
 ISVD_API isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out);
 ISVD_API isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *stream);
+
+/* Choose the operator's sparse-product launch shape for block width b and
+ * storage dtype by timing isvd_apply for a fixed list of candidates (row
+ * kernel: occupancy, L2 budget for hub columns, hub split threshold, wide
+ * slabs; the ring kernel), keep the fastest (applied with isvd_set_tuning and
+ * copied to *out when out is not NULL).  cache_path (HOST, may be NULL): a text
+ * file of earlier results keyed by the operator's shape and degree histogram,
+ * b, dtype and the device name; a hit applies the stored shape without timing,
+ * a miss appends the new result.  Synchronises `stream`; allocates two probe
+ * blocks through the operator's allocator.  No counterpart in the paper.
+ * Errors: INVALID_ARGUMENT, WORKSPACE, CUDA (the previous shape is restored). */
+ISVD_API isvd_status isvd_autotune(isvd_operator *op, int32_t b, isvd_dtype dtype, const char *cache_path,
+                                   isvd_tuning *out, void *stream);
+
+/* Failure-detection self-test: launches one CTA that waits, through the same
+ * bounded mbarrier wait the tensor-core kernels use, on a barrier that nothing
+ * arrives on; after spin_limit polls (1..2^24) the wait gives up and the kernel
+ * sets dev_info->status to ISVD_ERR_TIMEOUT and returns, leaving the context
+ * usable.  dev_info: DEVICE isvd_info, cleared by the caller.  No counterpart
+ * in the paper. */
+ISVD_API isvd_status isvd_selftest_wait(int32_t spin_limit, isvd_info *dev_info, void *stream);
 
 /* Number of kernel launches in the CUDA graph that the last isvd_svd call on
  * this operator replayed (-1 if none yet).  Introspection for benchmarks. */

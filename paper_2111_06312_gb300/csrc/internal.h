@@ -15,6 +15,7 @@ namespace isvd {
 // ---- errors -----------------------------------------------------------------
 void set_error(const char *fmt, ...);
 isvd_status fail(isvd_status s, const char *fmt, ...);
+const char *last_error();
 
 #define ISVD_CUDA_TRY(expr)                                                                      \
   do {                                                                                           \
@@ -130,7 +131,7 @@ int chunk_slab_cols(int dtype);
 // number of columns per bucket; gathers of the hottest buckets whose rows fit
 // l2_budget bytes get the L2 evict_last policy.
 constexpr size_t kRingSmemBudget = 200 * 1024;
-constexpr int64_t kRingL2Budget = 96ll << 20;
+constexpr int64_t kRingL2Budget = 64ll << 20;
 struct RingTags {
   const int32_t *tagged = nullptr;
   int64_t hist[32] = {};

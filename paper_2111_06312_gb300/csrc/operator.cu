@@ -623,7 +623,7 @@ bool add_slabs(SpmmArgs &a, int dtype, int32_t b, int32_t scols, int32_t col_bas
 
 int slabs_needed(int dtype, int32_t b, int32_t scols) {
   const int vn = dtype == DT_F32 ? 4 : 8;
-  const int cap = scols == ring_max_cols(dtype) ? scols : 32 * vn;  // ring slabs span the full width
+  const int cap = scols == ring_max_cols(dtype) ? scols : 64 * vn;  // ring slabs span the full width
   int sc = scols > cap ? cap : scols;
   return (int)ceil_div(b, sc);
 }
@@ -1018,14 +1018,15 @@ isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
                (op->spmm_algo == 2 ? ISVD_TUNE_RING_KERNEL : 0) | (op->hot_tags ? ISVD_TUNE_HOT_TAGS : 0) |
                (op->rows_occupancy >= 3 ? ISVD_TUNE_ROWS_OCC3 : 0);
   out->chunk_nnz = op->chunk_nnz;
+  out->l2_budget_mb = (int32_t)(op->tags_A.l2_budget >> 20);
   return ISVD_OK;
 }
 
 isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *stream) {
   if (!op || !t) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
-  if (t->slab_cols_f32 < 4 || t->slab_cols_f32 > 128 || t->slab_cols_f32 % 4 || t->slab_cols_bf16 < 8 ||
-      t->slab_cols_bf16 > 256 || t->slab_cols_bf16 % 8 || t->heavy_threshold < 32 || t->heavy_chunk < 32 ||
-      t->chunk_nnz < 32 || t->chunk_nnz > (1 << 20))
+  if (t->slab_cols_f32 < 4 || t->slab_cols_f32 > 256 || t->slab_cols_f32 % 4 || t->slab_cols_bf16 < 8 ||
+      t->slab_cols_bf16 > 512 || t->slab_cols_bf16 % 8 || t->heavy_threshold < 32 || t->heavy_chunk < 32 ||
+      t->chunk_nnz < 32 || t->chunk_nnz > (1 << 20) || t->l2_budget_mb < 1 || t->l2_budget_mb > 1024)
     return fail(ISVD_ERR_INVALID_ARGUMENT, "tuning field out of range");
   cudaStream_t s = (cudaStream_t)stream;
   ISVD_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1037,6 +1038,7 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
   op->hot_tags = (t->flags & ISVD_TUNE_HOT_TAGS) ? 1 : 0;
   op->rows_occupancy = (t->flags & ISVD_TUNE_ROWS_OCC3) ? 3 : 2;
   op->chunk_nnz = t->chunk_nnz;
+  op->tags_A.l2_budget = (int64_t)t->l2_budget_mb << 20;
   HeavyPlan *plans[3] = {&op->heavy_A, &op->heavy_X, &op->heavy_XT};
   for (HeavyPlan *hp : plans) {
     hp->threshold = t->heavy_threshold;

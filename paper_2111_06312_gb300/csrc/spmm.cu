@@ -135,8 +135,10 @@ struct Lane {
   int gl;         // lane within the group
   int sub;        // group index within the warp
   unsigned mask;  // lanes of this group
-  int col;        // first column (within the slab) owned by this lane
+  int col;        // first column (within the slab) of the lane's first 16-byte chunk
   bool active;    // col < width
+  int col2;       // wide slabs (two chunks per lane): first column of the second chunk
+  bool active2;
 };
 
 template <int DT>
@@ -149,16 +151,21 @@ __device__ __forceinline__ Lane make_lane(const SpmmSlab &sl) {
   L.mask = (L.G == 32) ? 0xffffffffu : (((1u << L.G) - 1u) << (L.sub * L.G));
   L.col = L.gl * Vec<DT>::N;
   L.active = L.col < sl.width;
+  L.col2 = (L.gl + L.G) * Vec<DT>::N;
+  L.active2 = L.col2 < sl.width;
   return L;
 }
 
-// acc += sum over nonzeros e in [e0, e1) of a_e w_j in_j (slab columns of this lane)
-template <int DT, bool HINT>
+// acc += sum over nonzeros e in [e0, e1) of a_e w_j in_j (slab columns of this
+// lane: one 16-byte chunk, or two in wide slabs (CPL = 2), acc[c * VN + k]).
+template <int DT, bool HINT, int CPL>
 __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int e0,
                                              int e1, const Policies &pol, float *acc) {
   using V = Vec<DT>;
   constexpr int VN = V::N;
+  constexpr int U = CPL == 1 ? 4 : 2;  // nonzeros per step (the same registers in flight)
   const char *inb = reinterpret_cast<const char *>(sl.in) + (size_t)L.col * V::BYTES;
+  const size_t off2 = (size_t)(L.col2 - L.col) * V::BYTES;
   const size_t ldb = (size_t)sl.ldi * V::BYTES;
   for (int e = e0; e < e1; e += L.G) {
     const int me = e + L.gl;
@@ -178,84 +185,101 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
     }
     const int cnt = min(L.G, e1 - e);
     int t = 0;
-    for (; t + 4 <= cnt; t += 4) {
-      const int j0 = __shfl_sync(L.mask, j, t, L.G);
-      const int j1 = __shfl_sync(L.mask, j, t + 1, L.G);
-      const int j2 = __shfl_sync(L.mask, j, t + 2, L.G);
-      const int j3 = __shfl_sync(L.mask, j, t + 3, L.G);
-      const float w0 = __shfl_sync(L.mask, w, t, L.G);
-      const float w1 = __shfl_sync(L.mask, w, t + 1, L.G);
-      const float w2 = __shfl_sync(L.mask, w, t + 2, L.G);
-      const float w3 = __shfl_sync(L.mask, w, t + 3, L.G);
-      if (L.active) {
-        float v0[VN], v1[VN], v2[VN], v3[VN];
-        V::unpack(ld16<HINT>(inb + (size_t)(j0 & 0x7fffffff) * ldb, j0 < 0 ? pol.stream : pol.keep), v0);
-        V::unpack(ld16<HINT>(inb + (size_t)(j1 & 0x7fffffff) * ldb, j1 < 0 ? pol.stream : pol.keep), v1);
-        V::unpack(ld16<HINT>(inb + (size_t)(j2 & 0x7fffffff) * ldb, j2 < 0 ? pol.stream : pol.keep), v2);
-        V::unpack(ld16<HINT>(inb + (size_t)(j3 & 0x7fffffff) * ldb, j3 < 0 ? pol.stream : pol.keep), v3);
+    for (; t + U <= cnt; t += U) {
+      int jj[U];
+      float ww[U];
 #pragma unroll
-        for (int k = 0; k < VN; ++k) {
-          acc[k] = fmaf(w0, v0[k], acc[k]);
-          acc[k] = fmaf(w1, v1[k], acc[k]);
-          acc[k] = fmaf(w2, v2[k], acc[k]);
-          acc[k] = fmaf(w3, v3[k], acc[k]);
+      for (int u = 0; u < U; ++u) {
+        jj[u] = __shfl_sync(L.mask, j, t + u, L.G);
+        ww[u] = __shfl_sync(L.mask, w, t + u, L.G);
+      }
+      if (L.active) {
+        uint4 raw[U][CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const char *src = inb + (size_t)(jj[u] & 0x7fffffff) * ldb;
+          const uint64_t pl = jj[u] < 0 ? pol.stream : pol.keep;
+          raw[u][0] = ld16<HINT>(src, pl);
+          if (CPL == 2) raw[u][CPL - 1] = L.active2 ? ld16<HINT>(src + off2, pl) : make_uint4(0u, 0u, 0u, 0u);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            float v[VN];
+            V::unpack(raw[u][c], v);
+#pragma unroll
+            for (int k = 0; k < VN; ++k) acc[c * VN + k] = fmaf(ww[u], v[k], acc[c * VN + k]);
+          }
       }
     }
     for (; t < cnt; ++t) {
       const int j0 = __shfl_sync(L.mask, j, t, L.G);
       const float w0 = __shfl_sync(L.mask, w, t, L.G);
       if (L.active) {
-        float v0[VN];
-        V::unpack(ld16<HINT>(inb + (size_t)(j0 & 0x7fffffff) * ldb, j0 < 0 ? pol.stream : pol.keep), v0);
+        const char *src = inb + (size_t)(j0 & 0x7fffffff) * ldb;
+        const uint64_t pl = j0 < 0 ? pol.stream : pol.keep;
+        uint4 raw[CPL];
+        raw[0] = ld16<HINT>(src, pl);
+        if (CPL == 2) raw[CPL - 1] = L.active2 ? ld16<HINT>(src + off2, pl) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int k = 0; k < VN; ++k) acc[k] = fmaf(w0, v0[k], acc[k]);
+        for (int c = 0; c < CPL; ++c) {
+          float v[VN];
+          V::unpack(raw[c], v);
+#pragma unroll
+          for (int k = 0; k < VN; ++k) acc[c * VN + k] = fmaf(w0, v[k], acc[c * VN + k]);
+        }
       }
     }
   }
 }
 
-template <int DT, bool HINT>
+template <int DT, bool HINT, int CPL>
 __device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int64_t r,
-                                         const Policies &pol, float *acc) {
+                                         const Policies &pol, float *acc_all) {
   using V = Vec<DT>;
   constexpr int VN = V::N;
-  if (!L.active) return;
-  if (a.self_term) {
-    float v[VN];
-    V::unpack(ld16<false>(reinterpret_cast<const char *>(sl.in) + ((size_t)r * sl.ldi + L.col) * V::BYTES, 0), v);
-    const float w = a.colw ? __ldg(a.colw + r) : 1.f;
-#pragma unroll
-    for (int k = 0; k < VN; ++k) acc[k] = fmaf(w, v[k], acc[k]);
-  }
   const float sc = a.scalar * (a.rowscale ? __ldg(a.rowscale + r) : 1.f);
+  const float as = sl.axpy ? a.ax_scalar * (a.ax_rowscale ? __ldg(a.ax_rowscale + r) : 1.f) : 0.f;
+  const float ws = a.self_term ? (a.colw ? __ldg(a.colw + r) : 1.f) : 0.f;
 #pragma unroll
-  for (int k = 0; k < VN; ++k) acc[k] *= sc;
-  if (sl.axpy) {
-    float v[VN];
-    // plain load: the axpy block may be the output block (in-place accumulate)
-    V::unpack(*reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(sl.axpy) +
-                                               ((size_t)r * sl.lda + L.col) * V::BYTES),
-              v);
-    const float as = a.ax_scalar * (a.ax_rowscale ? __ldg(a.ax_rowscale + r) : 1.f);
+  for (int c = 0; c < CPL; ++c) {
+    const int col = c == 0 ? L.col : L.col2;
+    if (!(c == 0 ? L.active : L.active2)) break;
+    float *acc = acc_all + c * VN;
+    if (a.self_term) {
+      float v[VN];
+      V::unpack(ld16<false>(reinterpret_cast<const char *>(sl.in) + ((size_t)r * sl.ldi + col) * V::BYTES, 0), v);
 #pragma unroll
-    for (int k = 0; k < VN; ++k) acc[k] = fmaf(as, v[k], acc[k]);
+      for (int k = 0; k < VN; ++k) acc[k] = fmaf(ws, v[k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] *= sc;
+    if (sl.axpy) {
+      float v[VN];
+      // plain load: the axpy block may be the output block (in-place accumulate)
+      V::unpack(*reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(sl.axpy) +
+                                                 ((size_t)r * sl.lda + col) * V::BYTES),
+                v);
+#pragma unroll
+      for (int k = 0; k < VN; ++k) acc[k] = fmaf(as, v[k], acc[k]);
+    }
+    for (int t = 0; t < a.lr_rank; ++t) {
+      const int tu = t - a.lr_ones_first;
+      const float u = (tu < 0 || !a.lr_u) ? 1.f : __ldg(a.lr_u + (size_t)r * a.lr_ldu + tu);
+      const float al = a.lr_alpha[t] * u;
+      const float *cf = a.lr_c + (size_t)t * a.lr_ldc + sl.col0 + col;
+#pragma unroll
+      for (int k = 0; k < VN; ++k) acc[k] = fmaf(al, __ldg(cf + k), acc[k]);
+    }
+    const int valid = min(VN, sl.width - col);
+    char *o = reinterpret_cast<char *>(sl.out) + ((size_t)r * sl.ldo + col) * V::BYTES;
+    if (valid >= VN) st16<HINT>(o, V::pack(acc), pol.stream);
+    else V::store_partial(o, acc, valid);
   }
-  for (int t = 0; t < a.lr_rank; ++t) {
-    const int tu = t - a.lr_ones_first;
-    const float u = (tu < 0 || !a.lr_u) ? 1.f : __ldg(a.lr_u + (size_t)r * a.lr_ldu + tu);
-    const float al = a.lr_alpha[t] * u;
-    const float *c = a.lr_c + (size_t)t * a.lr_ldc + sl.col0 + L.col;
-#pragma unroll
-    for (int k = 0; k < VN; ++k) acc[k] = fmaf(al, __ldg(c + k), acc[k]);
-  }
-  const int valid = min(VN, sl.width - L.col);
-  char *o = reinterpret_cast<char *>(sl.out) + ((size_t)r * sl.ldo + L.col) * V::BYTES;
-  if (valid >= VN) st16<HINT>(o, V::pack(acc), pol.stream);
-  else V::store_partial(o, acc, valid);
 }
 
-template <int DT, bool HINT, int MINB>
+template <int DT, bool HINT, int MINB, int CPL>
 __global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_constant__ SpmmArgs a) {
   constexpr int VN = Vec<DT>::N;
   const SpmmSlab &sl = a.slab[blockIdx.y];
@@ -269,15 +293,15 @@ __global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_const
     if (r >= a.rows) continue;  // uniform within the group
     const int e0 = ld_idx<HINT>(a.rowptr + r, pol.stream), e1 = ld_idx<HINT>(a.rowptr + r + 1, pol.stream);
     if (e1 - e0 > a.heavy_threshold) continue;
-    float acc[VN];
+    float acc[CPL * VN];
 #pragma unroll
-    for (int k = 0; k < VN; ++k) acc[k] = 0.f;
-    gather_range<DT, HINT>(a, sl, L, e0, e1, pol, acc);
-    epilogue<DT, HINT>(a, sl, L, r, pol, acc);
+    for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
+    gather_range<DT, HINT, CPL>(a, sl, L, e0, e1, pol, acc);
+    epilogue<DT, HINT, CPL>(a, sl, L, r, pol, acc);
   }
 }
 
-template <int DT, bool HINT>
+template <int DT, bool HINT, int CPL>
 __global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant__ SpmmArgs a,
                                                           const int2 *__restrict__ chunks,
                                                           const int32_t *__restrict__ chunk_end, int32_t n,
@@ -293,19 +317,21 @@ __global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant_
     const int64_t c = base + L.sub;
     if (c >= n) continue;
     const int e0 = chunks[c].y, e1 = chunk_end[c];
-    float acc[VN];
+    float acc[CPL * VN];
 #pragma unroll
-    for (int k = 0; k < VN; ++k) acc[k] = 0.f;
-    gather_range<DT, HINT>(a, sl, L, e0, e1, pol, acc);
-    if (L.active) {
-      float *p = partial + (size_t)c * pw + sl.col0 + L.col;
+    for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
+    gather_range<DT, HINT, CPL>(a, sl, L, e0, e1, pol, acc);
 #pragma unroll
-      for (int k = 0; k < VN; ++k) p[k] = acc[k];
+    for (int h = 0; h < CPL; ++h) {
+      if (!(h == 0 ? L.active : L.active2)) break;
+      float *p = partial + (size_t)c * pw + sl.col0 + (h == 0 ? L.col : L.col2);
+#pragma unroll
+      for (int k = 0; k < VN; ++k) p[k] = acc[h * VN + k];
     }
   }
 }
 
-template <int DT, bool HINT>
+template <int DT, bool HINT, int CPL>
 __global__ void __launch_bounds__(256) spmm_finish_kernel(const __grid_constant__ SpmmArgs a,
                                                           const int4 *__restrict__ hrows, int32_t n,
                                                           const float *__restrict__ partial, int64_t pw) {
@@ -320,17 +346,19 @@ __global__ void __launch_bounds__(256) spmm_finish_kernel(const __grid_constant_
     const int64_t h = base + L.sub;
     if (h >= n) continue;
     const int4 hr = hrows[h];
-    float acc[VN];
+    float acc[CPL * VN];
 #pragma unroll
-    for (int k = 0; k < VN; ++k) acc[k] = 0.f;
-    if (L.active) {
+    for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      if (!(q == 0 ? L.active : L.active2)) break;
       for (int c = hr.y; c < hr.y + hr.z; ++c) {
-        const float *p = partial + (size_t)c * pw + sl.col0 + L.col;
+        const float *p = partial + (size_t)c * pw + sl.col0 + (q == 0 ? L.col : L.col2);
 #pragma unroll
-        for (int k = 0; k < VN; ++k) acc[k] += p[k];
+        for (int k = 0; k < VN; ++k) acc[q * VN + k] += p[k];
       }
     }
-    epilogue<DT, HINT>(a, sl, L, hr.x, pol, acc);
+    epilogue<DT, HINT, CPL>(a, sl, L, hr.x, pol, acc);
   }
 }
 
@@ -340,8 +368,8 @@ int pow2_ceil(int x) {
   return p;
 }
 
-template <int DT, bool HINT>
-cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s) {
+template <int DT, bool HINT, int CPL>
+cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s) {
   const int threads = 256;
   int gmin = 32;
   for (int i = 0; i < a.nslabs; ++i) gmin = gmin < a.slab[i].group ? gmin : a.slab[i].group;
@@ -352,27 +380,41 @@ cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, in
   if (bx < 1) bx = 1;
   dim3 grid((unsigned)bx, (unsigned)a.nslabs);
   if (a.rows_occupancy >= 3)
-    spmm_rows_kernel<DT, HINT, 6><<<grid, threads, 0, s>>>(a);
+    spmm_rows_kernel<DT, HINT, 6, CPL><<<grid, threads, 0, s>>>(a);
   else
-    spmm_rows_kernel<DT, HINT, 1><<<grid, threads, 0, s>>>(a);
+    spmm_rows_kernel<DT, HINT, 1, CPL><<<grid, threads, 0, s>>>(a);
   if (hp.n_chunks > 0) {
     int64_t cx = ceil_div(hp.n_chunks, rows_per_block);
     if (cx > cap) cx = cap;
-    spmm_chunks_kernel<DT, HINT><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, s>>>(
+    spmm_chunks_kernel<DT, HINT, CPL><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, s>>>(
         a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
     int64_t fx = ceil_div(hp.n_rows, rows_per_block);
     if (fx > cap) fx = cap;
-    spmm_finish_kernel<DT, HINT><<<dim3((unsigned)fx, (unsigned)a.nslabs), threads, 0, s>>>(a, hp.rows, hp.n_rows,
-                                                                                      partial, pw);
+    spmm_finish_kernel<DT, HINT, CPL><<<dim3((unsigned)fx, (unsigned)a.nslabs), threads, 0, s>>>(
+        a, hp.rows, hp.n_rows, partial, pw);
   }
   return cudaGetLastError();
 }
 
+// Wide slabs (more than 32 chunks of 16 bytes) use two chunks per lane.
+template <int DT, bool HINT>
+cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s) {
+  bool wide = false;
+  for (int i = 0; i < a.nslabs; ++i) wide = wide || a.slab[i].width > a.slab[i].group * Vec<DT>::N;
+  return wide ? launch_cpl<DT, HINT, 2>(a, hp, partial, pw, s) : launch_cpl<DT, HINT, 1>(a, hp, partial, pw, s);
+}
+
 }  // namespace
 
+// Slabs of at most slab_cols columns.  Up to 32 * vn columns a slab gives each
+// lane of its row group one 16-byte chunk; wider slab_cols (wide mode) give
+// each lane two chunks when a slab has more than 16, so that rows of 17..64
+// chunks pack into groups of half the lanes (e.g. 144 BF16 columns: 2 rows
+// per warp instead of 1 with 14 idle lanes).
 int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out) {
   const int vn = dtype == DT_F32 ? 4 : 8;
-  int max_cols = 32 * vn;
+  const bool wide = slab_cols > 32 * vn;
+  int max_cols = 64 * vn;  // 32 lanes x two 16-byte chunks
   if (slab_cols > max_cols) slab_cols = max_cols;
   if (slab_cols < vn) slab_cols = vn;
   int n = 0;
@@ -381,7 +423,8 @@ int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out) {
     SpmmSlab sl{};
     sl.col0 = c0;
     sl.width = w;
-    sl.group = pow2_ceil((w + vn - 1) / vn);
+    const int chunks = (w + vn - 1) / vn;
+    sl.group = (wide && chunks > 16) ? pow2_ceil((chunks + 1) / 2) : pow2_ceil(chunks);
     out[n++] = sl;
   }
   return n;

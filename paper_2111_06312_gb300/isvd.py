@@ -107,6 +107,8 @@ def lib():
             L.isvd_small_svd.argtypes = [P, P, I32, P, P, P, P, P]
             L.isvd_closed_form.argtypes = [P, P, I64, P, P, I64, I32, P, I64, I32, C.c_double, P, I64, P]
             L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
+            L.isvd_autotune.argtypes = [P, I32, C.c_int, C.c_char_p, P, P]
+            L.isvd_selftest_wait.argtypes = [I32, P, P]
             L.isvd_batched_kernel_nodes.argtypes = []
             L.isvd_batched_kernel_nodes.restype = C.c_int64
             L.isvd_graph_kernel_nodes.argtypes = [P]
@@ -117,7 +119,7 @@ def lib():
             L.isvd_last_error.restype = C.c_char_p
             for name in ("isvd_create_operator", "isvd_operator_shape", "isvd_apply", "isvd_apply_T", "isvd_svd",
                          "isvd_gaussian", "isvd_philox_words", "isvd_orthonormalize", "isvd_small_svd",
-                         "isvd_closed_form", "isvd_svd_batched"):
+                         "isvd_closed_form", "isvd_svd_batched", "isvd_autotune", "isvd_selftest_wait"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -275,10 +277,11 @@ class Operator:
         return U, S, V, info
 
     # ---- launch shapes of the sparse products ----
-    _TUNING_FIELDS = ("slab_cols_f32", "slab_cols_bf16", "heavy_threshold", "heavy_chunk", "flags", "chunk_nnz")
+    _TUNING_FIELDS = ("slab_cols_f32", "slab_cols_bf16", "heavy_threshold", "heavy_chunk", "flags", "chunk_nnz",
+                      "l2_budget_mb")
 
     def tuning(self) -> dict:
-        t = (C.c_int32 * 6)()
+        t = (C.c_int32 * 7)()
         lib().isvd_get_tuning.argtypes = [C.c_void_p, C.c_void_p]
         lib().isvd_get_tuning.restype = C.c_int
         _check(lib().isvd_get_tuning(self._handle, t), "isvd_get_tuning")
@@ -305,10 +308,19 @@ class Operator:
             if kernel not in ("ring", "rows", "chunks"):
                 raise ValueError(f"unknown kernel {kernel!r}")
             vals[4] = (vals[4] & ~6) | {"ring": 4, "rows": 2, "chunks": 0}[kernel]
-        t = (C.c_int32 * 6)(*vals)
+        t = (C.c_int32 * 7)(*vals)
         lib().isvd_set_tuning.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib().isvd_set_tuning.restype = C.c_int
         _check(lib().isvd_set_tuning(self._handle, t, _stream()), "isvd_set_tuning")
+        return self.tuning()
+
+    def autotune(self, b: int, dtype=torch.float32, cache_path: str | None = None) -> dict:
+        """Time isvd_apply over the candidate launch shapes at block width b
+        and keep the fastest (isvd_autotune); returns the chosen tuning."""
+        code = F32 if dtype == torch.float32 else BF16
+        t = (C.c_int32 * 7)()
+        path = cache_path.encode() if cache_path else None
+        _check(lib().isvd_autotune(self._handle, int(b), code, path, t, _stream()), "isvd_autotune")
         return self.tuning()
 
     def graph_kernel_nodes(self) -> int:
@@ -442,3 +454,10 @@ class Batch:
     @staticmethod
     def kernel_nodes() -> int:
         return int(lib().isvd_batched_kernel_nodes())
+
+
+def selftest_wait(spin_limit: int = 1000, device="cuda") -> dict:
+    """Run the bounded-wait self-test; the returned status should be TIMEOUT."""
+    info = torch.zeros(4, dtype=torch.int32, device=device)
+    _check(lib().isvd_selftest_wait(int(spin_limit), _ptr(info), _stream()), "isvd_selftest_wait")
+    return info_dict(info)

@@ -46,7 +46,7 @@ def _time(fn, reps, flush):
 def set_tuning(op, slab32=None, slab16=None, heavy=None, chunk=None, hints=None, row_kernel=None, chunk_nnz=None):
     """Read-modify-write of isvd_tuning: [slab_f32, slab_bf16, heavy_threshold,
     heavy_chunk, flags (1 = L2 hints, 2 = row-group kernel), chunk_nnz]."""
-    t = (C.c_int32 * 6)()
+    t = (C.c_int32 * 7)()
     isvd.lib().isvd_get_tuning.argtypes = [C.c_void_p, C.c_void_p]
     isvd.lib().isvd_set_tuning.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     isvd.lib().isvd_get_tuning(op._handle, t)
@@ -120,13 +120,16 @@ def main():
                               "tuning": tun, **r}), flush=True)
         else:
             cases = [dict(kernel="rows", slab_cols_f32=128, slab_cols_bf16=256, cache_hints=h, hot_tags=t,
-                          rows_occupancy=o) for h, t in ((0, 0), (1, 0), (1, 1)) for o in (2, 3)]
-            cases += [dict(kernel="rows", slab_cols_f32=sc, slab_cols_bf16=2 * sc, cache_hints=1, hot_tags=1,
-                           rows_occupancy=o) for sc in (64, 96) for o in (2, 3)]
-            cases += [dict(kernel="rows", heavy_threshold=ht, heavy_chunk=ht, cache_hints=1, hot_tags=1,
-                           rows_occupancy=o) for ht in (64, 256) for o in (2, 3)]
-            cases += [dict(kernel="ring", chunk_nnz=512, cache_hints=1)]
+                          rows_occupancy=3, l2_budget_mb=96) for h, t in ((0, 0), (1, 0))]
+            cases += [dict(kernel="rows", slab_cols_f32=256, slab_cols_bf16=512, cache_hints=1, hot_tags=1,
+                           rows_occupancy=o, l2_budget_mb=mb) for o in (2, 3) for mb in (64, 96)]
+            cases += [dict(kernel="rows", slab_cols_f32=128, slab_cols_bf16=256, cache_hints=1, hot_tags=1,
+                           rows_occupancy=3, l2_budget_mb=mb) for mb in (24, 48, 64, 80, 96, 112, 128)]
+            cases += [dict(kernel="rows", slab_cols_f32=128, slab_cols_bf16=256, cache_hints=1, hot_tags=1,
+                           rows_occupancy=3, l2_budget_mb=64, heavy_threshold=ht, heavy_chunk=ht) for ht in (64, 256)]
             for kw in cases:
+                if a.dtype == "bf16" and kw.get("slab_cols_f32") == 256:
+                    kw = dict(kw, slab_cols_bf16=512)
                 tun = op.set_tuning(**kw)
                 r = spmm_case(g, op, a.width, a.dtype, a.reps, flush)
                 r.pop("all_ms")

@@ -104,7 +104,16 @@ def make_ops(g, norm, K, ones, adj, weighted, lowrank, seed=5):
     return gpu, oracle.graph_operator(g, **kw)
 
 
-KERNELS = ["ring", "chunks", "rows"]
+KERNELS = ["ring", "chunks", "rows", "rows_wide"]
+
+
+def tune(op, kernel, **kw):
+    """rows_wide: the row kernel with slabs wider than 32 lanes x 16 bytes
+    (two 16-byte chunks per lane)."""
+    if kernel == "rows_wide":
+        op.set_tuning(kernel="rows", slab_cols_f32=256, slab_cols_bf16=512, **kw)
+    else:
+        op.set_tuning(kernel=kernel, **kw)
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -115,7 +124,7 @@ def test_poly_apply_fp32(hub_graph, case, b, transpose, kernel):
     g = hub_graph
     gpu, ref = make_ops(g, *case)
     with gpu:
-        gpu.set_tuning(kernel=kernel, chunk_nnz=256)
+        tune(gpu, kernel, chunk_nnz=256)
         G = isvd.gaussian(3, g.n, b)
         Y = gpu.apply(G, transpose=transpose)
         Yr = ref.apply(npy(G), transpose=transpose)
@@ -129,7 +138,7 @@ def test_poly_apply_bf16(hub_graph, case, kernel):
     g = hub_graph
     gpu, ref = make_ops(g, *case)
     with gpu:
-        gpu.set_tuning(kernel=kernel)
+        tune(gpu, kernel)
         G = isvd.gaussian(4, g.n, 72, dtype=torch.bfloat16)
         Y = gpu.apply(G)
         Yr = ref.apply(npy(G))
@@ -143,7 +152,7 @@ def test_apply_empty_rows_and_hubs(kernel):
     assert (g.degrees() == 0).any() and g.degrees().max() > 600
     gpu, ref = make_ops(g, "sym", 5, True, False, False, False)
     with gpu:
-        gpu.set_tuning(kernel=kernel, chunk_nnz=64)
+        tune(gpu, kernel, chunk_nnz=64)
         for b in (5, 40, 130):
             for tr in (False, True):
                 G = isvd.gaussian(8, g.n, b)
@@ -181,7 +190,7 @@ def test_concat_apply(hub_graph, L, norm, dense, transpose, kernel):
         Xg = (d, x.rowptr, x.colidx, x.values)
         Xo = (d, x.rowptr, x.colidx, x.values.astype(np.float64))
     with isvd.graph_operator(g, form="concat", norm=norm, X=Xg, L=L) as gpu:
-        gpu.set_tuning(kernel=kernel, chunk_nnz=128)
+        tune(gpu, kernel, chunk_nnz=128)
         ref = oracle.graph_operator(g, form="concat", norm=norm, X=Xo, L=L)
         r, c = gpu.shape
         assert (r, c) == ref.shape
@@ -276,7 +285,7 @@ def test_svd_ne_small_parity(ne_small, kernel):
     """Cora-sized NE operator: k = 32, oversample 10, 4 power iterations."""
     g = ne_small
     with isvd.graph_operator(g, coeffs=C5, ones_coeff=-LAM) as gpu:
-        gpu.set_tuning(kernel=kernel)
+        tune(gpu, kernel)
         ref = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
         out = check_svd(gpu, ref, 32, 10, 4, synth.BASE_SEED)
     print(out)
@@ -305,7 +314,7 @@ def test_svd_concat_pubmed_sized(kernel):
     g, x = synth.workload_concat_graph()
     X = (x.d, x.rowptr, x.colidx, x.values)
     with isvd.graph_operator(g, form="concat", norm="sym", X=X, L=2) as gpu:
-        gpu.set_tuning(kernel=kernel)
+        tune(gpu, kernel)
         ref = oracle.graph_operator(g, form="concat", norm="sym",
                                     X=(x.d, x.rowptr, x.colidx, x.values.astype(np.float64)), L=2)
         out = check_svd(gpu, ref, 64, 10, 4, synth.BASE_SEED + 1)
