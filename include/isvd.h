@@ -229,7 +229,7 @@ ISVD_API isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t ro
  * when they need it (code running inside another framework's allocator or
  * memory-pool callback, latency-bound services that forbid cudaMalloc on the
  * hot path because it can synchronise the device).  Its scratch is one
- * file-scope device array of about 5 MB that every GPU which loads the
+ * file-scope device array of about 10 MB that every GPU which loads the
  * library holds until the process exits.
  *   - Same arguments and results as isvd_orthonormalize (no operator), but
  *     l <= ISVD_NOALLOC_MAX_BLOCK (64); larger l returns ISVD_ERR_UNSUPPORTED.

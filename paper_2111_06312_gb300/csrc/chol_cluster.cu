@@ -28,6 +28,7 @@ namespace {
 constexpr int kCholThreads = 512;
 constexpr int kNB = 16;
 constexpr int kCholMaxCluster = 16;
+constexpr double kReorthThreshold = 0.25;
 
 __host__ __device__ inline int cols_per_cta(int l, int cl) { return (l + cl - 1) / cl; }
 __host__ __device__ inline size_t packed_size(int l) { return (size_t)l * (l + 1) / 2; }
@@ -186,13 +187,27 @@ __global__ void __launch_bounds__(kCholThreads) chol_cluster_kernel(const double
     }
   }
   cluster.sync();  // no distributed-shared-memory access after this point
+  // From pass 2 on, R = chol(Q^T Q) of an already orthonormalised block should
+  // be close to I; a factor far from it (max |R - I| > kReorthThreshold) means
+  // the block entering this pass was still ill-conditioned, so one more pass
+  // is scheduled (the same gate as after a shift).
+  if (rank == 0 && ok && pass >= 2) {
+    double dev = 0.0;
+    for (int idx = tid; idx < l * l; idx += nt) {
+      const int i = idx / l, c = idx - i * l;
+      if (c >= i) dev = fmax(dev, fabs(X[packed_off(i, l) + (c - i)] - (i == c ? 1.0 : 0.0)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if (lane == 0 && dev > kReorthThreshold) atomicMax(&state[0], pass - 1);
+  }
   if (rank == 0 && tid == 0) {
     if (!ok) {
       state[1] = 1;
       atomicExch(&info->status, (int)ISVD_ERR_NOT_POSITIVE_DEFINITE);
     } else {
       if (shift > 0.0) {
-        state[0] = pass;
+        atomicMax(&state[0], pass);
         atomicAdd(&info->chol_shifts, 1);
       }
       atomicAdd(&info->cholqr_passes, 1);

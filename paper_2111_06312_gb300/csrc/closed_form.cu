@@ -75,6 +75,16 @@ __global__ void closed_form_reduce_kernel(const double *__restrict__ partial, in
 
 }  // namespace
 
+int32_t tn_tiles(int32_t p, int32_t q) { return ((p + kTnTile - 1) / kTnTile) * ((q + kTnTile - 1) / kTnTile); }
+
+cudaError_t tn_partial_launch(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t rows, int32_t p,
+                              int32_t q, double *partial, int32_t nparts, cudaStream_t s) {
+  const int64_t rpp = round_up(ceil_div(rows, nparts), kTnRows);
+  tn_partial_kernel<<<dim3((unsigned)nparts, (unsigned)tn_tiles(p, q)), 256, 0, s>>>(A, lda, B, ldb, rows, p, q, rpp,
+                                                                                      partial);
+  return cudaGetLastError();
+}
+
 int32_t closed_form_parts(int64_t rows, int32_t k, int32_t m) {
   const int tiles = ((k + kTnTile - 1) / kTnTile) * ((m + kTnTile - 1) / kTnTile);
   int64_t parts = ceil_div(rows, 1024);

@@ -7,7 +7,8 @@
 // panel, so it is stored and multiplied for those columns only (MMA N shrinks
 // panel by panel, and its accumulator starts at that column).  Q is streamed in
 // 128-row tiles, panel by panel, by cp.async straight into the swizzled
-// layout (row r of the tile = 128 bytes of row r of Q).  FP32 blocks use
+// layout (row r of the tile = 128 bytes of row r of Q), three panels ahead of
+// the two operand stages the MMA reads.  FP32 blocks use
 // 3xTF32 (A and B split into TF32 hi + lo); BF16 blocks one BF16 MMA.  The
 // FP32 accumulator (128 x round16(l)) is double-buffered in tensor memory so
 // the epilogue warps write tile t while tile t+1 is multiplied.
@@ -26,7 +27,8 @@ constexpr int kProd = kProdWarps * 32;
 constexpr int kMmaWarp = kProdWarps;       // warp 8
 constexpr int kEpiWarp0 = kProdWarps + 1;  // warps 9..12
 constexpr int kThreads = (kProdWarps + 1 + 4) * 32;
-constexpr int kStages = 3;
+constexpr int kStages = 2;  // operand stages shared with the MMA warp
+constexpr int kMaxSmem = 225 * 1024;  // dynamic; the static barriers take the rest of the 227 KB
 constexpr int kTmemCols = 512;
 constexpr int kDBufCol = 256;  // column offset of accumulator buffer 1
 
@@ -69,7 +71,9 @@ __host__ __device__ Layout make_layout(int l) {
   return L;
 }
 
-template <int DT>
+// kRaw: raw panels in flight (refilled by the producers alone); 3 where the
+// shared memory allows, else 2.
+template <int DT, int kRaw>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, const float *__restrict__ B,
                    int64_t ldb, const int32_t *gate_state, int32_t gate_pass, int32_t *err_state) {
@@ -84,6 +88,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char *bhi = sm;
   unsigned char *blo = sm + L.bbytes;                         // F32 only
   unsigned char *astage = sm + C::NT * L.bbytes;              // [kStages][NT][16 KB]
+  unsigned char *rawring = astage + (size_t)kStages * C::STAGE;  // [kRaw][16 KB]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (rows + 127) / 128;
   const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], kProd);
+      mbar_init(&full[s], 1);  // one arrive after the producers' barrier
       mbar_init(&empty[s], 1);
     }
     for (int d = 0; d < 2; ++d) {
@@ -130,25 +135,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp < kProdWarps) {
     // ---------------- producers: stream A panels ----------------
+    // Raw panels land in a ring of kRaw stages (cp.async, swizzled layout) that
+    // the producers refill as soon as they have transformed a panel, so loads
+    // run ahead of the MMA; the transform writes the operand stage (TF32 hi / lo
+    // or BF16 with padding columns zeroed) once the MMA has released it.
     auto tile_row0 = [&](int64_t lt) { return ((int64_t)blockIdx.x + lt * gridDim.x) * 128; };
     auto issue = [&](int64_t g) {
-      const int s = (int)(g % kStages);
-      const int64_t lt = g / L.KP;
-      const int p = (int)(g - lt * L.KP);
-      unsigned char *ahi = astage + (size_t)s * C::STAGE;
-      const int64_t rb = tile_row0(lt);
-      for (int t = tid; t < 128 * 8; t += kProd) {  // 128 rows x 8 pieces of 16 bytes
-        const int r = t >> 3, q = t & 7;
-        const int64_t row = rb + r;
-        const int64_t colb = (int64_t)p * 128 + q * 16;   // byte offset in the row
-        const bool ok = row < rows && colb < ldq * C::ES;
-        const char *src = ok ? Q + ((size_t)row * ldq) * C::ES + colb : Q;
-        cp_async16_zfill(smem_u32(ahi + sw128(r, q * 16)), src, ok ? 16u : 0u);
+      if (g < G) {
+        const int64_t lt = g / L.KP;
+        const int p = (int)(g - lt * L.KP);
+        unsigned char *rb = rawring + (size_t)(g % kRaw) * (128 * 128);
+        const int64_t r0 = tile_row0(lt);
+        for (int t = tid; t < 128 * 8; t += kProd) {  // 128 rows x 8 pieces of 16 bytes
+          const int r = t >> 3, q = t & 7;
+          const int64_t row = r0 + r;
+          const int64_t colb = (int64_t)p * 128 + q * 16;   // byte offset in the row
+          const bool ok = row < rows && colb < ldq * C::ES;
+          const char *src = ok ? Q + ((size_t)row * ldq) * C::ES + colb : Q;
+          cp_async16_zfill(smem_u32(rb + sw128(r, q * 16)), src, ok ? 16u : 0u);
+        }
       }
+      cp_async_commit();  // one group per panel (empty past the end) keeps the wait count fixed
     };
     auto transform = [&](int64_t g) {
       const int s = (int)(g % kStages);
       const int p = (int)(g % L.KP);
+      const unsigned char *rb = rawring + (size_t)(g % kRaw) * (128 * 128);
       unsigned char *ahi = astage + (size_t)s * C::STAGE;
       unsigned char *alo = ahi + 128 * 128;
       for (int t = tid; t < 128 * 8; t += kProd) {
@@ -156,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t off = sw128(r, q * 16);
         const int k0 = p * C::KE + q * (16 / C::ES);  // first column of this piece
         if (C::F32) {
-          float4 v = *reinterpret_cast<float4 *>(ahi + off);
+          const float4 v = *reinterpret_cast<const float4 *>(rb + off);
           float x[4] = {v.x, v.y, v.z, v.w}, hi[4], lo[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
@@ -165,40 +177,33 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           *reinterpret_cast<float4 *>(ahi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
           *reinterpret_cast<float4 *>(alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
-        } else if (k0 + 8 > l) {
-          unsigned short *h = reinterpret_cast<unsigned short *>(ahi + off);
+        } else {
+          uint4 v = *reinterpret_cast<const uint4 *>(rb + off);
+          if (k0 + 8 > l) {
+            unsigned short *h = reinterpret_cast<unsigned short *>(&v);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (k0 + j >= l) h[j] = 0;
+            for (int j = 0; j < 8; ++j)
+              if (k0 + j >= l) h[j] = 0;
+          }
+          *reinterpret_cast<uint4 *>(ahi + off) = v;
         }
       }
     };
-    int64_t next_issue = 0;
+    for (int64_t g = 0; g < kRaw - 1; ++g) issue(g);
     for (int64_t g = 0; g < G; ++g) {
-      // keep two panels in flight ahead of the one being transformed
-      while (next_issue < G && next_issue <= g + 2) {
-        const int s = (int)(next_issue % kStages);
-        if (tid == 0 && next_issue >= kStages &&
-            !mbar_wait(&empty[s], (uint32_t)(((next_issue / kStages) & 1) ^ 1))) {
-          abort_flag = 1;
-          if (err_state) atomicExch(&err_state[2], 1);
-        }
-        producer_bar();
-        if (abort_flag) break;
-        issue(next_issue);
-        cp_async_commit();
-        ++next_issue;
+      issue(g + kRaw - 1);           // into the raw stage transformed in the previous iteration
+      cp_async_wait<kRaw - 1>();     // this thread's copies of panel g have landed
+      const int s = (int)(g % kStages);
+      if (tid == 0 && g >= kStages && !mbar_wait(&empty[s], (uint32_t)(((g / kStages) & 1) ^ 1))) {
+        abort_flag = 1;
+        if (err_state) atomicExch(&err_state[2], 1);
       }
+      producer_bar();  // every producer's copies of panel g landed; operand stage s is free
       if (abort_flag) break;
-      // wait until panel g has landed: at most (next_issue - 1 - g) younger groups pending
-      const int64_t younger = next_issue - 1 - g;
-      if (younger >= 2) cp_async_wait<2>();
-      else if (younger == 1) cp_async_wait<1>();
-      else cp_async_wait<0>();
-      producer_bar();
       transform(g);
       fence_async_shared();
-      mbar_arrive(&full[g % kStages]);
+      producer_bar();  // the operand stage is written (and the raw stage of panel g may be refilled)
+      if (tid == 0) mbar_arrive(&full[s]);
     }
     cp_async_wait<0>();
   } else if (warp == kMmaWarp) {
@@ -287,10 +292,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int DT>
-size_t gemm_tc_smem(int32_t l) {
+size_t gemm_tc_smem(int32_t l, int raw) {
   using C = GemmCfg<DT>;
   const Layout L = make_layout<DT>(l);
-  return (size_t)C::NT * L.bbytes + (size_t)kStages * C::STAGE + 1024;
+  return (size_t)C::NT * L.bbytes + (size_t)kStages * C::STAGE + (size_t)raw * 128 * 128 + 1024;
 }
 
 std::once_flag g_once;
@@ -300,14 +305,29 @@ cudaError_t g_err = cudaSuccess;
 
 cudaError_t gemm_tc_init() {
   std::call_once(g_once, [] {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<DT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gemm_tc_smem<DT_F32>(ISVD_MAX_BLOCK));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tc_kernel<DT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)gemm_tc_smem<DT_BF16>(ISVD_MAX_BLOCK));
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *fn) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    };
+    set((const void *)gemm_tc_kernel<DT_F32, 2>);
+    set((const void *)gemm_tc_kernel<DT_F32, 3>);
+    set((const void *)gemm_tc_kernel<DT_BF16, 2>);
+    set((const void *)gemm_tc_kernel<DT_BF16, 3>);
     g_err = e;
   });
   return g_err;
+}
+
+template <int DT>
+void launch_gemm(void *Q, int64_t ldq, int64_t rows, int32_t l, const float *B, int64_t ldb, PassGate g, int grid,
+                 cudaStream_t s) {
+  int32_t *err = const_cast<int32_t *>(g.state);
+  const size_t s3 = gemm_tc_smem<DT>(l, 3);
+  if (s3 <= (size_t)kMaxSmem)
+    gemm_tc_kernel<DT, 3><<<grid, kThreads, s3, s>>>(Q, ldq, rows, l, B, ldb, g.state, g.pass, err);
+  else
+    gemm_tc_kernel<DT, 2><<<grid, kThreads, gemm_tc_smem<DT>(l, 2), s>>>(Q, ldq, rows, l, B, ldb, g.state, g.pass,
+                                                                          err);
 }
 
 cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, const float *B,
@@ -316,12 +336,8 @@ cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t row
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (rows + 127) / 128;
   const int grid = (int)std::min<int64_t>(ntiles, kNumSMs);
-  int32_t *err = const_cast<int32_t *>(g.state);
-  if (dtype == DT_F32)
-    gemm_tc_kernel<DT_F32><<<grid, kThreads, gemm_tc_smem<DT_F32>(l), s>>>(Q, ldq, rows, l, B, ldb, g.state, g.pass, err);
-  else
-    gemm_tc_kernel<DT_BF16><<<grid, kThreads, gemm_tc_smem<DT_BF16>(l), s>>>(Q, ldq, rows, l, B, ldb, g.state, g.pass,
-                                                                            err);
+  if (dtype == DT_F32) launch_gemm<DT_F32>(Q, ldq, rows, l, B, ldb, g, grid, s);
+  else launch_gemm<DT_BF16>(Q, ldq, rows, l, B, ldb, g, grid, s);
   return cudaGetLastError();
 }
 

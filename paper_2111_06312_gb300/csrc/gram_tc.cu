@@ -4,16 +4,20 @@
 // Q is n x l row-major (l <= 160).  Each CTA reduces a contiguous range of
 // rows: 32 (FP32) or 64 (BF16) rows at a time are copied raw into shared
 // memory with cp.async (four chunks in flight), then producer warps write the
-// transposed chunk as a K-major operand tile (128-byte swizzle): row m of the
-// tile holds column m of Q over the chunk's rows.  The same tile is both MMA
+// transposed chunk as a K-major operand tile (128-byte swizzle; three tile
+// stages): row m of the tile holds column m of Q over the chunk's rows.  The same tile is both MMA
 // operands (A rows and B rows are both columns of Q):
 //   tile 1: W[0:128, 0:N1]      M = 128, N = round16(l)
 //   tile 2: W[128:256, 128:N1]  M = 128, N = round16(l - 128)   (l > 128)
 // and W[128:, :128] is the transpose of tile 1's right part.  FP32 blocks use
 // 3xTF32 (x = hi + lo with hi in TF32: hi*hi + hi*lo + lo*hi); BF16 blocks use
-// one BF16 MMA (exact products).  Accumulators stay in tensor memory for the
-// whole row range; each CTA writes its l x l partial, combined in FP64 in a
-// fixed order by gram_reduce (deterministic).
+// one BF16 MMA (exact products).  The tensor cores' FP32 accumulation loses
+// a little on every addition, and over thousands of rows the loss adds up
+// (CholeskyQR2's orthogonality fell linearly with the rows per CTA, 1.2e-4
+// at 6,600), so each 256-row segment is accumulated in tensor memory (two
+// buffers, alternating) and four epilogue warps add it into the CTA's FP64
+// partial (kept in L2) while the next segment is multiplied.  The partials
+// are combined in FP64 in a fixed order by gram_reduce (deterministic).
 #include <mutex>
 
 #include "internal.h"
@@ -26,11 +30,15 @@ using namespace tc;
 
 constexpr int kProdWarps = 8;
 constexpr int kProd = kProdWarps * 32;
-constexpr int kThreads = kProd + 32;  // + MMA warp
+constexpr int kMmaWarp = kProdWarps;       // warp 8
+constexpr int kEpiWarp0 = kProdWarps + 1;  // warps 9..12
+constexpr int kThreads = kProd + 32 + 128;
 constexpr int kRawStages = 4;
-constexpr int kTileStages = 2;
-constexpr int kTmemCols = 256;
+constexpr int kTileStages = 3;
+constexpr int kTmemCols = 512;
+constexpr int kAccCols = 256;  // accumulator buffer b at column b * kAccCols
 constexpr int kTile2Col = 192;
+constexpr int kSegRows = 256;  // rows summed in tensor memory before promotion to FP64
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
@@ -52,16 +60,20 @@ struct GramCfg {
 
 template <int DT>
 __global__ void __launch_bounds__(kThreads, 1)
-    gram_tc_kernel(const void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, float *__restrict__ partial,
+    gram_tc_kernel(const void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, double *__restrict__ partial,
                    int64_t rows_per_cta, const int32_t *gate_state, int32_t gate_pass, int32_t *err_state) {
   using C = GramCfg<DT>;
   if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
-  const int MT = l > 128 ? 256 : 128;
-  const int tile_bytes = MT * 128;
+  // A tile holds round8(l) rows (at least 128, the MMA's M).  For l > 128 the
+  // second MMA (M = 128 from row 128) also reads the bytes after the tile's
+  // last row: they lie inside the next buffer of the same allocation and only
+  // reach accumulator rows >= l - 128 of that MMA, which are never read.
+  const int TR = l > 128 ? (l + 7) & ~7 : 128;
+  const int tile_bytes = TR * 128;
   const int lp = (l + 7) & ~7;                     // raw row pitch in elements (16-byte multiple)
   const int raw_bytes = C::BK * lp * C::ES;
   extern __shared__ __align__(1024) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full[kTileStages], empty[kTileStages], done;
+  __shared__ __align__(8) uint64_t full[kTileStages], empty[kTileStages], seg_full[2], seg_free[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   unsigned char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
@@ -71,6 +83,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r1 = min(rows, r0 + rows_per_cta);
   const int nchunks = r1 > r0 ? (int)((r1 - r0 + C::BK - 1) / C::BK) : 0;
+  constexpr int F = kSegRows / C::BK;  // chunks per segment
+  const int nseg = (nchunks + F - 1) / F;
   const int N1 = (l + 15) & ~15;
   const int N2 = l > 128 ? ((l - 128 + 15) & ~15) : 0;
 
@@ -78,10 +92,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     reinterpret_cast<uint4 *>(tiles)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     for (int s = 0; s < kTileStages; ++s) {
-      mbar_init(&full[s], kProd);
+      mbar_init(&full[s], 1);  // one arrive after the producers' barrier
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&seg_full[b], 1);
+      mbar_init(&seg_free[b], 128);
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -154,86 +171,109 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       fence_async_shared();
-      mbar_arrive(&full[s]);
-      producer_bar();  // raw buffer of chunk c may be refilled after this
+      producer_bar();  // the tile is written (and the raw buffer of chunk c may be refilled)
+      if (tid == 0) mbar_arrive(&full[s]);
     }
     cp_async_wait<0>();
-  } else if (lane == 0) {
-    // ---------------- MMA issuer ----------------
-    const uint32_t fmt = C::F32 ? 2u : 1u;
-    const uint32_t id1 = idesc(fmt, 128, N1);
-    const uint32_t id2 = idesc(fmt, 128, N2 > 0 ? N2 : 16);
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c % kTileStages;
-      if (abort_flag || !mbar_wait(&full[s], (c / kTileStages) & 1)) {
-        if (err_state) atomicExch(&err_state[2], 1);
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t fmt = C::F32 ? 2u : 1u;
+      const uint32_t id1 = idesc(fmt, 128, N1);
+      const uint32_t id2 = idesc(fmt, 128, N2 > 0 ? N2 : 16);
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c % kTileStages;
+        const int seg = c / F, b = seg & 1, cs = c - seg * F;
+        if (cs == 0 && seg >= 2 && !mbar_wait(&seg_free[b], (uint32_t)(((seg >> 1) - 1) & 1))) {
+          if (err_state) atomicExch(&err_state[2], 1);
+          abort_flag = 1;
+          break;
+        }
+        if (abort_flag || !mbar_wait(&full[s], (c / kTileStages) & 1)) {
+          if (err_state) atomicExch(&err_state[2], 1);
+          abort_flag = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * kAccCols);
+        const uint32_t hi = smem_u32(tiles + (size_t)(s * C::NT) * tile_bytes);
+        const uint32_t lo = hi + tile_bytes;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t acc = (cs > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t ah = desc_sw128(hi + kk * 32, 1024);
+          if (C::F32) {
+            const uint64_t al = desc_sw128(lo + kk * 32, 1024);
+            mma_tf32(d, ah, ah, id1, acc);
+            mma_tf32(d, ah, al, id1, 1u);
+            mma_tf32(d, al, ah, id1, 1u);
+            if (N2) {
+              const uint64_t bh = desc_sw128(hi + 16384 + kk * 32, 1024);
+              const uint64_t bl = desc_sw128(lo + 16384 + kk * 32, 1024);
+              mma_tf32(d + kTile2Col, bh, bh, id2, acc);
+              mma_tf32(d + kTile2Col, bh, bl, id2, 1u);
+              mma_tf32(d + kTile2Col, bl, bh, id2, 1u);
+            }
+          } else {
+            mma_bf16(d, ah, ah, id1, acc);
+            if (N2) {
+              const uint64_t bh = desc_sw128(hi + 16384 + kk * 32, 1024);
+              mma_bf16(d + kTile2Col, bh, bh, id2, acc);
+            }
+          }
+        }
+        commit(&empty[s]);
+        if (cs == F - 1 || c == nchunks - 1) commit(&seg_full[b]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: each segment's sums -> the FP64 partial ----------------
+    // Partial layout: P[n][i] = W[i][n] for i < 128 (tile 1, every n < l) and
+    // P[128 + b][128 + a] = W[128 + a][128 + b] (tile 2); W is symmetric and the
+    // reduction maps the rest.  Thread (quarter q, lane) owns W row i = 32 q + lane;
+    // the quarter-0 warp also owns tile 2's rows.
+    double *P = partial + (size_t)blockIdx.x * l * l;
+    const int q = warp & 3;  // a warp reads the tensor-memory lanes of its quarter, 32 (warp % 4)
+    const int i = q * 32 + lane;
+    uint32_t r[32];
+    for (int seg = 0; seg < nseg; ++seg) {
+      const int b = seg & 1;
+      if (!mbar_wait(&seg_full[b], (uint32_t)((seg >> 1) & 1))) {
+        if (err_state && lane == 0) atomicExch(&err_state[2], 1);
         break;
       }
       fence_after();
-      const uint32_t hi = smem_u32(tiles + (size_t)(s * C::NT) * tile_bytes);
-      const uint32_t lo = hi + tile_bytes;
+      const uint32_t d = tmem + (uint32_t)(b * kAccCols) + ((uint32_t)(q * 32) << 16);
+      // 32 columns at a time: all loads of the running sums first, then the
+      // adds and stores (no load waits behind a store)
+      auto promote = [&](uint32_t taddr, double *base, int64_t stride, int ncols) {
+        tmem_ld32(taddr, r);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-        const uint64_t ah = desc_sw128(hi + kk * 32, 1024);
-        if (C::F32) {
-          const uint64_t al = desc_sw128(lo + kk * 32, 1024);
-          mma_tf32(tmem, ah, ah, id1, acc);
-          mma_tf32(tmem, ah, al, id1, 1u);
-          mma_tf32(tmem, al, ah, id1, 1u);
-          if (N2) {
-            const uint64_t bh = desc_sw128(hi + 16384 + kk * 32, 1024);
-            const uint64_t bl = desc_sw128(lo + 16384 + kk * 32, 1024);
-            mma_tf32(tmem + kTile2Col, bh, bh, id2, acc);
-            mma_tf32(tmem + kTile2Col, bh, bl, id2, 1u);
-            mma_tf32(tmem + kTile2Col, bl, bh, id2, 1u);
-          }
-        } else {
-          mma_bf16(tmem, ah, ah, id1, acc);
-          if (N2) {
-            const uint64_t bh = desc_sw128(hi + 16384 + kk * 32, 1024);
-            mma_bf16(tmem + kTile2Col, bh, bh, id2, acc);
-          }
+        for (int h = 0; h < 32; h += 16) {
+          double old[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            old[j] = (seg > 0 && h + j < ncols) ? __ldcg(base + (int64_t)(h + j) * stride) : 0.0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (h + j < ncols) __stcg(base + (int64_t)(h + j) * stride, old[j] + (double)__uint_as_float(r[h + j]));
         }
+      };
+      for (int cb = 0; cb < N1; cb += 32) {
+        const int ncols = i < l ? min(32, l - cb) : 0;
+        promote(d + cb, P + (size_t)cb * l + i, l, ncols);
       }
-      commit(&empty[s]);
+      if (N2 && q == 0) {
+        const int a = lane;  // W row 128 + a; column 128 + j of tile 2
+        const int ncols = 128 + a < l ? min(N2, l - 128) : 0;
+        promote(d + kTile2Col, P + (size_t)128 * l + 128 + a, l, ncols);
+      }
+      fence_before();
+      mbar_arrive(&seg_free[b]);
     }
-    commit(&done);
-  }
-  // ---------------- epilogue: TMEM -> partial ----------------
-  __syncwarp();
-  const bool ok = mbar_wait(&done, 0);
-  if (!ok && err_state && tid == 0) atomicExch(&err_state[2], 1);
-  fence_after();
-  float *P = partial + (size_t)blockIdx.x * l * l;
-  if (nchunks == 0 || !ok) {
-    for (int i = tid; i < l * l; i += blockDim.x) P[i] = 0.f;
-  } else if (warp < 4) {
-    const int i = warp * 32 + lane;  // W row
-    uint32_t r[32];
-    for (int cb = 0; cb < N1; cb += 32) {
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cb, r);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = cb + j;
-        if (i < l && n < l) {
-          const float v = __uint_as_float(r[j]);
-          P[(size_t)i * l + n] = v;
-          if (n >= 128) P[(size_t)n * l + i] = v;  // W[128:, :128] by symmetry
-        }
-      }
-    }
-  } else if (warp < 8 && N2 > 0) {
-    const int w4 = warp - 4;
-    const int i = 128 + w4 * 32 + lane;
-    uint32_t r[32];
-    for (int cb = 0; cb < N2; cb += 32) {
-      tmem_ld32(tmem + ((uint32_t)(w4 * 32) << 16) + kTile2Col + cb, r);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = 128 + cb + j;
-        if (i < l && n < l) P[(size_t)i * l + n] = __uint_as_float(r[j]);
-      }
+    if (nseg == 0) {
+      // no rows here: this partial is zero
+      for (int idx = i; idx < l * l; idx += 128) P[idx] = 0.0;
     }
   }
   fence_before();
@@ -241,22 +281,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-__global__ void gram_reduce_tc_kernel(const float *partial, int32_t n_part, int32_t l, double *W,
+// W[r][c] = sum over partials of P[r][c], except the block r < 128 <= c,
+// which tile 1 stored transposed (P[c][r]).
+__global__ void gram_reduce_tc_kernel(const double *partial, int32_t n_part, int32_t l, double *W,
                                       const int32_t *gate_state, int32_t gate_pass) {
   if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)l * l) return;
+  const int r = (int)(idx / l), c = (int)(idx - (int64_t)r * l);
+  const int64_t src = (r < 128 && c >= 128) ? (int64_t)c * l + r : idx;
   double s = 0.0;
-  for (int p = 0; p < n_part; ++p) s += (double)partial[(int64_t)p * l * l + idx];
+  for (int p = 0; p < n_part; ++p) s += partial[(int64_t)p * l * l + src];
   W[idx] = s;
 }
 
 template <int DT>
 size_t gram_tc_smem(int32_t l) {
   using C = GramCfg<DT>;
-  const int MT = l > 128 ? 256 : 128;
+  const int TR = l > 128 ? (l + 7) & ~7 : 128;
   const int lp = (l + 7) & ~7;
-  return (size_t)kTileStages * C::NT * MT * 128 + (size_t)kRawStages * C::BK * lp * C::ES + 1024;
+  // tiles, then the raw ring (at least 16 KB after the last tile, see above)
+  return (size_t)kTileStages * C::NT * TR * 128 + (size_t)kRawStages * C::BK * lp * C::ES + 1024;
 }
 
 std::once_flag g_once;
@@ -283,7 +328,7 @@ int32_t gram_partials(int64_t rows) {
   return (int32_t)p;
 }
 
-cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, float *partial, int32_t n_part,
+cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, double *partial, int32_t n_part,
                         double *W, PassGate g, cudaStream_t s) {
   cudaError_t e = gram_tc_init();
   if (e != cudaSuccess) return e;

@@ -153,7 +153,7 @@ cudaError_t lowrank_project_launch(const void *G, int64_t ldg, int dtype, int64_
                                    double *partial, int32_t n_part, float *c, int64_t ldc, cudaStream_t s);
 int32_t lowrank_partials(int64_t rows);
 
-// Gram W (FP64, l x l) = Q^T Q over rows; partial workspace n_part x l x l FP32.
+// Gram W (FP64, l x l) = Q^T Q over rows; partial workspace n_part x l x l FP64.
 // gate: when non-null and *gate_flag says so, the kernels return at once
 // (conditional CholeskyQR passes).
 struct PassGate {
@@ -161,7 +161,7 @@ struct PassGate {
   int32_t pass = 0;                // 1-based pass number; passes > 2 are conditional
 };
 int32_t gram_partials(int64_t rows);
-cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, float *partial,
+cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, double *partial,
                         int32_t n_part, double *W, PassGate g, cudaStream_t s);
 
 // Q <- Q B in place on the tensor cores, B (l x l, FP32) upper triangular.
@@ -179,6 +179,21 @@ int32_t closed_form_parts(int64_t rows, int32_t k, int32_t m);
 cudaError_t closed_form_launch(const float *U, int64_t ldu, const float *S, const float *V, int64_t ldv, int64_t r,
                                int64_t c, int32_t k, const float *Y, int64_t ldy, int32_t m, double rcond,
                                float *W, int64_t ldw, double *partial, int32_t nparts, float *Z, cudaStream_t s);
+
+// C (p x q, FP64 partials per row part) = A^T B over `rows` rows (closed_form.cu).
+int32_t tn_tiles(int32_t p, int32_t q);
+cudaError_t tn_partial_launch(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t rows, int32_t p,
+                              int32_t q, double *partial, int32_t nparts, cudaStream_t s);
+
+// Dense X in the CONCAT operator (xdense.cu): P = X [G_0 | ... | G_L] and
+// out_l = X^T P_l (P_0 = H copied into segment 0).  Scratch: xdense_scratch_bytes.
+int32_t xdense_parts(int64_t n, int32_t d, int32_t q);
+size_t xdense_scratch_bytes(int32_t d, int32_t segs, int32_t bseg, int64_t n);
+cudaError_t xdense_forward(const float *X, int64_t n, int32_t d, const void *G, int64_t ldg, int dtype, int32_t b,
+                           int32_t bseg, int32_t segs, void *P, int64_t ldp, void *scratch, cudaStream_t s);
+cudaError_t xdense_transpose(const float *X, int64_t n, int32_t d, const float *H, int64_t ldh, int32_t b,
+                             int32_t bseg, int32_t segs, float *P, int64_t ldp, float *out, int64_t ldo, void *scratch,
+                             cudaStream_t s);
 
 // ---- small FP64 kernels -------------------------------------------------------
 // Orthonormalisation state block (device, int32[8]):
@@ -209,7 +224,7 @@ cudaError_t dense_kernels_init();
 
 // Device buffers of one orthonormalisation (CholeskyQR2 with shift).
 struct OrthBufs {
-  float *gram_partial = nullptr;  // n_part x l x l FP32
+  double *gram_partial = nullptr;  // n_part x l x l FP64
   double *W = nullptr, *tmp = nullptr;  // l x l FP64 each
   float *Rinv = nullptr;          // l x l FP32
   int32_t *state = nullptr;       // kOrthStateInts
@@ -279,6 +294,7 @@ struct ApplyScratch {
   float *lr_c = nullptr;
   double *lr_partial = nullptr;
   float *heavy_partial = nullptr;
+  void *xdense = nullptr;  // dense-X products (CONCAT with dense X)
 };
 size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool transpose);
 void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool transpose, char *base,

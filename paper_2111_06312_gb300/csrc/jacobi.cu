@@ -11,8 +11,9 @@
 // barrier per step).  Rotations are not accumulated: after convergence the
 // columns w_p of G J have norms sigma_p, Vo = W Sigma^-1 and
 // Uo = J = A W Sigma^-2 (A A^T j_p = sigma_p^2 j_p), one FP64 product.
-// Rotation: Rutishauser's formula; converged when every pair satisfies
-// |g_p.g_q| <= tol ||g_p|| ||g_q||, tol = max(1e-15, sqrt(l) eps).
+// Rotation: Rutishauser's formula, column norms carried along (recomputed each
+// sweep); converged when every pair satisfies |g_p.g_q| <= tol ||g_p|| ||g_q||,
+// tol = max(1e-15, sqrt(l) eps).
 #include <cooperative_groups.h>
 
 #include <mutex>
@@ -37,26 +38,33 @@ __device__ __forceinline__ void warp_sum3(double &a, double &b, double &c) {
   }
 }
 
-// One warp rotates columns gp, gq (length l) if they are not yet orthogonal.
-__device__ __forceinline__ int rotate_pair(double *gp, double *gq, int l, int lane, double tol, double tiny) {
-  double al = 0.0, be = 0.0, ga = 0.0;
-  for (int i = lane; i < l; i += 32) {
-    const double x = gp[i], y = gq[i];
-    al += x * x;
-    be += y * y;
-    ga += x * y;
-  }
-  warp_sum3(al, be, ga);
+// One warp rotates columns gp, gq (length l, squared norms *np, *nq kept by the
+// caller) if they are not yet orthogonal.  Only g_p . g_q is summed; the norms
+// follow the rotation in closed form (||g_p'||^2 = ||g_p||^2 - t g_p.g_q,
+// ||g_q'||^2 = ||g_q||^2 + t g_p.g_q) and are recomputed exactly every sweep.
+__device__ __forceinline__ int rotate_pair(double *gp, double *gq, double *np, double *nq, int l, int lane,
+                                           double tol, double tiny) {
+  double ga = 0.0;
+  for (int i = lane; i < l; i += 32) ga += gp[i] * gq[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  const double al = *np, be = *nq;
   if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) return 0;
   if (al <= tiny && be <= tiny) return 0;
   const double zeta = (be - al) / (2.0 * ga);
   const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+  const double cs = rsqrt(1.0 + t * t), sn = cs * t;
   for (int i = lane; i < l; i += 32) {
     const double x = gp[i], y = gq[i];
     gp[i] = cs * x - sn * y;
     gq[i] = sn * x + cs * y;
   }
+  __syncwarp();
+  if (lane == 0) {
+    *np = al - t * ga;
+    *nq = be + t * ga;
+  }
+  __syncwarp();
   return 1;
 }
 
@@ -82,12 +90,14 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
   const int nb = 2 * CL;
   const int l3 = nb * bs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  extern __shared__ double sm[];  // [2 buffers][2 slots][bs][l]
+  extern __shared__ double sm[];  // [2 buffers][2 slots][bs][l], then norms [2 buffers][2 slots][bs]
   __shared__ int ids[2][2];
   __shared__ int any_flags[kJacMaxCluster];
   __shared__ int stop;
   __shared__ double red[kJacThreads / 32];
   auto colp = [&](int buf, int slot, int j) { return sm + ((size_t)(buf * 2 + slot) * bs + j) * l; };
+  double *nrm = sm + (size_t)4 * bs * l;
+  auto nrmp = [&](int buf, int slot, int j) { return nrm + (buf * 2 + slot) * bs + j; };
 
   if (tid == 0) {
     ids[0][0] = c;
@@ -117,13 +127,25 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
   cluster.sync();
   for (int sweep = 0; sweep < 60; ++sweep) {
     int rotated = 0;
+    // exact squared norms of the columns held here
+    for (int q = warp; q < 2 * bs; q += nwarp) {
+      const double *g = colp(cur, q / bs, q % bs);
+      double s2 = 0.0;
+      for (int i = lane; i < l; i += 32) s2 += g[i] * g[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) *nrmp(cur, q / bs, q % bs) = s2;
+    }
+    __syncthreads();
     // pairs inside each of the two blocks held here
     for (int r = 0; r < bsp - 1; ++r) {
       for (int pi = warp; pi < bsp; pi += nwarp) {  // bsp/2 pairs per slot, two slots
         const int slot = pi / (bsp / 2), kk = pi - slot * (bsp / 2);
         int p, q;
         tourney(r, kk, bsp, p, q);
-        if (p < bs && q < bs) rotated |= rotate_pair(colp(cur, slot, p), colp(cur, slot, q), l, lane, tol, tiny);
+        if (p < bs && q < bs)
+          rotated |= rotate_pair(colp(cur, slot, p), colp(cur, slot, q), nrmp(cur, slot, p), nrmp(cur, slot, q), l,
+                                 lane, tol, tiny);
       }
       __syncthreads();
     }
@@ -131,7 +153,8 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
     for (int step = 0; step < nb - 1; ++step) {
       for (int r = 0; r < bs; ++r) {
         for (int i = warp; i < bs; i += nwarp)
-          rotated |= rotate_pair(colp(cur, 0, i), colp(cur, 1, (i + r) % bs), l, lane, tol, tiny);
+          rotated |= rotate_pair(colp(cur, 0, i), colp(cur, 1, (i + r) % bs), nrmp(cur, 0, i),
+                                 nrmp(cur, 1, (i + r) % bs), l, lane, tol, tiny);
         __syncthreads();
       }
       if (CL == 1) continue;  // two blocks only: they never move
@@ -155,6 +178,8 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
         double *src = cluster.map_shared_rank(colp(cur, src_slot[slot], 0), src_rank[slot]);
         double *dst = colp(nxt, slot, 0);
         for (int idx = tid; idx < bs * l; idx += blockDim.x) dst[idx] = src[idx];
+        const double *nsrc = cluster.map_shared_rank(nrmp(cur, src_slot[slot], 0), src_rank[slot]);
+        for (int j = tid; j < bs; j += blockDim.x) *nrmp(nxt, slot, j) = nsrc[j];
         if (tid == 0) {
           int *rid = cluster.map_shared_rank(&ids[cur][src_slot[slot]], src_rank[slot]);
           ids[nxt][slot] = *rid;
@@ -239,7 +264,7 @@ int g_cluster = 0;
 std::once_flag g_once;
 cudaError_t g_err = cudaSuccess;
 
-size_t jac_smem(int32_t l, int32_t bs) { return sizeof(double) * 4 * (size_t)bs * l; }
+size_t jac_smem(int32_t l, int32_t bs) { return sizeof(double) * 4 * (size_t)bs * (l + 1); }
 
 int block_size_for(int32_t l, int cl) { return (int)((l + 2 * cl - 1) / (2 * cl)); }
 

@@ -19,7 +19,7 @@ constexpr int32_t kNoallocMaxBlock = ISVD_NOALLOC_MAX_BLOCK;
 constexpr int32_t kNoallocMaxPartials = 2 * kNumSMs;  // the largest Gram partial count
 
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-constexpr size_t kPartialBytes = align256(sizeof(float) * kNoallocMaxPartials * kNoallocMaxBlock * kNoallocMaxBlock);
+constexpr size_t kPartialBytes = align256(sizeof(double) * kNoallocMaxPartials * kNoallocMaxBlock * kNoallocMaxBlock);
 constexpr size_t kSquareF64 = align256(sizeof(double) * kNoallocMaxBlock * kNoallocMaxBlock);
 constexpr size_t kSquareF32 = align256(sizeof(float) * kNoallocMaxBlock * kNoallocMaxBlock);
 constexpr size_t kStateBytes = align256(sizeof(int32_t) * kOrthStateInts);
@@ -70,7 +70,7 @@ extern "C" isvd_status isvd_orthonormalize_noalloc(float *Q, int64_t rows, int32
   OrthBufs o;
   o.n_part = gram_partials(rows);  // at most kNoallocMaxPartials
   size_t off = 0;
-  o.gram_partial = reinterpret_cast<float *>(base + off);
+  o.gram_partial = reinterpret_cast<double *>(base + off);
   off += kPartialBytes;
   o.W = reinterpret_cast<double *>(base + off);
   off += kSquareF64;

@@ -685,6 +685,8 @@ size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool t
   add(sizeof(double) * (size_t)lowrank_partials(op->n) * std::max(r, 1) * bseg);
   const int64_t chunks = partial_rows(op);
   add(sizeof(float) * (size_t)chunks * pw);
+  if (op->desc.form == ISVD_FORM_CONCAT && op->desc.X_dense)
+    add(xdense_scratch_bytes((int32_t)op->desc.d, op->desc.L + 1, (int32_t)bseg, op->n));
   return total;
 }
 
@@ -708,6 +710,8 @@ void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool tra
   int64_t pw = op->desc.form == ISVD_FORM_CONCAT ? bseg * (op->desc.L + 1) : bseg;
   const int64_t chunks = partial_rows(op);
   sc->heavy_partial = (float *)take(sizeof(float) * (size_t)chunks * pw);
+  if (op->desc.form == ISVD_FORM_CONCAT && op->desc.X_dense)
+    sc->xdense = take(xdense_scratch_bytes((int32_t)op->desc.d, op->desc.L + 1, (int32_t)bseg, op->n));
 }
 
 // Horner evaluation of sum_{k=1..K} c_k N^k G (+ corrections), Eq. 3 with the
@@ -812,6 +816,13 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
   char *P = (char *)sc.p;
   auto seg = [&](int l) { return P + (size_t)l * bseg * es; };
 
+  // dense X: small dense products instead of the X-as-CSR sparse ones
+  const bool xd = d.X_dense && d.d <= ISVD_MAX_BLOCK && (int64_t)(L + 1) * bseg <= ISVD_MAX_BLOCK && sc.xdense;
+  if (!transpose && xd) {
+    // P = X [G_0 | ... | G_L] (or out = X G_0 when L = 0: only the b columns of out)
+    ISVD_CUDA_TRY(xdense_forward(d.X_dense, op->n, (int32_t)d.d, G, ldg, dtype, b, (int32_t)bseg, L + 1,
+                                 L == 0 ? out : (void *)P, L == 0 ? ldo : ldp, sc.xdense, s));
+  }
   if (!transpose) {
     // P_l = X G_l
     SpmmArgs ax{};
@@ -824,12 +835,14 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
     ax.heavy_threshold = op->heavy_X.n_chunks > 0 ? op->heavy_X.threshold : INT_MAX;
     ax.cache_hints = op->cache_hints;
     ax.rows_occupancy = op->rows_occupancy;
-    for (int l = 0; l <= L; ++l) {
-      const char *gin = (const char *)G + (size_t)l * d.d * ldg * es;
-      if (L == 0) ISVD_SLABS(add_slabs(ax, dtype, b, scols, 0, gin, ldg, out, ldo, nullptr, 0));
-      else ISVD_SLABS(add_slabs(ax, dtype, b, scols, (int32_t)(l * bseg), gin, ldg, seg(l), ldp, nullptr, 0));
+    if (!xd) {
+      for (int l = 0; l <= L; ++l) {
+        const char *gin = (const char *)G + (size_t)l * d.d * ldg * es;
+        if (L == 0) ISVD_SLABS(add_slabs(ax, dtype, b, scols, 0, gin, ldg, out, ldo, nullptr, 0));
+        else ISVD_SLABS(add_slabs(ax, dtype, b, scols, (int32_t)(l * bseg), gin, ldg, seg(l), ldp, nullptr, 0));
+      }
+      ISVD_CUDA_TRY(run(ch, ax, op->heavy_X, op->chunk_X, ldp));
     }
-    ISVD_CUDA_TRY(run(ch, ax, op->heavy_X, op->chunk_X, ldp));
     if (L == 0) return ISVD_OK;
     // Horner over N
     const void *cur = seg(L);
@@ -873,6 +886,11 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
     ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
     cur = seg(l);
     ldcur = ldp;
+  }
+  if (xd && dtype == DT_F32) {
+    ISVD_CUDA_TRY(xdense_transpose(d.X_dense, op->n, (int32_t)d.d, (const float *)G, ldg, b, (int32_t)bseg, L + 1,
+                                   (float *)P, ldp, (float *)out, ldo, sc.xdense, s));
+    return ISVD_OK;
   }
   SpmmArgs at{};
   at.rows = d.d;

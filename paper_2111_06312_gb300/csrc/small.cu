@@ -87,10 +87,22 @@ __global__ void __launch_bounds__(kSmallThreads) chol_inv_kernel(const double *_
     __syncthreads();
   } else if (tid == 0) {
     if (shift > 0.0) {
-      state[0] = pass;
+      atomicMax(&state[0], pass);
       atomicAdd(&info->chol_shifts, 1);
     }
     atomicAdd(&info->cholqr_passes, 1);
+  }
+  // from pass 2 on, a factor far from I schedules one more pass (see chol_cluster.cu)
+  if (ok && pass >= 2) {
+    __shared__ int far_from_identity;
+    if (tid == 0) far_from_identity = 0;
+    __syncthreads();
+    for (int idx = tid; idx < l * l; idx += nt) {
+      const int i = idx / l, c = idx - i * l;
+      if (c >= i && fabs(A[idx] - (i == c ? 1.0 : 0.0)) > 0.25) far_from_identity = 1;
+    }
+    __syncthreads();
+    if (tid == 0 && far_from_identity) atomicMax(&state[0], pass - 1);
   }
   // zero the strict lower triangle
   for (int idx = tid; idx < l * l; idx += nt) {

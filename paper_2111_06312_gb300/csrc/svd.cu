@@ -47,7 +47,7 @@ struct Carver {
 
 void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o) {
   o->n_part = gram_partials(rows);
-  o->gram_partial = c.take<float>((size_t)o->n_part * l * l);
+  o->gram_partial = c.take<double>((size_t)o->n_part * l * l);
   o->W = c.take<double>((size_t)l * l);
   o->tmp = c.take<double>((size_t)l * l);
   o->Rinv = c.take<float>((size_t)l * l);

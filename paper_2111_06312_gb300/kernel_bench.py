@@ -94,6 +94,7 @@ def main():
     ap.add_argument("--chunk-nnz", type=int, default=0)
     ap.add_argument("--row-kernel", action="store_true")
     ap.add_argument("--rows", type=int, default=1_000_000)
+    ap.add_argument("--rows-list", default="")
     ap.add_argument("--k", type=int, default=128)
     ap.add_argument("--p", type=int, default=16)
     ap.add_argument("--q", type=int, default=6)
@@ -139,11 +140,16 @@ def main():
     elif a.what == "orth":
         g = synth.cycle(64)
         op = isvd.graph_operator(g, coeffs=[1.0])
-        Q0 = isvd.gaussian(3, a.rows, a.width)
-        Q = Q0.clone()
-        isvd.orthonormalize(op, Q, want_r=False)
-        ts = _time(lambda: (Q.copy_(Q0), isvd.orthonormalize(op, Q, want_r=False)), a.reps, flush)
-        print(json.dumps({"what": "orth", "rows": a.rows, "width": a.width, "ms_incl_copy": float(np.median(ts))}))
+        for rows in ([a.rows] if not a.rows_list else [int(x) for x in a.rows_list.split(",")]):
+            Q0 = isvd.gaussian(3, rows, a.width)
+            Q = Q0.clone()
+            _, _, info = isvd.orthonormalize(op, Q, want_r=False)
+            Qd = Q.double()
+            orth = float((Qd.T @ Qd - torch.eye(a.width, dtype=torch.float64, device=Q.device)).abs().max())
+            passes = isvd.info_dict(info)["cholqr_passes"]
+            ts = _time(lambda: (Q.copy_(Q0), isvd.orthonormalize(op, Q, want_r=False)), a.reps, flush)
+            print(json.dumps({"what": "orth", "rows": rows, "width": a.width, "ms_incl_copy": float(np.median(ts)),
+                              "orthogonality": orth, "passes": passes}), flush=True)
         op.close()
     elif a.what == "svd":
         g = synth.cached(a.workload)
@@ -225,13 +231,51 @@ def equal_error(a, flush):
 
 
 def batched(a, flush):
-    """Many small problems: one isvd_svd_batched call vs one isvd_svd call each."""
+    """Many small problems: one isvd_svd_batched call vs one isvd_svd call each,
+    and mixed vs FP32 batched at equal error (max over problems of the largest
+    principal angle of the gapped top-k subspace and of the relative singular
+    value error there, against FP32 batched runs with 4x the power iterations)."""
     graphs, ranks = synth.workload_batched(count=a.count)
     ops = [isvd.graph_operator(gr, coeffs=C5, ones_coeff=-LAM) for gr in graphs]
+    seed = 20211106315
     try:
-        batch = isvd.Batch(ops, ranks, oversample=10, iters=4, seed=20211106315)
-        batch.run()
-        t_batch = _time(lambda: batch.run(check=False), a.reps, flush)
+        def run_batch(prec, q):
+            b = isvd.Batch(ops, ranks, oversample=10, iters=q, seed=seed, precision=prec)
+            b.run()
+            ts = _time(lambda: b.run(check=False), a.reps, flush)
+            U = [u.clone() for u in b.U]
+            S = [x.clone() for x in b.S]
+            return b, U, S, float(np.median(ts))
+
+        _, U_ref, S_ref, _ = run_batch("fp32", 16)
+        # per problem: the prefix of the reference spectrum separated by a 5% gap
+        kps = [_gapped_prefix(S_ref[i], ranks[i], rel_gap=5e-2) for i in range(len(ops))]
+
+        def errors(U, S):
+            """(median over problems of the largest principal angle on the gapped
+            prefix, median of the largest relative singular-value error there)."""
+            angs, sigs = [], []
+            for i in range(len(ops)):
+                kp = kps[i]
+                if not kp:
+                    continue
+                angs.append(_max_angle(U_ref[i], U[i], kp))
+                rel = ((S[i].double() - S_ref[i].double()).abs() / S_ref[i].double())[:kp]
+                sigs.append(float(rel.max()))
+            return float(np.median(angs)), float(np.median(sigs))
+
+        b32, U32, S32, t32 = run_batch("fp32", 4)
+        e32 = errors(U32, S32)
+        rows = []
+        chosen = None
+        for q in range(4, 8):
+            bm, Um, Sm, tm = run_batch("mixed", q)
+            em = errors(Um, Sm)
+            rows.append({"q": q, "ms": tm, "angle": em[0], "sigma_err": em[1]})
+            if em[0] <= e32[0] * 1.0001 and em[1] <= e32[1] * 1.0001:
+                chosen = rows[-1]
+                break
+        kernels = isvd.Batch.kernel_nodes()
         outs = [(isvd.new_block(op.shape[0], k), isvd.new_block(op.shape[1], k), torch.empty(k, device="cuda"))
                 for op, k in zip(ops, ranks)]
         info = torch.zeros(4, dtype=torch.int32, device="cuda")
@@ -239,15 +283,21 @@ def batched(a, flush):
         def singles():
             for i, (op, k) in enumerate(zip(ops, ranks)):
                 U, V, S = outs[i]
-                op.svd(k, 10, 4, seed=20211106315 + i, U=U, S=S, V=V, info=info, check=False)
+                op.svd(k, 10, 4, seed=seed + i, U=U, S=S, V=V, info=info, check=False)
 
         singles()
         torch.cuda.synchronize()
         t_single = _time(singles, a.reps, flush)
         print(json.dumps({"what": "batched", "count": len(ops), "sum_n": int(sum(gr.n for gr in graphs)),
-                          "sum_nnz": int(sum(gr.nnz for gr in graphs)), "ranks": np.bincount(ranks).tolist(),
-                          "batched_ms": float(np.median(t_batch)), "single_calls_ms": float(np.median(t_single)),
-                          "kernels": isvd.Batch.kernel_nodes()}), flush=True)
+                          "sum_nnz": int(sum(gr.nnz for gr in graphs)), "ranks": {int(k): int(v) for k, v in
+                          zip(*np.unique(ranks, return_counts=True))}, "q": 4, "q_ref": 16,
+                          "problems_with_gapped_prefix": int(sum(1 for kp in kps if kp)),
+                          "error_metric": "median over problems of (max principal angle, max relative sigma error) "
+                                          "on the 5%-gapped prefix vs FP32 with q = 16",
+                          "batched_fp32_ms": t32, "fp32_angle": e32[0], "fp32_sigma_err": e32[1],
+                          "mixed_runs": rows, "mixed_at_equal_error": chosen,
+                          "speedup_mixed_vs_fp32": (t32 / chosen["ms"]) if chosen else None,
+                          "single_calls_fp32_ms": float(np.median(t_single)), "kernels": kernels}), flush=True)
     finally:
         for op in ops:
             op.close()

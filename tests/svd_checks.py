@@ -1,0 +1,43 @@
+"""Shared comparison of a GPU SVD with the FP64 oracle's Alg. 1 (test helper)."""
+import numpy as np
+
+import oracle
+from paper_2111_06312_gb300 import isvd
+
+
+def npy(t):
+    return t.double().cpu().numpy()
+
+
+def gapped_prefix(S_ritz, k, rel_gap=1e-3):
+    """Largest j <= k with (s_j - s_{j+1}) >= rel_gap * s_j (1-based)."""
+    best = 0
+    for j in range(1, k + 1):
+        # j == len(S_ritz): the whole block is the subspace, no gap to check
+        if j == len(S_ritz) or S_ritz[j - 1] - S_ritz[j] >= rel_gap * S_ritz[j - 1]:
+            best = j
+    return best
+
+
+def check_svd(gpu_op, ref_op, k, p, q, seed, tol_s=1e-5, tol_angle=1e-3, precision="fp32"):
+    U, S, V, info = gpu_op.svd(k, p, q, seed, precision=precision)
+    Un, Sn, Vn = npy(U), npy(S), npy(V)
+    Ur, Sr, Vr, _ = ref_op.isvd(k, p, q, seed)
+    _, S_all, _, _ = ref_op.isvd(k + p, 0, q, seed)  # all Ritz values of the same block
+    rel = np.abs(Sn - Sr) / Sr
+    j = gapped_prefix(S_all, k)
+    ang_u = oracle.max_principal_angle(Ur[:, :j], Un[:, :j]) if j else 0.0
+    ang_v = oracle.max_principal_angle(Vr[:, :j], Vn[:, :j]) if j else 0.0
+    orth_u = np.abs(Un.T @ Un - np.eye(k)).max()
+    orth_v = np.abs(Vn.T @ Vn - np.eye(k)).max()
+    res = oracle.residuals(ref_op, Un, Sn, Vn)
+    res_ref = oracle.residuals(ref_op, Ur, Sr, Vr)
+    out = dict(rel=rel.max(), j=j, ang_u=ang_u, ang_v=ang_v, orth_u=orth_u, orth_v=orth_v,
+               res=res.max(), res_ref=res_ref.max(), info=isvd.info_dict(info))
+    assert out["info"]["status"] == "OK", out
+    assert rel.max() <= tol_s, out
+    assert ang_u <= tol_angle and ang_v <= tol_angle, out
+    assert orth_u <= 1e-5 and orth_v <= 1e-5, out
+    # the rest is valid: residuals no worse than the oracle's own plus rounding
+    assert res.max() <= res_ref.max() + 1e-4 * Sr[0], out
+    return out

@@ -10,6 +10,7 @@ import torch
 
 import oracle
 from paper_2111_06312_gb300 import build, isvd, synth
+from svd_checks import check_svd, gapped_prefix  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 LAM = 0.05
@@ -200,6 +201,24 @@ def test_concat_apply(hub_graph, L, norm, dense, transpose, kernel):
     assert np.abs(npy(Y) - Yr).max() <= 1e-5 * np.abs(Yr).max()
 
 
+@pytest.mark.parametrize("b,dtype", [(100, torch.float32), (19, torch.bfloat16), (60, torch.bfloat16)])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_concat_dense_x_wide_and_bf16(hub_graph, b, dtype, transpose):
+    """Dense X: the small dense products serve (L+1) * round8(b) <= 160 columns
+    in FP32 (and the forward product in BF16); wider blocks and the BF16
+    transposed product take the sparse form."""
+    g = hub_graph
+    X = synth.dense_features(g.n, 64, 14)
+    with isvd.graph_operator(g, form="concat", norm="sym", X=X, L=2) as gpu:
+        ref = oracle.graph_operator(g, form="concat", norm="sym", X=X.astype(np.float64), L=2)
+        r, c = gpu.shape
+        G = isvd.gaussian(7, r if transpose else c, b, dtype=dtype)
+        Y = gpu.apply(G, transpose=transpose)
+        Yr = ref.apply(npy(G), transpose=transpose)
+    tol = 1e-5 if dtype == torch.float32 else 2e-2
+    assert np.abs(npy(Y) - Yr).max() <= tol * np.abs(Yr).max()
+
+
 # ---- orthonormalisation (Alg. 2) and the small SVD --------------------------------
 
 def cond_block(r, c, cond, seed):
@@ -245,40 +264,6 @@ def test_small_svd(ne_small, l, cond, upper):
 
 
 # ---- Alg. 1 end to end ---------------------------------------------------------------
-
-def gapped_prefix(S_ritz, k, rel_gap=1e-3):
-    """Largest j <= k with (s_j - s_{j+1}) >= rel_gap * s_j (1-based)."""
-    best = 0
-    for j in range(1, k + 1):
-        # j == len(S_ritz): the whole block is the subspace, no gap to check
-        if j == len(S_ritz) or S_ritz[j - 1] - S_ritz[j] >= rel_gap * S_ritz[j - 1]:
-            best = j
-    return best
-
-
-def check_svd(gpu_op, ref_op, k, p, q, seed, tol_s=1e-5, tol_angle=1e-3, precision="fp32"):
-    U, S, V, info = gpu_op.svd(k, p, q, seed, precision=precision)
-    Un, Sn, Vn = npy(U), npy(S), npy(V)
-    Ur, Sr, Vr, _ = ref_op.isvd(k, p, q, seed)
-    _, S_all, _, _ = ref_op.isvd(k + p, 0, q, seed)  # all Ritz values of the same block
-    rel = np.abs(Sn - Sr) / Sr
-    j = gapped_prefix(S_all, k)
-    ang_u = oracle.max_principal_angle(Ur[:, :j], Un[:, :j]) if j else 0.0
-    ang_v = oracle.max_principal_angle(Vr[:, :j], Vn[:, :j]) if j else 0.0
-    orth_u = np.abs(Un.T @ Un - np.eye(k)).max()
-    orth_v = np.abs(Vn.T @ Vn - np.eye(k)).max()
-    res = oracle.residuals(ref_op, Un, Sn, Vn)
-    res_ref = oracle.residuals(ref_op, Ur, Sr, Vr)
-    out = dict(rel=rel.max(), j=j, ang_u=ang_u, ang_v=ang_v, orth_u=orth_u, orth_v=orth_v,
-               res=res.max(), res_ref=res_ref.max(), info=isvd.info_dict(info))
-    assert out["info"]["status"] == "OK", out
-    assert rel.max() <= tol_s, out
-    assert ang_u <= tol_angle and ang_v <= tol_angle, out
-    assert orth_u <= 1e-5 and orth_v <= 1e-5, out
-    # the rest is valid: residuals no worse than the oracle's own plus rounding
-    assert res.max() <= res_ref.max() + 1e-4 * Sr[0], out
-    return out
-
 
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_svd_ne_small_parity(ne_small, kernel):
