@@ -365,6 +365,8 @@ def run_ours(args):
                      "spmm_per_apply": K, "storage": "f32" if es == 4 else "bf16"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " (copy, burst)",
+                         "traffic_gbs": (traffic / (apply_ms * 1e-3) / 1e9) if traffic else None,
+                         "traffic_frac": (traffic / (apply_ms * 1e-3) / 1e9 / hbm) if traffic else None,
                          "kernel": "SpMM: one M.Q apply = %d Horner SpMMs (%s kernel) + projection, width %d"
                                    % (K, kernel, l)},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

@@ -291,7 +291,8 @@ enum {
   ISVD_TUNE_ROW_KERNEL = 2,
   ISVD_TUNE_RING_KERNEL = 4,
   ISVD_TUNE_HOT_TAGS = 8,    /* with CACHE_HINTS: keep priority only for hub columns (by degree) */
-  ISVD_TUNE_ROWS_OCC3 = 16   /* row kernel compiled for high occupancy (6 CTAs of 256 threads per SM) */
+  ISVD_TUNE_ROWS_OCC3 = 16,  /* row kernel compiled for high occupancy (6 CTAs of 256 threads per SM) */
+  ISVD_TUNE_PREFETCH = 32    /* row kernel: L2 prefetch of the next row's first neighbour rows */
 };
 
 /* Read / replace the operator's launch shapes.  isvd_set_tuning rebuilds the

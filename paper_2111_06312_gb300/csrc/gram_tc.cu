@@ -14,7 +14,7 @@
 // one BF16 MMA (exact products).  The tensor cores' FP32 accumulation loses
 // a little on every addition, and over thousands of rows the loss adds up
 // (CholeskyQR2's orthogonality fell linearly with the rows per CTA, 1.2e-4
-// at 6,600), so each 256-row segment is accumulated in tensor memory (two
+// at 6,600), so each 384-row segment is accumulated in tensor memory (two
 // buffers, alternating) and four epilogue warps add it into the CTA's FP64
 // partial (kept in L2) while the next segment is multiplied.  The partials
 // are combined in FP64 in a fixed order by gram_reduce (deterministic).
@@ -38,7 +38,7 @@ constexpr int kTileStages = 3;
 constexpr int kTmemCols = 512;
 constexpr int kAccCols = 256;  // accumulator buffer b at column b * kAccCols
 constexpr int kTile2Col = 192;
-constexpr int kSegRows = 256;  // rows summed in tensor memory before promotion to FP64
+constexpr int kSegRows = 384;  // rows summed in tensor memory before promotion to FP64
 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");

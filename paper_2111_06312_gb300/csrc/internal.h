@@ -82,6 +82,7 @@ struct SpmmArgs {
   int32_t cache_hints;      // L2 eviction-priority hints on gathers and streams
   const int32_t *tagged;    // nullable: colidx with degree buckets (RingTags), for the hints
   int32_t rows_occupancy;   // row kernel: 3 = compiled for 6 resident CTAs per SM (40 registers), else default
+  int32_t prefetch;         // row kernel: L2 prefetch of the next row's first neighbour rows
   int32_t nslabs;
   SpmmSlab slab[kMaxSlabs];
 };
@@ -266,6 +267,7 @@ struct isvd_operator {
   int32_t cache_hints = 1;
   int32_t hot_tags = 1;     // row kernel: L2 priority only for gathers of hub columns
   int32_t rows_occupancy = 3;
+  int32_t prefetch = 0;
   struct GraphEntry {
     uint64_t key[16];
     cudaGraphExec_t exec;

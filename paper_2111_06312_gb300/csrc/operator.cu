@@ -578,6 +578,7 @@ SpmmArgs base_args_A(const isvd_operator *op) {
   a.heavy_threshold = op->heavy_A.n_chunks > 0 ? op->heavy_A.threshold : INT_MAX;
   a.cache_hints = op->cache_hints;
   a.rows_occupancy = op->rows_occupancy;
+  a.prefetch = op->prefetch;
   return a;
 }
 
@@ -835,6 +836,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
     ax.heavy_threshold = op->heavy_X.n_chunks > 0 ? op->heavy_X.threshold : INT_MAX;
     ax.cache_hints = op->cache_hints;
     ax.rows_occupancy = op->rows_occupancy;
+    ax.prefetch = op->prefetch;
     if (!xd) {
       for (int l = 0; l <= L; ++l) {
         const char *gin = (const char *)G + (size_t)l * d.d * ldg * es;
@@ -902,6 +904,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
   at.heavy_threshold = op->heavy_XT.n_chunks > 0 ? op->heavy_XT.threshold : INT_MAX;
   at.cache_hints = op->cache_hints;
   at.rows_occupancy = op->rows_occupancy;
+  at.prefetch = op->prefetch;
   for (int l = 0; l <= L; ++l) {
     const void *in = l == 0 ? G : (const void *)seg(l);
     const int64_t ldi = l == 0 ? ldg : ldp;
@@ -1034,7 +1037,7 @@ isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
   out->heavy_chunk = op->heavy_A.chunk;
   out->flags = (op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0) | (op->spmm_algo == 0 ? ISVD_TUNE_ROW_KERNEL : 0) |
                (op->spmm_algo == 2 ? ISVD_TUNE_RING_KERNEL : 0) | (op->hot_tags ? ISVD_TUNE_HOT_TAGS : 0) |
-               (op->rows_occupancy >= 3 ? ISVD_TUNE_ROWS_OCC3 : 0);
+               (op->rows_occupancy >= 3 ? ISVD_TUNE_ROWS_OCC3 : 0) | (op->prefetch ? ISVD_TUNE_PREFETCH : 0);
   out->chunk_nnz = op->chunk_nnz;
   out->l2_budget_mb = (int32_t)(op->tags_A.l2_budget >> 20);
   return ISVD_OK;
@@ -1055,6 +1058,7 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
   op->spmm_algo = (t->flags & ISVD_TUNE_RING_KERNEL) ? 2 : (t->flags & ISVD_TUNE_ROW_KERNEL) ? 0 : 1;
   op->hot_tags = (t->flags & ISVD_TUNE_HOT_TAGS) ? 1 : 0;
   op->rows_occupancy = (t->flags & ISVD_TUNE_ROWS_OCC3) ? 3 : 2;
+  op->prefetch = (t->flags & ISVD_TUNE_PREFETCH) ? 1 : 0;
   op->chunk_nnz = t->chunk_nnz;
   op->tags_A.l2_budget = (int64_t)t->l2_budget_mb << 20;
   HeavyPlan *plans[3] = {&op->heavy_A, &op->heavy_X, &op->heavy_XT};

@@ -116,6 +116,8 @@ struct Vec<DT_BF16> {
   }
 };
 
+constexpr int kPrefetchNonzeros = 8;  // neighbour rows of the next row prefetched to L2
+
 struct Policies {
   uint64_t keep, stream;
 };
@@ -279,6 +281,22 @@ __device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, 
   }
 }
 
+// L2 prefetch of the first neighbour rows of the group's next row: more
+// requests in flight without holding registers.  Lane gl of the group takes
+// nonzero gl / lines and 128-byte line gl % lines of its gathered row.
+template <int DT>
+__device__ __forceinline__ void prefetch_next_row(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int64_t rn) {
+  if (rn >= a.rows) return;
+  const int e0 = __ldg(a.rowptr + rn), e1 = __ldg(a.rowptr + rn + 1);
+  const int row_bytes = sl.width * Vec<DT>::BYTES;
+  const int lines = (row_bytes + 127) / 128;
+  const int t = L.gl / lines, line = L.gl - t * lines;
+  if (e1 - e0 > a.heavy_threshold || t >= kPrefetchNonzeros || e0 + t >= e1 || line >= lines) return;
+  const int32_t c = a.tagged ? (__ldg(a.tagged + e0 + t) & ((1 << 26) - 1)) : __ldg(a.colidx + e0 + t);
+  const char *p = reinterpret_cast<const char *>(sl.in) + ((size_t)c * sl.ldi) * Vec<DT>::BYTES + line * 128;
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int DT, bool HINT, int MINB, int CPL>
 __global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_constant__ SpmmArgs a) {
   constexpr int VN = Vec<DT>::N;
@@ -292,6 +310,7 @@ __global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_const
     const int64_t r = base + L.sub;
     if (r >= a.rows) continue;  // uniform within the group
     const int e0 = ld_idx<HINT>(a.rowptr + r, pol.stream), e1 = ld_idx<HINT>(a.rowptr + r + 1, pol.stream);
+    if (a.prefetch) prefetch_next_row<DT>(a, sl, L, r + nwarp * rpw);
     if (e1 - e0 > a.heavy_threshold) continue;
     float acc[CPL * VN];
 #pragma unroll

@@ -289,10 +289,12 @@ class Operator:
         d["cache_hints"] = bool(d["flags"] & 1)
         d["hot_tags"] = bool(d["flags"] & 8)
         d["rows_occupancy"] = 3 if d["flags"] & 16 else 2
+        d["prefetch"] = bool(d["flags"] & 32)
         d["kernel"] = "ring" if d["flags"] & 4 else "rows" if d["flags"] & 2 else "chunks"
         return d
 
-    def set_tuning(self, kernel=None, cache_hints=None, hot_tags=None, rows_occupancy=None, **fields):
+    def set_tuning(self, kernel=None, cache_hints=None, hot_tags=None, rows_occupancy=None, prefetch=None,
+                   **fields):
         """kernel: 'ring' (nonzero chunks, full-width gathers through shared
         memory), 'rows' (row groups with hub splitting) or 'chunks' (nonzero
         chunks over narrow column slabs); other keys as in isvd_tuning."""
@@ -304,6 +306,8 @@ class Operator:
             vals[4] = (vals[4] & ~8) | (8 if hot_tags else 0)
         if rows_occupancy is not None:
             vals[4] = (vals[4] & ~16) | (16 if rows_occupancy >= 3 else 0)
+        if prefetch is not None:
+            vals[4] = (vals[4] & ~32) | (32 if prefetch else 0)
         if kernel is not None:
             if kernel not in ("ring", "rows", "chunks"):
                 raise ValueError(f"unknown kernel {kernel!r}")
