@@ -98,63 +98,95 @@ __global__ void philox_words_kernel(uint32_t k0, uint32_t k1, int64_t rows, uint
 // columns each), then the 8 row lanes are combined in FP64.  Phase 2 adds the
 // n_part partials in block order in FP64.
 template <typename T>
+__device__ __forceinline__ void load4(const T *p, float *v);
+template <>
+__device__ __forceinline__ void load4<float>(const float *p, float *v) {
+  const float4 x = *reinterpret_cast<const float4 *>(p);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = x.z;
+  v[3] = x.w;
+}
+template <>
+__device__ __forceinline__ void load4<__nv_bfloat16>(const __nv_bfloat16 *p, float *v) {
+  const uint2 x = *reinterpret_cast<const uint2 *>(p);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&x.y));
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+// Lane x of a warp owns columns [4x, 4x + 4) and [128 + 4x, 132 + 4x) of each
+// 256-column pass (one vector load each; columns past b are loaded from the
+// row's padding, which ld % 8 == 0 keeps inside the row, and not summed).
+template <typename T, int RMAX>
 __global__ void __launch_bounds__(256) project_partial_kernel(const T *G, int64_t ldg, int64_t rows, int32_t b,
                                                               const float *V, int64_t ldv, int32_t r,
                                                               int32_t ones_first, double *partial, int64_t pb) {
-  __shared__ double red[8][ISVD_MAX_LOWRANK][33];
+  __shared__ double red[8][33];
   const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
   const int64_t p = blockIdx.x;
   const int64_t stride = (int64_t)gridDim.x * 8;
-  for (int c0 = 0; c0 < b; c0 += 128) {
-    const int col = c0 + 4 * x;
-    float acc[ISVD_MAX_LOWRANK][4];
+  for (int c0 = 0; c0 < b; c0 += 256) {
+    const int colA = c0 + 4 * x, colB = c0 + 128 + 4 * x;
+    const bool inA = colA < b, inB = colB < b;
+    float acc[RMAX][8];
 #pragma unroll
-    for (int t = 0; t < ISVD_MAX_LOWRANK; ++t)
+    for (int t = 0; t < RMAX; ++t)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[t][k] = 0.f;
-    if (col < b) {
+      for (int k = 0; k < 8; ++k) acc[t][k] = 0.f;
+    if (inA) {
       for (int64_t i = p * 8 + y; i < rows; i += stride) {
-        float v[4];
+        float v[8];
+        load4<T>(G + i * ldg + colA, v);
+        if (inB) load4<T>(G + i * ldg + colB, v + 4);
+        else v[4] = v[5] = v[6] = v[7] = 0.f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = (col + k < b) ? to_float(G[i * ldg + col + k]) : 0.f;
-#pragma unroll
-        for (int t = 0; t < ISVD_MAX_LOWRANK; ++t) {
+        for (int t = 0; t < RMAX; ++t) {
           if (t < r) {
             const int tv = t - ones_first;
             const float u = (tv < 0 || !V) ? 1.f : V[i * ldv + tv];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[t][k] = fmaf(u, v[k], acc[t][k]);
+            for (int k = 0; k < 8; ++k) acc[t][k] = fmaf(u, v[k], acc[t][k]);
           }
         }
       }
     }
-    // reduce the 8 row lanes for each of the 4 columns in turn
+    // sum the 8 row warps, one column at a time, in FP64
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int t = 0; t < RMAX; ++t) {
+      if (t >= r) break;
 #pragma unroll
-      for (int t = 0; t < ISVD_MAX_LOWRANK; ++t)
-        if (t < r) red[y][t][x] = (double)acc[t][k];
-      __syncthreads();
-      if (y == 0) {
-        for (int t = 0; t < r; ++t) {
+      for (int k = 0; k < 8; ++k) {
+        red[y][x] = (double)acc[t][k];
+        __syncthreads();
+        if (y == 0) {
           double sacc = 0.0;
-          for (int yy = 0; yy < 8; ++yy) sacc += red[yy][t][x];
-          if (col + k < b) partial[(p * r + t) * pb + col + k] = sacc;
+          for (int yy = 0; yy < 8; ++yy) sacc += red[yy][x];
+          const int col = (k < 4 ? colA : colB) + (k & 3);
+          if (col < b && (k < 4 ? inA : inB)) partial[(p * r + t) * pb + col] = sacc;
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
 }
 
+// one warp per output: lane j sums partials j, j + 32, ... in order, then a
+// fixed shuffle tree (the same order on every run)
 __global__ void project_final_kernel(const double *partial, int32_t n_part, int32_t r, int32_t b, int64_t pb,
                                      float *c, int64_t ldc) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)r * b) return;
+  const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (idx >= (int64_t)r * b) return;  // uniform within the warp
   const int t = (int)(idx / b), col = (int)(idx % b);
   double s = 0.0;
-  for (int p = 0; p < n_part; ++p) s += partial[((int64_t)p * r + t) * pb + col];
-  c[(int64_t)t * ldc + col] = (float)s;
+  for (int p = lane; p < n_part; p += 32) s += partial[((int64_t)p * r + t) * pb + col];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) c[(int64_t)t * ldc + col] = (float)s;
 }
 
 // ---- conditional CholeskyQR passes ------------------------------------------------
@@ -290,14 +322,24 @@ cudaError_t lowrank_project_launch(const void *G, int64_t ldg, int dtype, int64_
                                    int64_t ldv, int32_t r, int32_t ones_first, double *partial, int32_t n_part,
                                    float *c, int64_t ldc, cudaStream_t s) {
   const int64_t pb = round_up(b, 8);
-  if (dtype == DT_F32)
-    project_partial_kernel<float><<<n_part, 256, 0, s>>>((const float *)G, ldg, rows, b, V, ldv, r, ones_first,
-                                                          partial, pb);
-  else
-    project_partial_kernel<__nv_bfloat16><<<n_part, 256, 0, s>>>((const __nv_bfloat16 *)G, ldg, rows, b, V, ldv,
-                                                                  r, ones_first, partial, pb);
+  // the all-ones projection alone (r = 1) keeps one accumulator row: more resident warps
+  if (dtype == DT_F32) {
+    if (r == 1)
+      project_partial_kernel<float, 1><<<n_part, 256, 0, s>>>((const float *)G, ldg, rows, b, V, ldv, r, ones_first,
+                                                               partial, pb);
+    else
+      project_partial_kernel<float, ISVD_MAX_LOWRANK><<<n_part, 256, 0, s>>>((const float *)G, ldg, rows, b, V, ldv, r,
+                                                                              ones_first, partial, pb);
+  } else {
+    if (r == 1)
+      project_partial_kernel<__nv_bfloat16, 1><<<n_part, 256, 0, s>>>((const __nv_bfloat16 *)G, ldg, rows, b, V, ldv,
+                                                                       r, ones_first, partial, pb);
+    else
+      project_partial_kernel<__nv_bfloat16, ISVD_MAX_LOWRANK><<<n_part, 256, 0, s>>>(
+          (const __nv_bfloat16 *)G, ldg, rows, b, V, ldv, r, ones_first, partial, pb);
+  }
   const int64_t tot = (int64_t)r * b;
-  project_final_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, s>>>(partial, n_part, r, b, pb, c, ldc);
+  project_final_kernel<<<(unsigned)ceil_div(tot * 32, 256), 256, 0, s>>>(partial, n_part, r, b, pb, c, ldc);
   return cudaGetLastError();
 }
 

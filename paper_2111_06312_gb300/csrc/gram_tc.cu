@@ -290,9 +290,14 @@ __global__ void gram_reduce_tc_kernel(const double *partial, int32_t n_part, int
   if (idx >= (int64_t)l * l) return;
   const int r = (int)(idx / l), c = (int)(idx - (int64_t)r * l);
   const int64_t src = (r < 128 && c >= 128) ? (int64_t)c * l + r : idx;
-  double s = 0.0;
-  for (int p = 0; p < n_part; ++p) s += partial[(int64_t)p * l * l + src];
-  W[idx] = s;
+  // eight interleaved sums (fixed order), so the loads of different partials overlap
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int p = 0;
+  for (; p + 8 <= n_part; p += 8)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += partial[(int64_t)(p + u) * l * l + src];
+  for (; p < n_part; ++p) acc[p & 7] += partial[(int64_t)p * l * l + src];
+  W[idx] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 template <int DT>
