@@ -101,8 +101,14 @@ struct HeavyPlan {
 
 // Launch the SpMM described by `a` (dtype of in/axpy/out), splitting heavy
 // rows per `hp` using `partial` (hp.n_chunks x pw FP32, pw >= slab columns).
+// A second stream (and a fork / join event pair) on which the split hub rows
+// run beside the row-group kernel; all null: one stream.
+struct SideStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
 cudaError_t spmm_launch(const SpmmArgs &a, int dtype, const HeavyPlan &hp, float *partial,
-                        int64_t pw, cudaStream_t s);
+                        int64_t pw, cudaStream_t s, const SideStream &side);
 
 // Column slabs for a block of width b (row-major, 16-byte aligned).
 int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out);
@@ -263,6 +269,7 @@ struct isvd_operator {
   void *arena = nullptr;
   size_t arena_bytes = 0;
   cudaStream_t capture_stream = nullptr;
+  isvd::SideStream side;        // second stream: split hub rows beside the row-group kernel
   int32_t slab_cols_f32 = 128, slab_cols_bf16 = 256;
   int32_t cache_hints = 1;
   int32_t hot_tags = 1;     // row kernel: L2 priority only for gathers of hub columns

@@ -495,6 +495,9 @@ isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaS
   ISVD_CUDA_TRY(small_kernels_init());
   ISVD_CUDA_TRY(dense_kernels_init());
   ISVD_CUDA_TRY(cudaStreamCreateWithFlags(&op->capture_stream, cudaStreamNonBlocking));
+  ISVD_CUDA_TRY(cudaStreamCreateWithFlags(&op->side.stream, cudaStreamNonBlocking));
+  ISVD_CUDA_TRY(cudaEventCreateWithFlags(&op->side.fork, cudaEventDisableTiming));
+  ISVD_CUDA_TRY(cudaEventCreateWithFlags(&op->side.join, cudaEventDisableTiming));
 
   const int64_t n = op->n;
   float *vecs = (float *)owned_alloc(op, sizeof(float) * 4 * n, s);
@@ -658,7 +661,7 @@ cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, const ChunkPla
       a.slab[i].hot_bucket = hb;
     }
   }
-  return spmm_launch(a, c.dtype, hp, c.sc->heavy_partial, pw, c.s);
+  return spmm_launch(a, c.dtype, hp, c.sc->heavy_partial, pw, c.s, c.op->side);
 }
 
 int64_t partial_rows(const isvd_operator *op) {
@@ -992,6 +995,9 @@ void isvd_destroy_operator(isvd_operator *op) {
   free_chunks(op, &op->chunk_X, s);
   free_chunks(op, &op->chunk_XT, s);
   if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
+  if (op->side.fork) cudaEventDestroy(op->side.fork);
+  if (op->side.join) cudaEventDestroy(op->side.join);
+  if (op->side.stream) cudaStreamDestroy(op->side.stream);
   cudaStreamSynchronize(s);
   delete op;
 }

@@ -371,8 +371,29 @@ __global__ void __launch_bounds__(256) spmm_finish_kernel(const __grid_constant_
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
       if (!(q == 0 ? L.active : L.active2)) break;
-      for (int c = hr.y; c < hr.y + hr.z; ++c) {
-        const float *p = partial + (size_t)c * pw + sl.col0 + (q == 0 ? L.col : L.col2);
+      // chunk partials in order, 8 loads in flight (the largest hubs have hundreds)
+      const float *p0 = partial + (size_t)hr.y * pw + sl.col0 + (q == 0 ? L.col : L.col2);
+      int c = 0;
+      constexpr int NV = VN / 4;  // float4 per lane and chunk
+      for (; c + 8 <= hr.z; c += 8) {
+        float4 v[8][NV];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int h = 0; h < NV; ++h)
+            v[u][h] = __ldcg(reinterpret_cast<const float4 *>(p0 + (size_t)(c + u) * pw) + h);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int h = 0; h < NV; ++h) {
+            acc[q * VN + 4 * h + 0] += v[u][h].x;
+            acc[q * VN + 4 * h + 1] += v[u][h].y;
+            acc[q * VN + 4 * h + 2] += v[u][h].z;
+            acc[q * VN + 4 * h + 3] += v[u][h].w;
+          }
+      }
+      for (; c < hr.z; ++c) {
+        const float *p = p0 + (size_t)c * pw;
 #pragma unroll
         for (int k = 0; k < VN; ++k) acc[q * VN + k] += p[k];
       }
@@ -388,7 +409,8 @@ int pow2_ceil(int x) {
 }
 
 template <int DT, bool HINT, int CPL>
-cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s) {
+cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s,
+                       const SideStream &side) {
   const int threads = 256;
   int gmin = 32;
   for (int i = 0; i < a.nslabs; ++i) gmin = gmin < a.slab[i].group ? gmin : a.slab[i].group;
@@ -398,15 +420,31 @@ cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, i
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
   dim3 grid((unsigned)bx, (unsigned)a.nslabs);
+  // the hub chunks (their own partial buffer, no row in common with the row
+  // kernel) run on the side stream when there is one, filling the row kernel's tail
+  const bool fork = hp.n_chunks > 0 && side.stream && side.fork && side.join;
+  cudaStream_t hs = fork ? side.stream : s;
+  if (fork) {
+    cudaError_t e = cudaEventRecord(side.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
+    if (e != cudaSuccess) return e;
+  }
+  if (hp.n_chunks > 0) {
+    int64_t cx = ceil_div(hp.n_chunks, rows_per_block);
+    if (cx > cap) cx = cap;
+    spmm_chunks_kernel<DT, HINT, CPL><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, hs>>>(
+        a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
+  }
   if (a.rows_occupancy >= 3)
     spmm_rows_kernel<DT, HINT, 6, CPL><<<grid, threads, 0, s>>>(a);
   else
     spmm_rows_kernel<DT, HINT, 1, CPL><<<grid, threads, 0, s>>>(a);
+  if (fork) {
+    cudaError_t e = cudaEventRecord(side.join, side.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side.join, 0);
+    if (e != cudaSuccess) return e;
+  }
   if (hp.n_chunks > 0) {
-    int64_t cx = ceil_div(hp.n_chunks, rows_per_block);
-    if (cx > cap) cx = cap;
-    spmm_chunks_kernel<DT, HINT, CPL><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, s>>>(
-        a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
     int64_t fx = ceil_div(hp.n_rows, rows_per_block);
     if (fx > cap) fx = cap;
     spmm_finish_kernel<DT, HINT, CPL><<<dim3((unsigned)fx, (unsigned)a.nslabs), threads, 0, s>>>(
@@ -417,10 +455,12 @@ cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, i
 
 // Wide slabs (more than 32 chunks of 16 bytes) use two chunks per lane.
 template <int DT, bool HINT>
-cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s) {
+cudaError_t launch_dt(const SpmmArgs &a, const HeavyPlan &hp, float *partial, int64_t pw, cudaStream_t s,
+                      const SideStream &side) {
   bool wide = false;
   for (int i = 0; i < a.nslabs; ++i) wide = wide || a.slab[i].width > a.slab[i].group * Vec<DT>::N;
-  return wide ? launch_cpl<DT, HINT, 2>(a, hp, partial, pw, s) : launch_cpl<DT, HINT, 1>(a, hp, partial, pw, s);
+  return wide ? launch_cpl<DT, HINT, 2>(a, hp, partial, pw, s, side)
+              : launch_cpl<DT, HINT, 1>(a, hp, partial, pw, s, side);
 }
 
 }  // namespace
@@ -450,13 +490,13 @@ int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out) {
 }
 
 cudaError_t spmm_launch(const SpmmArgs &a, int dtype, const HeavyPlan &hp, float *partial, int64_t pw,
-                        cudaStream_t s) {
+                        cudaStream_t s, const SideStream &side) {
   if (a.rows == 0 || a.nslabs == 0) return cudaSuccess;
   if (a.cache_hints)
-    return dtype == DT_F32 ? launch_dt<DT_F32, true>(a, hp, partial, pw, s)
-                           : launch_dt<DT_BF16, true>(a, hp, partial, pw, s);
-  return dtype == DT_F32 ? launch_dt<DT_F32, false>(a, hp, partial, pw, s)
-                         : launch_dt<DT_BF16, false>(a, hp, partial, pw, s);
+    return dtype == DT_F32 ? launch_dt<DT_F32, true>(a, hp, partial, pw, s, side)
+                           : launch_dt<DT_BF16, true>(a, hp, partial, pw, s, side);
+  return dtype == DT_F32 ? launch_dt<DT_F32, false>(a, hp, partial, pw, s, side)
+                         : launch_dt<DT_BF16, false>(a, hp, partial, pw, s, side);
 }
 
 }  // namespace isvd
