@@ -220,7 +220,8 @@ ISVD_API isvd_status isvd_philox_words(uint64_t seed, int64_t rows, uint32_t *ou
  * follow (up to 4 passes).  R_out (DEVICE, l x l FP64, row-major, upper)
  * receives R with Q_in = Q_out R, or NULL.  dev_info as in
  * isvd_svd.  Uses the operator's workspace (any operator; pass the one whose
- * calls this is ordered with).  l <= ISVD_MAX_BLOCK. */
+ * calls this is ordered with).  l <= ISVD_MAX_BLOCK; ldq >= l and a
+ * multiple of 8, Q 16-byte aligned (else ISVD_ERR_INVALID_ARGUMENT). */
 ISVD_API isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t rows, int32_t l, int64_t ldq,
                                 double *R_out, isvd_info *dev_info, void *stream);
 

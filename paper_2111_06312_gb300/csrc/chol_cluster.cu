@@ -27,7 +27,6 @@ namespace {
 
 constexpr int kCholThreads = 512;
 constexpr int kNB = 16;
-constexpr int kCholMaxCluster = 16;
 constexpr double kReorthThreshold = 0.25;
 
 __host__ __device__ inline int cols_per_cta(int l, int cl) { return (l + cl - 1) / cl; }
@@ -45,7 +44,7 @@ __device__ __forceinline__ bool pass_skipped(const int32_t *state, int32_t pass)
   return pass > 2 && state[0] + 2 < pass;
 }
 
-__global__ void __launch_bounds__(kCholThreads) chol_cluster_kernel(const double *__restrict__ W, int32_t l,
+__global__ void __launch_bounds__(kCholThreads, 1) chol_cluster_kernel(const double *__restrict__ W, int32_t l,
                                                                     double unit_roundoff, float *__restrict__ Rinv,
                                                                     int64_t ldr, double *__restrict__ Rout,
                                                                     double *__restrict__ Racc,
@@ -134,20 +133,23 @@ __global__ void __launch_bounds__(kCholThreads) chol_cluster_kernel(const double
         failed = true;
         break;  // every CTA factors the same block, so all leave here together
       }
-      // (c) panel rows k0..k0+nb of the own columns
-      for (int cc = tid; cc < cpc; cc += nt) {
+      // (c) panel rows k0..k0+nb of the own columns, one warp per column
+      for (int cc = warp; cc < cpc; cc += nt / 32) {
         const int c = rank + cc * CL;
         if (c < k0 || c >= l) continue;
         double *a = Acol + (size_t)cc * l + k0;
         if (c < k0 + nb) {
-          for (int r = 0; r <= c - k0; ++r) a[r] = D[r * (kNB + 1) + (c - k0)];
+          if (lane <= c - k0) a[lane] = D[lane * (kNB + 1) + (c - k0)];
         } else {
-          // solve D^T x = a (D upper): x_r = (a_r - sum_{t<r} D_tr x_t) / D_rr
+          // solve D^T x = a (D upper), lane r holding row r: once x_r is
+          // final (x_r = a_r / D_rr), every later row s subtracts D_rs x_r
+          double x = lane < nb ? a[lane] : 0.0;
           for (int r = 0; r < nb; ++r) {
-            double s = a[r];
-            for (int t = 0; t < r; ++t) s -= D[t * (kNB + 1) + r] * a[t];
-            a[r] = s * invD[r];
+            const double xr = __shfl_sync(0xffffffffu, x, r) * invD[r];
+            if (lane == r) x = xr;
+            else if (lane > r && lane < nb) x = fma(-D[r * (kNB + 1) + lane], xr, x);
           }
+          if (lane < nb) a[lane] = x;
         }
       }
       cluster.sync();
@@ -240,20 +242,20 @@ __global__ void __launch_bounds__(kCholThreads) chol_cluster_kernel(const double
     }
   }
 
-  // own columns of S = R^-1: S_cc = 1/R_cc, S_ic = -(sum_{t=i+1}^{c} R_it S_tc) / R_ii
+  // own columns of S = R^-1: S_cc = 1/R_cc, S_ic = -(sum_{t=i+1}^{c} R_it S_tc) / R_ii,
+  // one warp per column, right-looking: once S_tc is final (t descending),
+  // every row i < t adds R_it S_tc to its running sum x[i] (lanes over i)
   double *x = xbuf + (size_t)warp * l;
   for (int cc = warp; cc < cpc; cc += nt / 32) {
     const int c = rank + cc * CL;
     if (c >= l) break;
-    if (lane == 0) x[c] = invd[c];
+    for (int i = lane; i < c; i += 32) x[i] = 0.0;
     __syncwarp();
-    for (int i = c - 1; i >= 0; --i) {
-      const double *Ri = X + packed_off(i, l) - i;  // Ri[t] = R_it for t >= i
-      double s = 0.0;
-      for (int t = i + 1 + lane; t <= c; t += 32) s += Ri[t] * x[t];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = -s * invd[i];
+    for (int t = c; t >= 0; --t) {
+      const double xt = t == c ? invd[c] : -x[t] * invd[t];
+      for (int i = lane; i < t; i += 32) x[i] = fma(X[packed_off(i, l) + (t - i)], xt, x[i]);
+      __syncwarp();
+      if (lane == 0) x[t] = xt;
       __syncwarp();
     }
     for (int i = lane; i < l; i += 32) Rinv[(size_t)i * ldr + c] = (i <= c) ? (float)x[i] : 0.f;

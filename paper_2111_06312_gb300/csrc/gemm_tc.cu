@@ -42,6 +42,20 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 __device__ __forceinline__ void producer_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kProd) : "memory"); }
 
+// 8 words to global memory: one 32-byte store when `aligned32` (the address
+// is then a multiple of 32), else two 16-byte stores (16-byte aligned address)
+__device__ __forceinline__ void st_32(void *p, bool aligned32, uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                      uint32_t e, uint32_t f, uint32_t g, uint32_t h) {
+  if (aligned32) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d),
+                 "r"(e), "r"(f), "r"(g), "r"(h)
+                 : "memory");
+  } else {
+    reinterpret_cast<uint4 *>(p)[0] = make_uint4(a, b, c, d);
+    reinterpret_cast<uint4 *>(p)[1] = make_uint4(e, f, g, h);
+  }
+}
+
 template <int DT>
 struct GemmCfg {
   static constexpr bool F32 = DT == DT_F32;
@@ -253,6 +267,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue: TMEM -> Q rows ----------------
     const int sub = warp & 3;  // TMEM lane quarter of this warp
     const int r = sub * 32 + lane;
+    // every row start is 32-byte aligned (the column offsets below are multiples of 32 bytes)
+    const bool v32 = ((uintptr_t)Q & 31) == 0 && ((ldq * C::ES) & 31) == 0;
     for (int64_t lt = 0; lt < my_tiles; ++lt) {
       const int d = (int)(lt & 1);
       if (!mbar_wait(&dfull[d], (uint32_t)((lt >> 1) & 1))) {
@@ -266,19 +282,41 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (d ? kDBufCol : 0) + cb, v);
         if (row < rows) {
           char *dst = Q + ((size_t)row * ldq + cb) * C::ES;
+          // 32-byte stores (a whole L2 sector each) where every row starts
+          // on a 32-byte boundary, else 16-byte pairs (the row pitch is a
+          // multiple of 8 elements); element stores for a ragged tail
+          const int n = min(32, l - cb);
           if (C::F32) {
-            const int n = min(32, l - cb);
-            if (n == 32) {
 #pragma unroll
-              for (int j = 0; j < 32; j += 4)
-                *reinterpret_cast<uint4 *>(dst + j * 4) = make_uint4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            } else {
-              for (int j = 0; j < n; ++j) reinterpret_cast<float *>(dst)[j] = __uint_as_float(v[j]);
+            for (int j = 0; j < 32; j += 8) {
+              if (j + 8 <= n) {
+                st_32(dst + j * 4, v32, v[j], v[j + 1], v[j + 2], v[j + 3], v[j + 4], v[j + 5], v[j + 6], v[j + 7]);
+              } else {
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                  if (j + t < n) reinterpret_cast<float *>(dst)[j + t] = __uint_as_float(v[j + t]);
+              }
             }
           } else {
-            const int n = min(32, l - cb);
-            __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(dst);
-            for (int j = 0; j < n; ++j) o[j] = __float2bfloat16_rn(__uint_as_float(v[j]));
+            uint32_t w[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]));
+              w[t] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 16) {
+              const int t0 = j / 2;
+              if (j + 16 <= n) {
+                st_32(dst + j * 2, v32, w[t0], w[t0 + 1], w[t0 + 2], w[t0 + 3], w[t0 + 4], w[t0 + 5], w[t0 + 6],
+                      w[t0 + 7]);
+              } else {
+#pragma unroll
+                for (int t = 0; t < 16; ++t)
+                  if (j + t < n)
+                    reinterpret_cast<__nv_bfloat16 *>(dst)[j + t] = __float2bfloat16_rn(__uint_as_float(v[j + t]));
+              }
+            }
           }
         }
       }

@@ -2,10 +2,12 @@
 // (tcgen05), the contraction of CholeskyQR (Alg. 2: L = chol(Q^T Q)).
 //
 // Q is n x l row-major (l <= 160).  Each CTA reduces a contiguous range of
-// rows: 32 (FP32) or 64 (BF16) rows at a time are copied raw into shared
-// memory with cp.async (four chunks in flight), then producer warps write the
-// transposed chunk as a K-major operand tile (128-byte swizzle; three tile
-// stages): row m of the tile holds column m of Q over the chunk's rows.  The same tile is both MMA
+// rows: 32 (FP32) or 64 (BF16) rows at a time are copied raw into a ring of
+// shared-memory stages (one bulk copy per chunk when the rows are contiguous,
+// else 16-byte cp.async pieces; as many stages as the shared memory holds),
+// then producer warps write the transposed chunk as a K-major operand tile
+// (128-byte swizzle; three tile stages): row m of the tile holds column m of
+// Q over the chunk's rows.  The same tile is both MMA
 // operands (A rows and B rows are both columns of Q):
 //   tile 1: W[0:128, 0:N1]      M = 128, N = round16(l)
 //   tile 2: W[128:256, 128:N1]  M = 128, N = round16(l - 128)   (l > 128)
@@ -15,9 +17,13 @@
 // a little on every addition, and over thousands of rows the loss adds up
 // (CholeskyQR2's orthogonality fell linearly with the rows per CTA, 1.2e-4
 // at 6,600), so each 384-row segment is accumulated in tensor memory (two
-// buffers, alternating) and four epilogue warps add it into the CTA's FP64
-// partial (kept in L2) while the next segment is multiplied.  The partials
-// are combined in FP64 in a fixed order by gram_reduce (deterministic).
+// buffers, alternating) and four epilogue warps add it into the CTA's partial
+// (kept in L2) while the next segment is multiplied.  The partial is a
+// double-FP32 pair (hi, lo): hi is the FP32 running sum and lo collects the
+// exact rounding error of every addition (Knuth's TwoSum), so hi + lo carries
+// about 44 bits, at a small fraction of the cost of FP64 additions (GB300
+// issues one FP64 add per clock per SM).  The partials are combined in FP64
+// in a fixed order by gram_reduce (deterministic).
 #include <mutex>
 
 #include "internal.h"
@@ -31,9 +37,9 @@ using namespace tc;
 constexpr int kProdWarps = 8;
 constexpr int kProd = kProdWarps * 32;
 constexpr int kMmaWarp = kProdWarps;       // warp 8
-constexpr int kEpiWarp0 = kProdWarps + 1;  // warps 9..12
 constexpr int kThreads = kProd + 32 + 128;
-constexpr int kRawStages = 4;
+constexpr int kMaxRaw = 8;              // raw chunk stages at most
+constexpr int kMaxSmem = 225 * 1024;    // dynamic shared memory; the static barriers take the rest
 constexpr int kTileStages = 3;
 constexpr int kTmemCols = 512;
 constexpr int kAccCols = 256;  // accumulator buffer b at column b * kAccCols
@@ -43,7 +49,6 @@ constexpr int kSegRows = 384;  // rows summed in tensor memory before promotion 
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
@@ -58,10 +63,23 @@ struct GramCfg {
   static constexpr int NT = F32 ? 2 : 1;    // tiles per stage (hi, lo)
 };
 
+// raw stages that fit beside the tile stages (kMaxRaw at most, 2 at least)
+template <int DT>
+__host__ __device__ inline int gram_raw_stages(int32_t l) {
+  using C = GramCfg<DT>;
+  const int TR = l > 128 ? (l + 7) & ~7 : 128;
+  const int lp = (l + 7) & ~7;
+  const long tiles = (long)kTileStages * C::NT * TR * 128;
+  const long raw = (long)C::BK * lp * C::ES;
+  long r = (kMaxSmem - 1024 - tiles) / raw;
+  return (int)(r > kMaxRaw ? kMaxRaw : (r < 2 ? 2 : r));
+}
+
 template <int DT>
 __global__ void __launch_bounds__(kThreads, 1)
-    gram_tc_kernel(const void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, double *__restrict__ partial,
-                   int64_t rows_per_cta, const int32_t *gate_state, int32_t gate_pass, int32_t *err_state) {
+    gram_tc_kernel(const void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, float2 *__restrict__ partial,
+                   int64_t rows_per_cta, int32_t bulk, const int32_t *gate_state, int32_t gate_pass,
+                   int32_t *err_state) {
   using C = GramCfg<DT>;
   if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
   // A tile holds round8(l) rows (at least 128, the MMA's M).  For l > 128 the
@@ -72,13 +90,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tile_bytes = TR * 128;
   const int lp = (l + 7) & ~7;                     // raw row pitch in elements (16-byte multiple)
   const int raw_bytes = C::BK * lp * C::ES;
+  const int R = gram_raw_stages<DT>(l);
   extern __shared__ __align__(1024) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full[kTileStages], empty[kTileStages], seg_full[2], seg_free[2];
+  __shared__ __align__(8) uint64_t full[kTileStages], empty[kTileStages], seg_full[2], seg_free[2], raw_full[kMaxRaw];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   unsigned char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
   unsigned char *tiles = sm;                                       // [kTileStages][NT][tile]
-  unsigned char *raw = sm + (size_t)kTileStages * C::NT * tile_bytes;  // [kRawStages][raw]
+  unsigned char *raw = sm + (size_t)kTileStages * C::NT * tile_bytes;  // [R][raw]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r1 = min(rows, r0 + rows_per_cta);
@@ -99,6 +118,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&seg_full[b], 1);
       mbar_init(&seg_free[b], 128);
     }
+    // a raw stage completes on the bulk copy's bytes, or on every producer's cp.async pieces
+    for (int s = 0; s < R; ++s) mbar_init(&raw_full[s], bulk ? 1 : kProd);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -114,37 +135,57 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- producers ----------------
     const char *Q = reinterpret_cast<const char *>(Qv);
     const int pieces = (l * C::ES + 15) / 16;  // 16-byte pieces per row
+    int issued = 0;
     auto issue = [&](int c) {
-      if (c < nchunks) {
-        unsigned char *rb = raw + (size_t)(c % kRawStages) * raw_bytes;
-        const int64_t row0 = r0 + (int64_t)c * C::BK;
-        for (int t = tid; t < C::BK * pieces; t += kProd) {
-          const int rr = t / pieces, pc = t - rr * pieces;
-          const int64_t r = row0 + rr;
-          if (r < r1) cp_async16(smem_u32(rb + (size_t)rr * lp * C::ES + pc * 16), Q + ((size_t)r * ldq) * C::ES + pc * 16);
+      if (c >= nchunks) return;
+      unsigned char *rb = raw + (size_t)(c % R) * raw_bytes;
+      const int64_t row0 = r0 + (int64_t)c * C::BK;
+      const int valid = (int)((r1 - row0) < C::BK ? (r1 - row0) : C::BK);
+      if (bulk) {
+        // rows row0.. are contiguous (ldq == lp): one copy of valid * lp elements
+        if (tid == 0) {
+          const uint32_t bytes = (uint32_t)valid * lp * C::ES;
+          mbar_expect_tx(&raw_full[c % R], bytes);
+          bulk_g2s(smem_u32(rb), Q + (size_t)row0 * ldq * C::ES, bytes, &raw_full[c % R]);
         }
+      } else {
+        int rr = tid / pieces, pc = tid - rr * pieces;
+        const int drr = kProd / pieces, dpc = kProd - drr * pieces;
+        while (rr < valid) {
+          cp_async16(smem_u32(rb + (size_t)rr * lp * C::ES + pc * 16), Q + ((size_t)(row0 + rr) * ldq) * C::ES + pc * 16);
+          rr += drr;
+          pc += dpc;
+          if (pc >= pieces) {
+            pc -= pieces;
+            ++rr;
+          }
+        }
+        cp_async_arrive_noinc(&raw_full[c % R]);
       }
-      cp_async_commit();
+      issued = c + 1;
     };
-    for (int c = 0; c < kRawStages - 1; ++c) issue(c);
-    for (int c = 0; c < nchunks; ++c) {
-      issue(c + kRawStages - 1);
-      cp_async_wait<kRawStages - 1>();
+    // task (m, kq) of the transform: column m of Q over 16 bytes of K (4 FP32
+    // or 8 BF16 rows); this thread's tasks advance by kProd = dk * l + dm
+    const int m0 = tid % l, k0 = tid / l, dm = kProd % l, dk = kProd / l;
+    int c = 0;
+    for (int j = 0; j < R - 1; ++j) issue(j);
+    for (; c < nchunks; ++c) {
+      issue(c + R - 1);  // into the raw stage transformed in the previous iteration
       const int s = c % kTileStages;
+      bool ok = mbar_wait(&raw_full[c % R], (uint32_t)((c / R) & 1));
       // one thread waits for the tile stage to be free; the decision is shared
-      if (tid == 0 && c >= kTileStages && !mbar_wait(&empty[s], ((c / kTileStages) & 1) ^ 1)) {
+      if (tid == 0 && c >= kTileStages && !mbar_wait(&empty[s], ((c / kTileStages) & 1) ^ 1)) ok = false;
+      if (!ok) {
         abort_flag = 1;
         if (err_state) atomicExch(&err_state[2], 1);
       }
-      producer_bar();  // chunk c is in shared memory for every producer; stage s is free
+      producer_bar();  // chunk c is in shared memory; stage s is free
       if (abort_flag) break;
-      const unsigned char *rb = raw + (size_t)(c % kRawStages) * raw_bytes;
+      const unsigned char *rb = raw + (size_t)(c % R) * raw_bytes;
       const int64_t row0 = r0 + (int64_t)c * C::BK;
       const int valid = (int)((r1 - row0) < C::BK ? (r1 - row0) : C::BK);
       unsigned char *thi = tiles + (size_t)(s * C::NT) * tile_bytes;
-      // task (m, kq): column m of Q over 16 bytes of K (4 FP32 or 8 BF16 rows)
-      for (int t = tid; t < l * 8; t += kProd) {
-        const int m = t % l, kq = t / l;
+      for (int m = m0, kq = k0; kq < 8;) {
         if (C::F32) {
           float hi[4], lo[4];
 #pragma unroll
@@ -169,11 +210,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           w.w = v[6] | ((uint32_t)v[7] << 16);
           *reinterpret_cast<uint4 *>(thi + sw128(m, 16 * kq)) = w;
         }
+        m += dm;
+        kq += dk;
+        if (m >= l) {
+          m -= l;
+          ++kq;
+        }
       }
       fence_async_shared();
-      producer_bar();  // the tile is written (and the raw buffer of chunk c may be refilled)
+      producer_bar();  // the tile is written (and the raw stage of chunk c may be refilled)
       if (tid == 0) mbar_arrive(&full[s]);
     }
+    // after an abort, let the copies already issued land before the CTA exits
+    for (int j = c; j < issued; ++j) mbar_wait(&raw_full[j % R], (uint32_t)((j / R) & 1));
     cp_async_wait<0>();
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
@@ -227,12 +276,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue: each segment's sums -> the FP64 partial ----------------
+    // ---------------- epilogue: each segment's sums -> the (hi, lo) partial ----------------
     // Partial layout: P[n][i] = W[i][n] for i < 128 (tile 1, every n < l) and
     // P[128 + b][128 + a] = W[128 + a][128 + b] (tile 2); W is symmetric and the
     // reduction maps the rest.  Thread (quarter q, lane) owns W row i = 32 q + lane;
     // the quarter-0 warp also owns tile 2's rows.
-    double *P = partial + (size_t)blockIdx.x * l * l;
+    float2 *P = partial + (size_t)blockIdx.x * l * l;
     const int q = warp & 3;  // a warp reads the tensor-memory lanes of its quarter, 32 (warp % 4)
     const int i = q * 32 + lane;
     uint32_t r[32];
@@ -245,18 +294,25 @@ __global__ void __launch_bounds__(kThreads, 1)
       fence_after();
       const uint32_t d = tmem + (uint32_t)(b * kAccCols) + ((uint32_t)(q * 32) << 16);
       // 32 columns at a time: all loads of the running sums first, then the
-      // adds and stores (no load waits behind a store)
-      auto promote = [&](uint32_t taddr, double *base, int64_t stride, int ncols) {
+      // additions and stores (no load waits behind a store).  hi + x = s + e
+      // exactly (TwoSum); e joins lo.
+      auto promote = [&](uint32_t taddr, float2 *base, int64_t stride, int ncols) {
         tmem_ld32(taddr, r);
 #pragma unroll
         for (int h = 0; h < 32; h += 16) {
-          double old[16];
+          float2 old[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            old[j] = (seg > 0 && h + j < ncols) ? __ldcg(base + (int64_t)(h + j) * stride) : 0.0;
+            old[j] = (seg > 0 && h + j < ncols) ? __ldcg(base + (int64_t)(h + j) * stride) : make_float2(0.f, 0.f);
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (h + j < ncols) __stcg(base + (int64_t)(h + j) * stride, old[j] + (double)__uint_as_float(r[h + j]));
+            if (h + j < ncols) {
+              const float x = __uint_as_float(r[h + j]);
+              const float sum = __fadd_rn(old[j].x, x);
+              const float bv = __fsub_rn(sum, old[j].x);
+              const float e = __fadd_rn(__fsub_rn(old[j].x, __fsub_rn(sum, bv)), __fsub_rn(x, bv));
+              __stcg(base + (int64_t)(h + j) * stride, make_float2(sum, __fadd_rn(old[j].y, e)));
+            }
         }
       };
       for (int cb = 0; cb < N1; cb += 32) {
@@ -273,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (nseg == 0) {
       // no rows here: this partial is zero
-      for (int idx = i; idx < l * l; idx += 128) P[idx] = 0.0;
+      for (int idx = i; idx < l * l; idx += 128) P[idx] = make_float2(0.f, 0.f);
     }
   }
   fence_before();
@@ -281,23 +337,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// W[r][c] = sum over partials of P[r][c], except the block r < 128 <= c,
-// which tile 1 stored transposed (P[c][r]).
-__global__ void gram_reduce_tc_kernel(const double *partial, int32_t n_part, int32_t l, double *W,
+// W[r][c] = sum over partials of P[r][c] (hi + lo, in FP64), except the
+// block r < 128 <= c, which tile 1 stored transposed (P[c][r]).
+__global__ void gram_reduce_tc_kernel(const float2 *partial, int32_t n_part, int32_t l, double *W,
                                       const int32_t *gate_state, int32_t gate_pass) {
   if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)l * l) return;
   const int r = (int)(idx / l), c = (int)(idx - (int64_t)r * l);
   const int64_t src = (r < 128 && c >= 128) ? (int64_t)c * l + r : idx;
-  // eight interleaved sums (fixed order), so the loads of different partials overlap
+  // eight interleaved sums (fixed order), so the loads of different partials
+  // overlap; the hi parts in FP64, the lo parts (each below 2^-20 of its hi)
+  // in FP32, which keeps their rounding far below FP32's
   double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  float lo[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int p = 0;
   for (; p + 8 <= n_part; p += 8)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] += partial[(int64_t)(p + u) * l * l + src];
-  for (; p < n_part; ++p) acc[p & 7] += partial[(int64_t)p * l * l + src];
-  W[idx] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    for (int u = 0; u < 8; ++u) {
+      const float2 v = partial[(int64_t)(p + u) * l * l + src];
+      acc[u] += (double)v.x;
+      lo[u] += v.y;
+    }
+#pragma unroll
+  for (int u = 0; u < 7; ++u)
+    if (p + u < n_part) {
+      const float2 v = partial[(int64_t)(p + u) * l * l + src];
+      acc[u] += (double)v.x;
+      lo[u] += v.y;
+    }
+  const float lsum = ((lo[0] + lo[1]) + (lo[2] + lo[3])) + ((lo[4] + lo[5]) + (lo[6] + lo[7]));
+  W[idx] = (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]))) + (double)lsum;
 }
 
 template <int DT>
@@ -306,7 +376,7 @@ size_t gram_tc_smem(int32_t l) {
   const int TR = l > 128 ? (l + 7) & ~7 : 128;
   const int lp = (l + 7) & ~7;
   // tiles, then the raw ring (at least 16 KB after the last tile, see above)
-  return (size_t)kTileStages * C::NT * TR * 128 + (size_t)kRawStages * C::BK * lp * C::ES + 1024;
+  return (size_t)kTileStages * C::NT * TR * 128 + (size_t)gram_raw_stages<DT>(l) * C::BK * lp * C::ES + 1024;
 }
 
 std::once_flag g_once;
@@ -316,11 +386,9 @@ cudaError_t g_err = cudaSuccess;
 
 cudaError_t gram_tc_init() {
   std::call_once(g_once, [] {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<DT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gram_tc_smem<DT_F32>(ISVD_MAX_BLOCK));
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<DT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gram_tc_kernel<DT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)gram_tc_smem<DT_BF16>(ISVD_MAX_BLOCK));
+      e = cudaFuncSetAttribute(gram_tc_kernel<DT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     g_err = e;
   });
   return g_err;
@@ -341,13 +409,18 @@ cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int
   const int64_t rpc = round_up(ceil_div(rows, n_part), bk);
   const int32_t used = (int32_t)std::max<int64_t>(1, ceil_div(rows, rpc));
   int32_t *err = const_cast<int32_t *>(g.state);
+  // one bulk copy per chunk when consecutive rows are contiguous (pitch = the
+  // 16-byte-rounded row) and the block starts on a 16-byte boundary
+  const int32_t bulk = ldq == ((l + 7) & ~7) && ((uintptr_t)Q & 15) == 0;
+  float2 *P = reinterpret_cast<float2 *>(partial);  // 8 bytes per element either way
   if (dtype == DT_F32)
-    gram_tc_kernel<DT_F32><<<used, kThreads, gram_tc_smem<DT_F32>(l), s>>>(Q, ldq, rows, l, partial, rpc, g.state,
+    gram_tc_kernel<DT_F32><<<used, kThreads, gram_tc_smem<DT_F32>(l), s>>>(Q, ldq, rows, l, P, rpc, bulk, g.state,
                                                                             g.pass, err);
   else
-    gram_tc_kernel<DT_BF16><<<used, kThreads, gram_tc_smem<DT_BF16>(l), s>>>(Q, ldq, rows, l, partial, rpc, g.state,
+    gram_tc_kernel<DT_BF16><<<used, kThreads, gram_tc_smem<DT_BF16>(l), s>>>(Q, ldq, rows, l, P, rpc, bulk, g.state,
                                                                               g.pass, err);
-  gram_reduce_tc_kernel<<<(unsigned)ceil_div((int64_t)l * l, 256), 256, 0, s>>>(partial, used, l, W, g.state, g.pass);
+  // small blocks spread the FP64 additions over all SMs
+  gram_reduce_tc_kernel<<<(unsigned)ceil_div((int64_t)l * l, 64), 64, 0, s>>>(P, used, l, W, g.state, g.pass);
   return cudaGetLastError();
 }
 

@@ -64,7 +64,8 @@ extern "C" isvd_status isvd_orthonormalize_noalloc(float *Q, int64_t rows, int32
     return fail(ISVD_ERR_UNSUPPORTED, "isvd_orthonormalize_noalloc: block width %d outside 1..%d (fixed scratch size)",
                 l, kNoallocMaxBlock);
   if (rows < l) return fail(ISVD_ERR_SHAPE, "need rows >= l");
-  if (ldq < l) return fail(ISVD_ERR_INVALID_ARGUMENT, "ldq must be >= l");
+  if (ldq < l || ldq % 8 || (uintptr_t)Q % 16)
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "ldq must be >= l and a multiple of 8, Q 16-byte aligned");
   unsigned char *base = nullptr;
   ISVD_TRY(setup_device(&base));
   OrthBufs o;

@@ -19,6 +19,11 @@
 // combined in chunk order, so results are deterministic.
 #include "internal.h"
 
+// blocks per SM of the FP32 row kernel at high occupancy (a build-time knob)
+#ifndef ISVD_ROWS_HIGH_OCC_F32
+#define ISVD_ROWS_HIGH_OCC_F32 6
+#endif
+
 namespace isvd {
 namespace {
 
@@ -435,8 +440,11 @@ cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, i
     spmm_chunks_kernel<DT, HINT, CPL><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, hs>>>(
         a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
   }
+  // high occupancy: 6 blocks of 256 threads per SM (40 registers) for FP32;
+  // BF16 rows hold twice the accumulators and take 5 (48 registers, no spills)
+  constexpr int kHighOcc = DT == DT_F32 ? ISVD_ROWS_HIGH_OCC_F32 : 5;
   if (a.rows_occupancy >= 3)
-    spmm_rows_kernel<DT, HINT, 6, CPL><<<grid, threads, 0, s>>>(a);
+    spmm_rows_kernel<DT, HINT, kHighOcc, CPL><<<grid, threads, 0, s>>>(a);
   else
     spmm_rows_kernel<DT, HINT, 1, CPL><<<grid, threads, 0, s>>>(a);
   if (fork) {

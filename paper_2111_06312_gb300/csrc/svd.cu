@@ -451,7 +451,8 @@ isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t rows, int32
                                 isvd_info *dev_info, void *stream) {
   if (!op || !Q) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
   if (l < 1 || l > ISVD_MAX_BLOCK || rows < l) return fail(ISVD_ERR_SHAPE, "need 1 <= l <= min(rows, %d)", ISVD_MAX_BLOCK);
-  if (ldq < l) return fail(ISVD_ERR_INVALID_ARGUMENT, "ldq must be >= l");
+  if (ldq < l || ldq % 8 || (uintptr_t)Q % 16)
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "ldq must be >= l and a multiple of 8, Q 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   Carver c{nullptr};
   OrthBufs o;

@@ -59,3 +59,19 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(isvd, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         isvd.lib()
+
+
+def test_orthonormalize_noalloc_rejects_bad_layouts_on_the_host(libisvd):
+    # the row pitch and base alignment that the kernels' 16-byte copies need are
+    # checked before the device is touched (no GPU here)
+    libisvd.isvd_last_error.restype = C.c_char_p
+    fn = libisvd.isvd_orthonormalize_noalloc
+    fn.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    fn.restype = C.c_int
+    fake = C.c_void_p(1 << 20)  # never dereferenced: every call below fails its host checks
+    assert fn(None, 100, 8, 8, None, None, None) == 1
+    assert fn(fake, 100, 8, 12, None, None, None) == 1  # pitch not a multiple of 8
+    assert b"multiple of 8" in libisvd.isvd_last_error()
+    assert fn(C.c_void_p((1 << 20) + 4), 100, 8, 8, None, None, None) == 1  # base not 16-byte aligned
+    assert fn(fake, 100, 8, 4, None, None, None) == 1  # pitch below the width
+    assert fn(fake, 4, 8, 8, None, None, None) == 3  # fewer rows than columns: ISVD_ERR_SHAPE

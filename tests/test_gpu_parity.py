@@ -246,6 +246,27 @@ def test_orthonormalize(ne_small, rows, l, cond):
         assert inf["chol_shifts"] >= 1 and inf["cholqr_passes"] >= 3
 
 
+@pytest.mark.parametrize("rows,l,width,col0", [(7001, 40, 64, 0), (3000, 144, 152, 4), (12345, 9, 24, 4)])
+def test_orthonormalize_strided_view(ne_small, rows, l, width, col0):
+    """A column slice of a wider buffer (row pitch above round8(l)): the Gram
+    loads rows piece by piece instead of one copy per chunk; a slice starting
+    at column 4 is 16- but not 32-byte aligned (16-byte stores in Q R^-1);
+    the other columns stay untouched."""
+    Q0 = cond_block(rows, l, 1e3, 11)
+    buf = torch.full((rows, width), 7.0, dtype=torch.float32, device="cuda")
+    buf[:, col0:col0 + l] = torch.tensor(Q0, dtype=torch.float32, device="cuda")
+    with isvd.graph_operator(ne_small, coeffs=C5) as op:
+        Qg, R, info = isvd.orthonormalize(op, buf[:, col0:col0 + l])
+        assert Qg.data_ptr() == buf[:, col0:].data_ptr()  # worked in place on the view
+        inf = isvd.info_dict(info)
+    assert inf["status"] == "OK"
+    Qn = npy(buf[:, col0:col0 + l])
+    assert np.abs(Qn.T @ Qn - np.eye(l)).max() < 2e-5
+    assert np.abs(Qn @ R.cpu().numpy() - Q0).max() < 1e-5 * np.abs(Q0).max()
+    rest = torch.cat([buf[:, :col0], buf[:, col0 + l:]], dim=1)
+    assert bool((rest == 7.0).all())
+
+
 @pytest.mark.parametrize("l,cond,upper", [(8, 10.0, False), (42, 1e6, True), (144, 1e8, True), (160, 1e3, False)])
 def test_small_svd(ne_small, l, cond, upper):
     A = cond_block(l, l, cond, 9)
