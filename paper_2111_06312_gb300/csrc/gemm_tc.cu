@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool v32 = ((uintptr_t)Q & 31) == 0 && ((ldq * C::ES) & 31) == 0;
     for (int64_t lt = 0; lt < my_tiles; ++lt) {
       const int d = (int)(lt & 1);
-      if (!mbar_wait(&dfull[d], (uint32_t)((lt >> 1) & 1))) {
+      if (!mbar_wait_sleep(&dfull[d], (uint32_t)((lt >> 1) & 1), 256)) {
         if (err_state && lane == 0) atomicExch(&err_state[2], 1);
         break;
       }

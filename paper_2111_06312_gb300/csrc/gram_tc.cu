@@ -17,13 +17,12 @@
 // a little on every addition, and over thousands of rows the loss adds up
 // (CholeskyQR2's orthogonality fell linearly with the rows per CTA, 1.2e-4
 // at 6,600), so each 384-row segment is accumulated in tensor memory (two
-// buffers, alternating) and four epilogue warps add it into the CTA's partial
-// (kept in L2) while the next segment is multiplied.  The partial is a
-// double-FP32 pair (hi, lo): hi is the FP32 running sum and lo collects the
-// exact rounding error of every addition (Knuth's TwoSum), so hi + lo carries
-// about 44 bits, at a small fraction of the cost of FP64 additions (GB300
-// issues one FP64 add per clock per SM).  The partials are combined in FP64
-// in a fixed order by gram_reduce (deterministic).
+// buffers, alternating) and eight epilogue warps add it, with round-to-nearest
+// FP32 additions, into the CTA's partial held in their registers (thread =
+// one row of W and half of its columns) while the next segment is multiplied.
+// The segment sums are few (17 per CTA at 10^6 rows), so this adds only
+// ~sqrt(17) u of relative error; the partials are written once at the end and
+// combined in FP64 in a fixed order by gram_reduce (deterministic).
 #include <mutex>
 
 #include "internal.h"
@@ -34,12 +33,15 @@ namespace {
 
 using namespace tc;
 
-constexpr int kProdWarps = 8;
+constexpr int kProdWarps = 7;  // with the MMA warp and 8 epilogue warps: 16 warps, 128 registers each
 constexpr int kProd = kProdWarps * 32;
-constexpr int kMmaWarp = kProdWarps;       // warp 8
-constexpr int kThreads = kProd + 32 + 128;
+constexpr int kMmaWarp = kProdWarps;       // warp 7
+constexpr int kEpiWarp0 = kProdWarps + 1;  // warps 8..15: epilogue (two per TMEM lane quarter)
+constexpr int kEpiThreads = 256;
+constexpr int kThreads = kProd + 32 + kEpiThreads;
+constexpr int kHalfBlocks = 5;  // 16-column blocks of tile 1 per epilogue half (N1 <= 160)
 constexpr int kMaxRaw = 8;              // raw chunk stages at most
-constexpr int kMaxSmem = 225 * 1024;    // dynamic shared memory; the static barriers take the rest
+constexpr int kMaxSmem = 221 * 1024;    // dynamic shared memory; the static part (tile-2 partial, barriers) takes the rest
 constexpr int kTileStages = 3;
 constexpr int kTmemCols = 512;
 constexpr int kAccCols = 256;  // accumulator buffer b at column b * kAccCols
@@ -77,7 +79,7 @@ __host__ __device__ inline int gram_raw_stages(int32_t l) {
 
 template <int DT>
 __global__ void __launch_bounds__(kThreads, 1)
-    gram_tc_kernel(const void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, float2 *__restrict__ partial,
+    gram_tc_kernel(const void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, float *__restrict__ partial,
                    int64_t rows_per_cta, int32_t bulk, const int32_t *gate_state, int32_t gate_pass,
                    int32_t *err_state) {
   using C = GramCfg<DT>;
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&seg_full[b], 1);
-      mbar_init(&seg_free[b], 128);
+      mbar_init(&seg_free[b], kEpiThreads);
     }
     // a raw stage completes on the bulk copy's bytes, or on every producer's cp.async pieces
     for (int s = 0; s < R; ++s) mbar_init(&raw_full[s], bulk ? 1 : kProd);
@@ -165,8 +167,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       issued = c + 1;
     };
     // task (m, kq) of the transform: column m of Q over 16 bytes of K (4 FP32
-    // or 8 BF16 rows); this thread's tasks advance by kProd = dk * l + dm
-    const int m0 = tid % l, k0 = tid / l, dm = kProd % l, dk = kProd / l;
+    // or 8 BF16 rows).  This thread's tasks (m0 + i kProd) are the same for
+    // every chunk: their shared-memory offsets are computed once (source: the
+    // task's first raw row; destination: the swizzled tile position).
+    constexpr int kMaxTasks = (ISVD_MAX_BLOCK * 8 + kProd - 1) / kProd;
+    const int rs = lp * C::ES;  // raw row pitch in bytes
+    uint32_t src_off[kMaxTasks], dst_off[kMaxTasks];
+    int row_of[kMaxTasks];
+    int ntask = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxTasks; ++i) {
+      const int t = tid + i * kProd;
+      const int m = t % l, kq = t / l;
+      row_of[i] = (C::F32 ? 4 : 8) * kq;
+      src_off[i] = (uint32_t)(row_of[i] * rs + m * C::ES);
+      dst_off[i] = sw128(m, 16 * kq);
+      if (t < l * 8) ntask = i + 1;
+    }
     int c = 0;
     for (int j = 0; j < R - 1; ++j) issue(j);
     for (; c < nchunks; ++c) {
@@ -185,36 +202,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row0 = r0 + (int64_t)c * C::BK;
       const int valid = (int)((r1 - row0) < C::BK ? (r1 - row0) : C::BK);
       unsigned char *thi = tiles + (size_t)(s * C::NT) * tile_bytes;
-      for (int m = m0, kq = k0; kq < 8;) {
+#pragma unroll
+      for (int i = 0; i < kMaxTasks; ++i) {
+        if (i >= ntask) break;
+        const unsigned char *src = rb + src_off[i];
+        const int rr0 = row_of[i];  // first raw row of the task (rows past valid read as 0)
         if (C::F32) {
           float hi[4], lo[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const int rr = 4 * kq + j;
-            const float x = rr < valid ? reinterpret_cast<const float *>(rb + (size_t)rr * lp * 4)[m] : 0.f;
+            const float x = (valid == C::BK || rr0 + j < valid) ? *reinterpret_cast<const float *>(src + j * rs) : 0.f;
             split_tf32(x, hi[j], lo[j]);
           }
-          *reinterpret_cast<float4 *>(thi + sw128(m, 16 * kq)) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<float4 *>(thi + tile_bytes + sw128(m, 16 * kq)) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+          *reinterpret_cast<float4 *>(thi + dst_off[i]) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<float4 *>(thi + tile_bytes + dst_off[i]) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         } else {
-          unsigned short v[8];
+          uint32_t v[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int rr = 8 * kq + j;
-            v[j] = rr < valid ? reinterpret_cast<const unsigned short *>(rb + (size_t)rr * lp * 2)[m] : (unsigned short)0;
-          }
-          uint4 w;
-          w.x = v[0] | ((uint32_t)v[1] << 16);
-          w.y = v[2] | ((uint32_t)v[3] << 16);
-          w.z = v[4] | ((uint32_t)v[5] << 16);
-          w.w = v[6] | ((uint32_t)v[7] << 16);
-          *reinterpret_cast<uint4 *>(thi + sw128(m, 16 * kq)) = w;
-        }
-        m += dm;
-        kq += dk;
-        if (m >= l) {
-          m -= l;
-          ++kq;
+          for (int j = 0; j < 8; ++j)
+            v[j] = (valid == C::BK || rr0 + j < valid) ? *reinterpret_cast<const unsigned short *>(src + j * rs) : 0u;
+          *reinterpret_cast<uint4 *>(thi + dst_off[i]) =
+              make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16));
         }
       }
       fence_async_shared();
@@ -276,15 +284,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue: each segment's sums -> the (hi, lo) partial ----------------
+    // ---------------- epilogue: each segment's sums -> the register partial ----------------
     // Partial layout: P[n][i] = W[i][n] for i < 128 (tile 1, every n < l) and
     // P[128 + b][128 + a] = W[128 + a][128 + b] (tile 2); W is symmetric and the
-    // reduction maps the rest.  Thread (quarter q, lane) owns W row i = 32 q + lane;
-    // the quarter-0 warp also owns tile 2's rows.
-    float2 *P = partial + (size_t)blockIdx.x * l * l;
+    // reduction maps the rest.  Thread (quarter q, half h, lane) owns W row
+    // i = 32 q + lane, columns [80 h, 80 h + 80) of tile 1; the quarter-0 warp
+    // of half 1 also owns tile 2's rows (partial in shared memory).
+    __shared__ float t2part[32 * 32];  // [column][lane]
     const int q = warp & 3;  // a warp reads the tensor-memory lanes of its quarter, 32 (warp % 4)
+    const int h = (warp - kEpiWarp0) >> 2;
     const int i = q * 32 + lane;
-    uint32_t r[32];
+    const int nblk = N1 / 16;
+    const bool owns_t2 = N2 > 0 && q == 0 && h == 1;
+    float part[kHalfBlocks][16];
+#pragma unroll
+    for (int k = 0; k < kHalfBlocks; ++k)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) part[k][j] = 0.f;
+    if (owns_t2)
+      for (int c = 0; c < 32; ++c) t2part[c * 32 + lane] = 0.f;
+    uint32_t v[16];
     for (int seg = 0; seg < nseg; ++seg) {
       const int b = seg & 1;
       if (!mbar_wait(&seg_full[b], (uint32_t)((seg >> 1) & 1))) {
@@ -293,81 +312,81 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_after();
       const uint32_t d = tmem + (uint32_t)(b * kAccCols) + ((uint32_t)(q * 32) << 16);
-      // 32 columns at a time: all loads of the running sums first, then the
-      // additions and stores (no load waits behind a store).  hi + x = s + e
-      // exactly (TwoSum); e joins lo.
-      auto promote = [&](uint32_t taddr, float2 *base, int64_t stride, int ncols) {
-        tmem_ld32(taddr, r);
 #pragma unroll
-        for (int h = 0; h < 32; h += 16) {
-          float2 old[16];
+      for (int k = 0; k < kHalfBlocks; ++k) {
+        const int blk = h * kHalfBlocks + k;
+        if (blk < nblk) {
+          tmem_ld16(d + (uint32_t)(blk * 16), v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            old[j] = (seg > 0 && h + j < ncols) ? __ldcg(base + (int64_t)(h + j) * stride) : make_float2(0.f, 0.f);
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (h + j < ncols) {
-              const float x = __uint_as_float(r[h + j]);
-              const float sum = __fadd_rn(old[j].x, x);
-              const float bv = __fsub_rn(sum, old[j].x);
-              const float e = __fadd_rn(__fsub_rn(old[j].x, __fsub_rn(sum, bv)), __fsub_rn(x, bv));
-              __stcg(base + (int64_t)(h + j) * stride, make_float2(sum, __fadd_rn(old[j].y, e)));
-            }
+          for (int j = 0; j < 16; ++j) part[k][j] = __fadd_rn(part[k][j], __uint_as_float(v[j]));
         }
-      };
-      for (int cb = 0; cb < N1; cb += 32) {
-        const int ncols = i < l ? min(32, l - cb) : 0;
-        promote(d + cb, P + (size_t)cb * l + i, l, ncols);
       }
-      if (N2 && q == 0) {
-        const int a = lane;  // W row 128 + a; column 128 + j of tile 2
-        const int ncols = 128 + a < l ? min(N2, l - 128) : 0;
-        promote(d + kTile2Col, P + (size_t)128 * l + 128 + a, l, ncols);
-      }
+      if (owns_t2)
+        for (int c0 = 0; c0 < N2; c0 += 16) {
+          tmem_ld16(d + (uint32_t)(kTile2Col + c0), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            t2part[(c0 + j) * 32 + lane] = __fadd_rn(t2part[(c0 + j) * 32 + lane], __uint_as_float(v[j]));
+        }
       fence_before();
       mbar_arrive(&seg_free[b]);
     }
-    if (nseg == 0) {
-      // no rows here: this partial is zero
-      for (int idx = i; idx < l * l; idx += 128) P[idx] = make_float2(0.f, 0.f);
+    // one write of the partial (zero when this CTA had no rows)
+    float *P = partial + (size_t)blockIdx.x * l * l;
+    if (i < l) {
+#pragma unroll
+      for (int k = 0; k < kHalfBlocks; ++k) {
+        const int c0 = (h * kHalfBlocks + k) * 16;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < l) P[(size_t)(c0 + j) * l + i] = part[k][j];
+      }
     }
+    if (owns_t2 && 128 + lane < l)
+      for (int c = 0; c < l - 128; ++c) P[(size_t)(128 + c) * l + 128 + lane] = t2part[c * 32 + lane];
   }
   fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// W[r][c] = sum over partials of P[r][c] (hi + lo, in FP64), except the
-// block r < 128 <= c, which tile 1 stored transposed (P[c][r]).
-__global__ void gram_reduce_tc_kernel(const float2 *partial, int32_t n_part, int32_t l, double *W,
-                                      const int32_t *gate_state, int32_t gate_pass) {
+// W[r][c] = sum over partials of P[r][c] (in FP64), except the block
+// r < 128 <= c, which tile 1 stored transposed (P[c][r]).  A block covers
+// kRedCols elements with kRedGroups thread rows; row g sums partials g,
+// g + kRedGroups, ... (eight interleaved sums per thread, so that loads
+// overlap), and the group sums are added in a fixed order (deterministic).
+constexpr int kRedCols = 64, kRedGroups = 4;
+
+__global__ void __launch_bounds__(kRedCols *kRedGroups)
+    gram_reduce_tc_kernel(const float *partial, int32_t n_part, int32_t l, double *W, const int32_t *gate_state,
+                          int32_t gate_pass) {
   if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)l * l) return;
-  const int r = (int)(idx / l), c = (int)(idx - (int64_t)r * l);
-  const int64_t src = (r < 128 && c >= 128) ? (int64_t)c * l + r : idx;
-  // eight interleaved sums (fixed order), so the loads of different partials
-  // overlap; the hi parts in FP64, the lo parts (each below 2^-20 of its hi)
-  // in FP32, which keeps their rounding far below FP32's
-  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  float lo[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int p = 0;
-  for (; p + 8 <= n_part; p += 8)
+  __shared__ double part[kRedGroups][kRedCols];
+  const int g = threadIdx.y;
+  const int64_t idx = (int64_t)blockIdx.x * kRedCols + threadIdx.x;
+  double total = 0.0;
+  if (idx < (int64_t)l * l) {
+    const int r = (int)(idx / l), c = (int)(idx - (int64_t)r * l);
+    const int64_t src = (r < 128 && c >= 128) ? (int64_t)c * l + r : idx;
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const int64_t stride = (int64_t)l * l;
+    int p = g;
+    for (; p + 7 * kRedGroups < n_part; p += 8 * kRedGroups)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const float2 v = partial[(int64_t)(p + u) * l * l + src];
-      acc[u] += (double)v.x;
-      lo[u] += v.y;
-    }
+      for (int u = 0; u < 8; ++u) acc[u] += (double)partial[(int64_t)(p + u * kRedGroups) * stride + src];
 #pragma unroll
-  for (int u = 0; u < 7; ++u)
-    if (p + u < n_part) {
-      const float2 v = partial[(int64_t)(p + u) * l * l + src];
-      acc[u] += (double)v.x;
-      lo[u] += v.y;
-    }
-  const float lsum = ((lo[0] + lo[1]) + (lo[2] + lo[3])) + ((lo[4] + lo[5]) + (lo[6] + lo[7]));
-  W[idx] = (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]))) + (double)lsum;
+    for (int u = 0; u < 7; ++u)
+      if (p + u * kRedGroups < n_part) acc[u] += (double)partial[(int64_t)(p + u * kRedGroups) * stride + src];
+    total = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  }
+  part[g][threadIdx.x] = total;
+  __syncthreads();
+  if (g == 0 && idx < (int64_t)l * l) {
+    double w = part[0][threadIdx.x];
+#pragma unroll
+    for (int t = 1; t < kRedGroups; ++t) w += part[t][threadIdx.x];
+    W[idx] = w;
+  }
 }
 
 template <int DT>
@@ -412,15 +431,15 @@ cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int
   // one bulk copy per chunk when consecutive rows are contiguous (pitch = the
   // 16-byte-rounded row) and the block starts on a 16-byte boundary
   const int32_t bulk = ldq == ((l + 7) & ~7) && ((uintptr_t)Q & 15) == 0;
-  float2 *P = reinterpret_cast<float2 *>(partial);  // 8 bytes per element either way
+  float *P = reinterpret_cast<float *>(partial);  // FP32 partials in the FP64-sized buffer
   if (dtype == DT_F32)
     gram_tc_kernel<DT_F32><<<used, kThreads, gram_tc_smem<DT_F32>(l), s>>>(Q, ldq, rows, l, P, rpc, bulk, g.state,
                                                                             g.pass, err);
   else
     gram_tc_kernel<DT_BF16><<<used, kThreads, gram_tc_smem<DT_BF16>(l), s>>>(Q, ldq, rows, l, P, rpc, bulk, g.state,
                                                                               g.pass, err);
-  // small blocks spread the FP64 additions over all SMs
-  gram_reduce_tc_kernel<<<(unsigned)ceil_div((int64_t)l * l, 64), 64, 0, s>>>(P, used, l, W, g.state, g.pass);
+  gram_reduce_tc_kernel<<<(unsigned)ceil_div((int64_t)l * l, kRedCols), dim3(kRedCols, kRedGroups), 0, s>>>(
+      P, used, l, W, g.state, g.pass);
   return cudaGetLastError();
 }
 
