@@ -6,12 +6,18 @@
 // triangular, panel p only multiplies output columns n >= first k of the
 // panel, so it is stored and multiplied for those columns only (MMA N shrinks
 // panel by panel, and its accumulator starts at that column).  Q is streamed in
-// 128-row tiles, panel by panel, by cp.async straight into the swizzled
-// layout (row r of the tile = 128 bytes of row r of Q), three panels ahead of
+// 128-row tiles, panel by panel, straight into the swizzled layout (row r of
+// the tile = 128 bytes of row r of Q): one TMA box load per panel (the tensor
+// map zero-fills columns >= l and rows past the end), or 16-byte cp.async
+// pieces where the block's base or pitch rules TMA out; three panels ahead of
 // the two operand stages the MMA reads.  FP32 blocks use
 // 3xTF32 (A and B split into TF32 hi + lo); BF16 blocks one BF16 MMA.  The
 // FP32 accumulator (128 x round16(l)) is double-buffered in tensor memory so
 // the epilogue warps write tile t while tile t+1 is multiplied.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
 #include <mutex>
 
 #include "internal.h"
@@ -25,7 +31,6 @@ using namespace tc;
 constexpr int kProdWarps = 8;
 constexpr int kProd = kProdWarps * 32;
 constexpr int kMmaWarp = kProdWarps;       // warp 8
-constexpr int kEpiWarp0 = kProdWarps + 1;  // warps 9..12
 constexpr int kThreads = (kProdWarps + 1 + 4) * 32;
 constexpr int kStages = 2;  // operand stages shared with the MMA warp
 constexpr int kMaxSmem = 225 * 1024;  // dynamic; the static barriers take the rest of the 227 KB
@@ -90,12 +95,13 @@ __host__ __device__ Layout make_layout(int l) {
 template <int DT, int kRaw>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, const float *__restrict__ B,
-                   int64_t ldb, const int32_t *gate_state, int32_t gate_pass, int32_t *err_state) {
+                   int64_t ldb, const __grid_constant__ CUtensorMap tmap, int32_t use_tma,
+                   const int32_t *gate_state, int32_t gate_pass, int32_t *err_state) {
   using C = GemmCfg<DT>;
   if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
   const Layout L = make_layout<DT>(l);
   extern __shared__ __align__(1024) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], dfull[2], dfree[2];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], dfull[2], dfree[2], raw_full[kRaw];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   unsigned char *sm = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
@@ -135,6 +141,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&dfull[d], 1);
       mbar_init(&dfree[d], 128);
     }
+    for (int r = 0; r < kRaw; ++r) mbar_init(&raw_full[r], 1);  // TMA: one expect_tx arrive + the box bytes
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -155,7 +162,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     // or BF16 with padding columns zeroed) once the MMA has released it.
     auto tile_row0 = [&](int64_t lt) { return ((int64_t)blockIdx.x + lt * gridDim.x) * 128; };
     auto issue = [&](int64_t g) {
-      if (g < G) {
+      if (g < G && use_tma) {
+        if (tid == 0) {
+          const int64_t lt = g / L.KP;
+          const int p = (int)(g - lt * L.KP);
+          unsigned char *rb = rawring + (size_t)(g % kRaw) * (128 * 128);
+          mbar_expect_tx(&raw_full[g % kRaw], 128 * 128);
+          tma_load_2d(smem_u32(rb), &tmap, p * C::KE, (int32_t)tile_row0(lt), &raw_full[g % kRaw]);
+        }
+      } else if (g < G) {
         const int64_t lt = g / L.KP;
         const int p = (int)(g - lt * L.KP);
         unsigned char *rb = rawring + (size_t)(g % kRaw) * (128 * 128);
@@ -171,29 +186,41 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       cp_async_commit();  // one group per panel (empty past the end) keeps the wait count fixed
     };
+    // this thread's four 16-byte pieces of a panel: (row t / 8, chunk t % 8)
+    // for t = tid + i kProd; the same swizzled offsets in every panel
+    static_assert(128 * 8 == 4 * kProd, "four 16-byte pieces of a panel per producer thread");
+    uint32_t poff[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = tid + i * kProd;
+      poff[i] = sw128(t >> 3, (t & 7) * 16);
+    }
     auto transform = [&](int64_t g) {
       const int s = (int)(g % kStages);
       const int p = (int)(g % L.KP);
       const unsigned char *rb = rawring + (size_t)(g % kRaw) * (128 * 128);
       unsigned char *ahi = astage + (size_t)s * C::STAGE;
       unsigned char *alo = ahi + 128 * 128;
-      for (int t = tid; t < 128 * 8; t += kProd) {
-        const int r = t >> 3, q = t & 7;
-        const uint32_t off = sw128(r, q * 16);
-        const int k0 = p * C::KE + q * (16 / C::ES);  // first column of this piece
+      // padding columns (>= l) never enter the product: TMA fills them with
+      // zeros, the cp.async pieces are cleared here
+      const bool clear = !use_tma && (p + 1) * C::KE > l;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t off = poff[i];
+        const int k0 = p * C::KE + (((tid + i * kProd) & 7) * (16 / C::ES));  // first column of this piece
         if (C::F32) {
           const float4 v = *reinterpret_cast<const float4 *>(rb + off);
           float x[4] = {v.x, v.y, v.z, v.w}, hi[4], lo[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            if (k0 + j >= l) x[j] = 0.f;  // padding columns never enter the product
+            if (clear && k0 + j >= l) x[j] = 0.f;
             split_tf32(x[j], hi[j], lo[j]);
           }
           *reinterpret_cast<float4 *>(ahi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
           *reinterpret_cast<float4 *>(alo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
         } else {
           uint4 v = *reinterpret_cast<const uint4 *>(rb + off);
-          if (k0 + 8 > l) {
+          if (clear && k0 + 8 > l) {
             unsigned short *h = reinterpret_cast<unsigned short *>(&v);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
@@ -204,21 +231,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
     for (int64_t g = 0; g < kRaw - 1; ++g) issue(g);
-    for (int64_t g = 0; g < G; ++g) {
+    int64_t g = 0;
+    for (; g < G; ++g) {
       issue(g + kRaw - 1);           // into the raw stage transformed in the previous iteration
-      cp_async_wait<kRaw - 1>();     // this thread's copies of panel g have landed
+      bool ok = true;
+      if (use_tma) ok = mbar_wait(&raw_full[g % kRaw], (uint32_t)((g / kRaw) & 1));  // the box landed
+      else cp_async_wait<kRaw - 1>();  // this thread's copies of panel g have landed
       const int s = (int)(g % kStages);
-      if (tid == 0 && g >= kStages && !mbar_wait(&empty[s], (uint32_t)(((g / kStages) & 1) ^ 1))) {
+      if (tid == 0 && g >= kStages && !mbar_wait(&empty[s], (uint32_t)(((g / kStages) & 1) ^ 1))) ok = false;
+      if (!ok) {
         abort_flag = 1;
         if (err_state) atomicExch(&err_state[2], 1);
       }
-      producer_bar();  // every producer's copies of panel g landed; operand stage s is free
+      producer_bar();  // panel g is in shared memory; operand stage s is free
       if (abort_flag) break;
       transform(g);
       fence_async_shared();
       producer_bar();  // the operand stage is written (and the raw stage of panel g may be refilled)
       if (tid == 0) mbar_arrive(&full[s]);
     }
+    // after an abort, let the boxes already requested land before the CTA exits
+    if (use_tma)
+      for (int64_t j = g; j < std::min<int64_t>(G, g + kRaw); ++j)
+        mbar_wait(&raw_full[j % kRaw], (uint32_t)((j / kRaw) & 1));
     cp_async_wait<0>();
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
@@ -356,16 +391,53 @@ cudaError_t gemm_tc_init() {
   return g_err;
 }
 
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on it)
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of Q (rows x l, pitch ldq) with 128-byte-swizzled boxes of one
+// panel (128 bytes of K) x 128 rows; false where TMA cannot be used (base not
+// 16-byte aligned, pitch not a multiple of 16 bytes, no driver entry point).
+template <int DT>
+bool make_tmap(CUtensorMap *m, void *Q, int64_t ldq, int64_t rows, int32_t l) {
+  using C = GemmCfg<DT>;
+  memset(m, 0, sizeof *m);
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn || ((uintptr_t)Q & 15) || ((ldq * C::ES) & 15) || rows < 1 || rows > (int64_t)INT32_MAX) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)l, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ldq * C::ES)};
+  const cuuint32_t box[2] = {(cuuint32_t)C::KE, 128u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = fn(m, C::F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Q, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <int DT>
 void launch_gemm(void *Q, int64_t ldq, int64_t rows, int32_t l, const float *B, int64_t ldb, PassGate g, int grid,
                  cudaStream_t s) {
   int32_t *err = const_cast<int32_t *>(g.state);
+  CUtensorMap tmap;
+  const int32_t tma = make_tmap<DT>(&tmap, Q, ldq, rows, l) ? 1 : 0;
   const size_t s3 = gemm_tc_smem<DT>(l, 3);
   if (s3 <= (size_t)kMaxSmem)
-    gemm_tc_kernel<DT, 3><<<grid, kThreads, s3, s>>>(Q, ldq, rows, l, B, ldb, g.state, g.pass, err);
+    gemm_tc_kernel<DT, 3><<<grid, kThreads, s3, s>>>(Q, ldq, rows, l, B, ldb, tmap, tma, g.state, g.pass, err);
   else
-    gemm_tc_kernel<DT, 2><<<grid, kThreads, gemm_tc_smem<DT>(l, 2), s>>>(Q, ldq, rows, l, B, ldb, g.state, g.pass,
-                                                                          err);
+    gemm_tc_kernel<DT, 2><<<grid, kThreads, gemm_tc_smem<DT>(l, 2), s>>>(Q, ldq, rows, l, B, ldb, tmap, tma,
+                                                                          g.state, g.pass, err);
 }
 
 cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, const float *B,

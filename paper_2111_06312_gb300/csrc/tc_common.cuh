@@ -66,6 +66,15 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                : "memory");
 }
 
+// Tiled TMA load of one box of a 2-D tensor map (coordinates in elements,
+// innermost first) into shared memory, completing its bytes on the mbarrier.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int32_t x, int32_t y, uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(mbar))
+      : "memory");
+}
+
 // One arrival on the mbarrier once all of this thread's earlier cp.async copies
 // have landed (the barrier's expected count includes it).
 __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t *mbar) {
