@@ -1,5 +1,8 @@
 // Q <- Q B on tcgen05 with B upper triangular (B = R^-1 of CholeskyQR,
-// Alg. 2: Q_hat = Q (L^-1)^T, L^T = R), in place, Q n x l row-major, l <= 160.
+// Alg. 2: Q_hat = Q (L^-1)^T, L^T = R), in place, Q n x l row-major, l <= 160;
+// and the general product Out[:, n0:n0+w] = Q B[:, n0:n0+w] into another
+// block (the U = Q Vo and V = Qt Uo products that close Alg. 1), in column
+// slices whose B panels fit in shared memory.
 //
 // B stays in shared memory for the whole kernel as K-major panels (128-byte
 // swizzle) of 32 (FP32) or 64 (BF16) rows of K; because B is upper
@@ -70,36 +73,46 @@ struct GemmCfg {
   static constexpr int STAGE = NT * 128 * 128;  // bytes per A stage
 };
 
-// Panel p of B holds K rows [p*KE, p*KE + KE) and output columns n in
-// [p*KE, N1): np(p) = N1 - p*KE rows of 128 bytes, at byte offset
-// bo(p) = 128 * sum_{q<p} np(q).
+// Panel p of B holds K rows [p*KE, p*KE + KE).  Triangular B: output columns
+// n in [p*KE, N1), np(p) = N1 - p*KE rows of 128 bytes at byte offset
+// bo(p) = 128 * sum_{q<p} np(q); general B: all N1 columns in every panel.
 struct Layout {
-  int KE, KP, N1, bbytes;
-  __host__ __device__ int np(int p) const { return N1 - p * KE; }
-  __host__ __device__ int bo(int p) const { return 128 * (p * N1 - KE * p * (p - 1) / 2); }
+  int KE, KP, N1, tri, bbytes;
+  __host__ __device__ int n_first(int p) const { return tri ? p * KE : 0; }
+  __host__ __device__ int np(int p) const { return N1 - n_first(p); }
+  __host__ __device__ int bo(int p) const { return tri ? 128 * (p * N1 - KE * p * (p - 1) / 2) : 128 * p * N1; }
 };
 
+// K = l; w output columns (w = l for the triangular in-place product)
 template <int DT>
-__host__ __device__ Layout make_layout(int l) {
+__host__ __device__ Layout make_layout(int l, int w, int tri) {
   using C = GemmCfg<DT>;
   Layout L{};
   L.KE = C::KE;
   L.KP = (l + C::KE - 1) / C::KE;
-  L.N1 = (l + 15) & ~15;
+  L.N1 = (w + 15) & ~15;
+  L.tri = tri;
   L.bbytes = L.bo(L.KP);
   return L;
 }
+
+// The output block: Out[row][c] for c < w, from B's columns n0 + c.
+struct GemmOut {
+  void *out;
+  int64_t ldo;
+  int32_t n0, w, tri;
+};
 
 // kRaw: raw panels in flight (refilled by the producers alone); 3 where the
 // shared memory allows, else 2.
 template <int DT, int kRaw>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_tc_kernel(void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, const float *__restrict__ B,
-                   int64_t ldb, const __grid_constant__ CUtensorMap tmap, int32_t use_tma,
+    gemm_tc_kernel(const void *__restrict__ Qv, int64_t ldq, int64_t rows, int32_t l, const float *__restrict__ B,
+                   int64_t ldb, const GemmOut o, const __grid_constant__ CUtensorMap tmap, int32_t use_tma,
                    const int32_t *gate_state, int32_t gate_pass, int32_t *err_state) {
   using C = GemmCfg<DT>;
   if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
-  const Layout L = make_layout<DT>(l);
+  const Layout L = make_layout<DT>(l, o.w, o.tri);
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], dfull[2], dfree[2], raw_full[kRaw];
   __shared__ uint32_t tmem_slot;
@@ -114,13 +127,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t G = my_tiles * L.KP;
 
-  // B panels: element (k, n) of B, k in panel p, n >= p*KE, stored K-major
+  // B panels: element (k, n0 + n) of B, k in panel p, n from n_first(p), stored K-major
   for (int p = 0; p < L.KP; ++p) {
     const int k0 = p * C::KE;
     for (int idx = tid; idx < L.np(p) * C::KE; idx += blockDim.x) {
       const int nn = idx / C::KE, kk = idx - nn * C::KE;
-      const int n = k0 + nn, k = k0 + kk;
-      const float x = (k < l && n < l && k <= n) ? B[(size_t)k * ldb + n] : 0.f;
+      const int n = L.n_first(p) + nn, k = k0 + kk;
+      const float x = (k < l && n < o.w && (!o.tri || k <= n)) ? B[(size_t)k * ldb + o.n0 + n] : 0.f;
       const uint32_t off = L.bo(p) + sw128(nn, kk * C::ES);
       if (C::F32) {
         float hi, lo;
@@ -152,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
-  char *Q = reinterpret_cast<char *>(Qv);
+  const char *Q = reinterpret_cast<const char *>(Qv);
 
   if (warp < kProdWarps) {
     // ---------------- producers: stream A panels ----------------
@@ -280,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t id = idesc(fmt, 128, L.np(p));
           const uint32_t ahi = smem_u32(astage + (size_t)s * C::STAGE), alo = ahi + 128 * 128;
           const uint32_t b_hi = smem_u32(bhi + L.bo(p)), b_lo = smem_u32(blo + L.bo(p));
-          const uint32_t dp = dcol + p * C::KE;  // accumulator columns n >= p*KE
+          const uint32_t dp = dcol + L.n_first(p);  // accumulator columns from n_first(p)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t acc = (p > 0 || kk > 0) ? 1u : 0u;
@@ -299,11 +312,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue: TMEM -> Q rows ----------------
+    // ---------------- epilogue: TMEM -> output rows ----------------
     const int sub = warp & 3;  // TMEM lane quarter of this warp
     const int r = sub * 32 + lane;
+    char *Out = reinterpret_cast<char *>(o.out);
     // every row start is 32-byte aligned (the column offsets below are multiples of 32 bytes)
-    const bool v32 = ((uintptr_t)Q & 31) == 0 && ((ldq * C::ES) & 31) == 0;
+    const bool v32 = ((uintptr_t)Out & 31) == 0 && ((o.ldo * C::ES) & 31) == 0;
     for (int64_t lt = 0; lt < my_tiles; ++lt) {
       const int d = (int)(lt & 1);
       if (!mbar_wait_sleep(&dfull[d], (uint32_t)((lt >> 1) & 1), 256)) {
@@ -316,11 +330,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int cb = 0; cb < L.N1; cb += 32) {
         tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (d ? kDBufCol : 0) + cb, v);
         if (row < rows) {
-          char *dst = Q + ((size_t)row * ldq + cb) * C::ES;
+          char *dst = Out + ((size_t)row * o.ldo + cb) * C::ES;
           // 32-byte stores (a whole L2 sector each) where every row starts
           // on a 32-byte boundary, else 16-byte pairs (the row pitch is a
           // multiple of 8 elements); element stores for a ragged tail
-          const int n = min(32, l - cb);
+          const int n = min(32, o.w - cb);
           if (C::F32) {
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
@@ -365,9 +379,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int DT>
-size_t gemm_tc_smem(int32_t l, int raw) {
+size_t gemm_tc_smem(int32_t l, int32_t w, int32_t tri, int raw) {
   using C = GemmCfg<DT>;
-  const Layout L = make_layout<DT>(l);
+  const Layout L = make_layout<DT>(l, w, tri);
   return (size_t)C::NT * L.bbytes + (size_t)kStages * C::STAGE + (size_t)raw * 128 * 128 + 1024;
 }
 
@@ -391,6 +405,8 @@ cudaError_t gemm_tc_init() {
   return g_err;
 }
 
+namespace {
+
 // cuTensorMapEncodeTiled from the driver (no link-time dependency on it)
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -411,7 +427,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // panel (128 bytes of K) x 128 rows; false where TMA cannot be used (base not
 // 16-byte aligned, pitch not a multiple of 16 bytes, no driver entry point).
 template <int DT>
-bool make_tmap(CUtensorMap *m, void *Q, int64_t ldq, int64_t rows, int32_t l) {
+bool make_tmap(CUtensorMap *m, const void *Q, int64_t ldq, int64_t rows, int32_t l) {
   using C = GemmCfg<DT>;
   memset(m, 0, sizeof *m);
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
@@ -420,34 +436,66 @@ bool make_tmap(CUtensorMap *m, void *Q, int64_t ldq, int64_t rows, int32_t l) {
   const cuuint64_t strides[1] = {(cuuint64_t)(ldq * C::ES)};
   const cuuint32_t box[2] = {(cuuint32_t)C::KE, 128u};
   const cuuint32_t estr[2] = {1u, 1u};
-  const CUresult r = fn(m, C::F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Q, dims,
+  const CUresult r = fn(m, C::F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void *>(Q), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
+// One launch per column slice of the output; false when no slice fits.
 template <int DT>
-void launch_gemm(void *Q, int64_t ldq, int64_t rows, int32_t l, const float *B, int64_t ldb, PassGate g, int grid,
-                 cudaStream_t s) {
+bool launch_gemm(const void *Q, int64_t ldq, int64_t rows, int32_t l, const float *B, int64_t ldb, GemmOut o,
+                 PassGate g, cudaStream_t s) {
+  using C = GemmCfg<DT>;
   int32_t *err = const_cast<int32_t *>(g.state);
+  const int64_t ntiles = (rows + 127) / 128;
+  const int grid = (int)std::min<int64_t>(ntiles, kNumSMs);
   CUtensorMap tmap;
   const int32_t tma = make_tmap<DT>(&tmap, Q, ldq, rows, l) ? 1 : 0;
-  const size_t s3 = gemm_tc_smem<DT>(l, 3);
-  if (s3 <= (size_t)kMaxSmem)
-    gemm_tc_kernel<DT, 3><<<grid, kThreads, s3, s>>>(Q, ldq, rows, l, B, ldb, tmap, tma, g.state, g.pass, err);
-  else
-    gemm_tc_kernel<DT, 2><<<grid, kThreads, gemm_tc_smem<DT>(l, 2), s>>>(Q, ldq, rows, l, B, ldb, tmap, tma,
-                                                                          g.state, g.pass, err);
+  // widest slice (a multiple of 16 columns) whose B panels fit beside 2 raw stages
+  int32_t wc = o.w;
+  if (!o.tri)
+    while (wc > 16 && gemm_tc_smem<DT>(l, wc, 0, 2) > (size_t)kMaxSmem) wc = ((wc - 1) & ~15);
+  if (gemm_tc_smem<DT>(l, wc, o.tri, 2) > (size_t)kMaxSmem) return false;
+  for (int32_t c0 = 0; c0 < o.w; c0 += wc) {
+    GemmOut os = o;
+    os.n0 = o.n0 + c0;
+    os.w = std::min(wc, o.w - c0);
+    os.out = reinterpret_cast<char *>(o.out) + (size_t)c0 * C::ES;
+    const size_t s3 = gemm_tc_smem<DT>(l, os.w, os.tri, 3);
+    if (s3 <= (size_t)kMaxSmem)
+      gemm_tc_kernel<DT, 3><<<grid, kThreads, s3, s>>>(Q, ldq, rows, l, B, ldb, os, tmap, tma, g.state, g.pass, err);
+    else
+      gemm_tc_kernel<DT, 2><<<grid, kThreads, gemm_tc_smem<DT>(l, os.w, os.tri, 2), s>>>(
+          Q, ldq, rows, l, B, ldb, os, tmap, tma, g.state, g.pass, err);
+  }
+  return true;
 }
+
+}  // namespace
 
 cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, const float *B,
                                     int64_t ldb, PassGate g, cudaStream_t s) {
   cudaError_t e = gemm_tc_init();
   if (e != cudaSuccess) return e;
-  const int64_t ntiles = (rows + 127) / 128;
-  const int grid = (int)std::min<int64_t>(ntiles, kNumSMs);
-  if (dtype == DT_F32) launch_gemm<DT_F32>(Q, ldq, rows, l, B, ldb, g, grid, s);
-  else launch_gemm<DT_BF16>(Q, ldq, rows, l, B, ldb, g, grid, s);
+  const GemmOut o{Q, ldq, 0, l, 1};
+  const bool ok = dtype == DT_F32 ? launch_gemm<DT_F32>(Q, ldq, rows, l, B, ldb, o, g, s)
+                                  : launch_gemm<DT_BF16>(Q, ldq, rows, l, B, ldb, o, g, s);
+  if (!ok) return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_tc_launch(const float *Q, int64_t ldq, int64_t rows, int32_t l, const float *B, int64_t ldb,
+                           int32_t w, float *out, int64_t ldo, bool *launched, cudaStream_t s) {
+  *launched = false;
+  cudaError_t e = gemm_tc_init();
+  if (e != cudaSuccess) return e;
+  // 16-byte stores and TMA boxes need 16-byte rows; the caller falls back otherwise
+  if (rows == 0 || w == 0 || ((uintptr_t)out & 15) || (ldo & 3) || ((uintptr_t)Q & 15) || (ldq & 3))
+    return cudaSuccess;
+  const GemmOut o{out, ldo, 0, w, 0};
+  *launched = launch_gemm<DT_F32>(Q, ldq, rows, l, B, ldb, o, PassGate{}, s);
   return cudaGetLastError();
 }
 

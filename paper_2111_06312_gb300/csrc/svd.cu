@@ -138,10 +138,16 @@ isvd_status svd_enqueue(isvd_operator *op, const SvdPlan &P, const SvdBufs &b, c
   // B = R^T Qt^T;  R = Uo S Vo^T  =>  B = Vo S (Qt Uo)^T:  U = Q Vo, V = Qt Uo
   ISVD_CUDA_TRY(small_svd_launch(b.Racc, P.l, b.Uo, b.So, b.Vo, b.jwork, /*Uk=*/b.Rk, /*Vk=*/b.Lk, /*Sk=*/P.S, P.k,
                                  info, P.iters, s));
-  ISVD_CUDA_TRY(gemm_small_launch(b.qr32, P.ld, DT_F32, rows, P.l, b.Lk, P.k, P.k, false, P.U, P.ldu, DT_F32,
-                                  PassGate{}, s));
-  ISVD_CUDA_TRY(gemm_small_launch(b.qc32, P.ld, DT_F32, cols, P.l, b.Rk, P.k, P.k, false, P.V, P.ldv, DT_F32,
-                                  PassGate{}, s));
+  // U = Q Vo_k, V = Qt Uo_k: tensor cores where the layout allows, else CUDA cores
+  auto product = [&](const float *Qb, int64_t n, const float *Bk, float *Out, int64_t ldo) -> cudaError_t {
+    bool launched = false;
+    cudaError_t e = gemm_tc_launch(Qb, P.ld, n, P.l, Bk, P.k, P.k, Out, ldo, &launched, s);
+    if (e == cudaSuccess && !launched)
+      e = gemm_small_launch(Qb, P.ld, DT_F32, n, P.l, Bk, P.k, P.k, false, Out, ldo, DT_F32, PassGate{}, s);
+    return e;
+  };
+  ISVD_CUDA_TRY(product(b.qr32, rows, b.Lk, P.U, P.ldu));
+  ISVD_CUDA_TRY(product(b.qc32, cols, b.Rk, P.V, P.ldv));
   return ISVD_OK;
 }
 
