@@ -67,11 +67,16 @@ __global__ void __launch_bounds__(kCholThreads, 1) chol_cluster_kernel(const dou
   __shared__ int s_fail;
   __shared__ double s_trace;
 
-  if (tid == 0) {
+  if (warp == 0) {
+    // trace of W: lanes over the diagonal, then a fixed-order reduction
     double t = 0.0;
-    for (int i = 0; i < l; ++i) t += W[(size_t)i * l + i];
-    s_trace = t;
-    if (rank == 0 && state[2]) atomicExch(&info->status, (int)ISVD_ERR_TIMEOUT);  // a Gram wait gave up
+    for (int i = lane; i < l; i += 32) t += W[(size_t)i * l + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+      s_trace = t;
+      if (rank == 0 && state[2]) atomicExch(&info->status, (int)ISVD_ERR_TIMEOUT);  // a Gram wait gave up
+    }
   }
   __syncthreads();
 

@@ -29,15 +29,6 @@ constexpr int kJacThreads = 256;
 constexpr int kJacMaxCluster = 16;
 constexpr int kJacMaxSmem = 200 * 1024;
 
-__device__ __forceinline__ void warp_sum3(double &a, double &b, double &c) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-  }
-}
-
 // One warp rotates columns gp, gq (length l, squared norms *np, *nq kept by the
 // caller) if they are not yet orthogonal.  Only g_p . g_q is summed; the norms
 // follow the rotation in closed form (||g_p'||^2 = ||g_p||^2 - t g_p.g_q,
@@ -218,20 +209,23 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
     }
   __threadfence();
   cluster.sync();
-  if (c == 0 && tid == 0) {
-    // descending order of the first l columns (the rest are zero padding); stable
-    for (int p = 0; p < l; ++p) perm_g[p] = p;
-    for (int a = 1; a < l; ++a) {
-      const int x = perm_g[a];
-      const double nx = nrm_g[x];
-      int b = a - 1;
-      while (b >= 0 && nrm_g[perm_g[b]] < nx) {
-        perm_g[b + 1] = perm_g[b];
-        --b;
-      }
-      perm_g[b + 1] = x;
+  if (c == 0) {
+    // descending order of the first l columns (the rest are zero padding),
+    // stable: rank of column p = #columns with a larger norm, or an equal norm
+    // and a smaller index (a NaN norm ranks below every number)
+    __shared__ double snrm[ISVD_MAX_BLOCK];
+    for (int p = tid; p < l; p += blockDim.x) {
+      const double x = nrm_g[p];
+      snrm[p] = x == x ? x : -1.0;
     }
-    if (info) info->iters_done = iters;
+    __syncthreads();
+    for (int p = tid; p < l; p += blockDim.x) {
+      const double x = snrm[p];
+      int rank = 0;
+      for (int q = 0; q < l; ++q) rank += (snrm[q] > x || (snrm[q] == x && q < p)) ? 1 : 0;
+      perm_g[rank] = p;
+    }
+    if (tid == 0 && info) info->iters_done = iters;
   }
   (void)l3;
   __threadfence();
