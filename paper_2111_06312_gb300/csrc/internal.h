@@ -91,6 +91,7 @@ struct SpmmArgs {
 // sums combined in chunk order (deterministic).
 struct HeavyPlan {
   int32_t n_rows = 0;       // heavy rows
+  int32_t n_big = 0;        // the first n_big rows have more than kBigHubChunks chunks
   int32_t n_chunks = 0;
   int2 *chunks = nullptr;   // (row, first nnz) per chunk; chunk end = next chunk or row end
   int32_t *chunk_end = nullptr;
@@ -98,6 +99,10 @@ struct HeavyPlan {
   int32_t threshold = 128;
   int32_t chunk = 128;
 };
+
+// Heavy rows with more chunks than this are summed by a whole CTA (eight
+// warps over the chunks) instead of one warp.
+constexpr int32_t kBigHubChunks = 32;
 
 // Launch the SpMM described by `a` (dtype of in/axpy/out), splitting heavy
 // rows per `hp` using `partial` (hp.n_chunks x pw FP32, pw >= slab columns).

@@ -218,7 +218,7 @@ void free_heavy(isvd_operator *op, HeavyPlan *hp, cudaStream_t s) {
   hp->chunks = nullptr;
   hp->chunk_end = nullptr;
   hp->rows = nullptr;
-  hp->n_rows = hp->n_chunks = 0;
+  hp->n_rows = hp->n_chunks = hp->n_big = 0;
 }
 
 void free_chunks(isvd_operator *op, ChunkPlan *cp, cudaStream_t s) {
@@ -252,7 +252,12 @@ isvd_status build_heavy(isvd_operator *op, const int32_t *rowptr_dev, int64_t ro
     }
     hrows.push_back(make_int4((int)i, first, (int)chunks.size() - first, 0));
   }
+  // rows with many chunks first (each then gets a whole CTA), row order kept within each part
+  std::stable_partition(hrows.begin(), hrows.end(), [](const int4 &h) { return h.z > kBigHubChunks; });
+  int32_t n_big = 0;
+  for (const int4 &h : hrows) n_big += h.z > kBigHubChunks ? 1 : 0;
   free_heavy(op, hp, s);
+  hp->n_big = n_big;
   hp->n_rows = (int32_t)hrows.size();
   hp->n_chunks = (int32_t)chunks.size();
   if (hp->n_chunks == 0) return ISVD_OK;

@@ -407,6 +407,81 @@ __global__ void __launch_bounds__(256) spmm_finish_kernel(const __grid_constant_
   }
 }
 
+// Rows with many chunks (the first n_big of the plan): one CTA per row and
+// slab; warp w sums chunks w, w + 8, ... (in order), the eight warp sums are
+// added in warp order, and warp 0 applies the epilogue.  Lanes past the first
+// row group of a warp (narrow slabs) stay idle.
+template <int DT, bool HINT, int CPL>
+__global__ void __launch_bounds__(256) spmm_finish_big_kernel(const __grid_constant__ SpmmArgs a,
+                                                              const int4 *__restrict__ hrows,
+                                                              const float *__restrict__ partial, int64_t pw) {
+  constexpr int VN = Vec<DT>::N;
+  constexpr int NW = 8;
+  __shared__ float4 red[NW][32][CPL * VN / 4];
+  const SpmmSlab &sl = a.slab[blockIdx.y];
+  const Lane L = make_lane<DT>(sl);
+  const Policies pol = make_policies<HINT>();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int4 hr = hrows[blockIdx.x];
+  float acc[CPL * VN];
+#pragma unroll
+  for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
+  if (L.sub == 0) {
+    constexpr int NV = VN / 4;  // float4 per lane and chunk
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      if (!(q == 0 ? L.active : L.active2)) break;
+      const float *p0 = partial + (size_t)hr.y * pw + sl.col0 + (q == 0 ? L.col : L.col2);
+      int c = warp;
+      for (; c + 3 * NW < hr.z; c += 4 * NW) {
+        float4 v[4][NV];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int h = 0; h < NV; ++h)
+            v[u][h] = __ldcg(reinterpret_cast<const float4 *>(p0 + (size_t)(c + u * NW) * pw) + h);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int h = 0; h < NV; ++h) {
+            acc[q * VN + 4 * h + 0] += v[u][h].x;
+            acc[q * VN + 4 * h + 1] += v[u][h].y;
+            acc[q * VN + 4 * h + 2] += v[u][h].z;
+            acc[q * VN + 4 * h + 3] += v[u][h].w;
+          }
+      }
+      for (; c < hr.z; c += NW) {
+        const float *pc = p0 + (size_t)c * pw;
+#pragma unroll
+        for (int k = 0; k < VN; ++k) acc[q * VN + k] += pc[k];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPL * VN / 4; ++k)
+    red[warp][lane][k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+  __syncthreads();
+  if (warp == 0 && L.sub == 0) {
+#pragma unroll
+    for (int k = 0; k < CPL * VN / 4; ++k) {
+      float4 t = red[0][lane][k];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) {
+        const float4 u = red[w][lane][k];
+        t.x += u.x;
+        t.y += u.y;
+        t.z += u.z;
+        t.w += u.w;
+      }
+      acc[4 * k] = t.x;
+      acc[4 * k + 1] = t.y;
+      acc[4 * k + 2] = t.z;
+      acc[4 * k + 3] = t.w;
+    }
+    epilogue<DT, HINT, CPL>(a, sl, L, hr.x, pol, acc);
+  }
+}
+
 int pow2_ceil(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -452,11 +527,14 @@ cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, i
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side.join, 0);
     if (e != cudaSuccess) return e;
   }
-  if (hp.n_chunks > 0) {
-    int64_t fx = ceil_div(hp.n_rows, rows_per_block);
+  if (hp.n_big > 0)
+    spmm_finish_big_kernel<DT, HINT, CPL><<<dim3((unsigned)hp.n_big, (unsigned)a.nslabs), threads, 0, s>>>(
+        a, hp.rows, partial, pw);
+  if (hp.n_rows > hp.n_big) {
+    int64_t fx = ceil_div(hp.n_rows - hp.n_big, rows_per_block);
     if (fx > cap) fx = cap;
     spmm_finish_kernel<DT, HINT, CPL><<<dim3((unsigned)fx, (unsigned)a.nslabs), threads, 0, s>>>(
-        a, hp.rows, hp.n_rows, partial, pw);
+        a, hp.rows + hp.n_big, hp.n_rows - hp.n_big, partial, pw);
   }
   return cudaGetLastError();
 }
