@@ -19,9 +19,16 @@
 // combined in chunk order, so results are deterministic.
 #include "internal.h"
 
-// blocks per SM of the FP32 row kernel at high occupancy (a build-time knob)
+// blocks per SM of the FP32 row kernel at high occupancy, and the nonzeros
+// in flight and blocks per SM of the wide (two chunks per lane) form: build-time knobs
 #ifndef ISVD_ROWS_HIGH_OCC_F32
 #define ISVD_ROWS_HIGH_OCC_F32 6
+#endif
+#ifndef ISVD_WIDE_UNROLL
+#define ISVD_WIDE_UNROLL 3
+#endif
+#ifndef ISVD_WIDE_MINB
+#define ISVD_WIDE_MINB 4
 #endif
 
 namespace isvd {
@@ -170,7 +177,7 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
                                              int e1, const Policies &pol, float *acc) {
   using V = Vec<DT>;
   constexpr int VN = V::N;
-  constexpr int U = CPL == 1 ? 4 : 2;  // nonzeros per step (the same registers in flight)
+  constexpr int U = CPL == 1 ? 4 : ISVD_WIDE_UNROLL;  // nonzeros per step
   const char *inb = reinterpret_cast<const char *>(sl.in) + (size_t)L.col * V::BYTES;
   const size_t off2 = (size_t)(L.col2 - L.col) * V::BYTES;
   const size_t ldb = (size_t)sl.ldi * V::BYTES;
@@ -517,7 +524,7 @@ cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, i
   }
   // high occupancy: 6 blocks of 256 threads per SM (40 registers) for FP32;
   // BF16 rows hold twice the accumulators and take 5 (48 registers, no spills)
-  constexpr int kHighOcc = DT == DT_F32 ? ISVD_ROWS_HIGH_OCC_F32 : 5;
+  constexpr int kHighOcc = CPL == 2 ? ISVD_WIDE_MINB : DT == DT_F32 ? ISVD_ROWS_HIGH_OCC_F32 : 5;
   if (a.rows_occupancy >= 3)
     spmm_rows_kernel<DT, HINT, kHighOcc, CPL><<<grid, threads, 0, s>>>(a);
   else

@@ -111,7 +111,7 @@ def main():
         g = synth.cached(a.workload)
         op = isvd.graph_operator(g, coeffs=[1.0], check_symmetry=False)
         if a.what == "spmm":
-            tun = set_tuning(op, slab32=a.slab or None, slab16=a.slab or None, heavy=a.heavy or None,
+            tun = set_tuning(op, slab32=min(a.slab, 256) or None, slab16=a.slab or None, heavy=a.heavy or None,
                              chunk=a.chunk or None, row_kernel=True if a.row_kernel else None,
                              chunk_nnz=a.chunk_nnz or None)
             if a.kernel:
