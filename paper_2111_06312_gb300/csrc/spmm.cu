@@ -248,6 +248,70 @@ __device__ __forceinline__ void gather_range(const SpmmArgs &a, const SpmmSlab &
   }
 }
 
+// The same sum for narrow slabs, whose warps hold several row groups (G < 32):
+// the groups step through their rows together, to the longest row of the
+// warp (maxlen, warp-uniform), so the warp issues one instruction stream
+// instead of one per group; entries past a row's length (len) load nothing
+// and weigh zero.  All 32 lanes must call it.
+template <int DT, bool HINT, int CPL>
+__device__ __forceinline__ void gather_range_grouped(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int e0,
+                                                     int len, int maxlen, const Policies &pol, float *acc) {
+  using V = Vec<DT>;
+  constexpr int VN = V::N;
+  constexpr int U = CPL == 1 ? 4 : ISVD_WIDE_UNROLL;
+  const char *inb = reinterpret_cast<const char *>(sl.in) + (size_t)L.col * V::BYTES;
+  const size_t off2 = (size_t)(L.col2 - L.col) * V::BYTES;
+  const size_t ldb = (size_t)sl.ldi * V::BYTES;
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  for (int off = 0; off < maxlen; off += L.G) {
+    const int me = off + L.gl;
+    int j = 0;
+    float w = 0.f;
+    if (me < len) {
+      const int e = e0 + me;
+      if (HINT && a.tagged) {
+        const int32_t t = ld_idx<HINT>(a.tagged + e, pol.stream);
+        j = t & ((1 << 26) - 1);
+        if ((t >> 26) < sl.hot_bucket) j |= (int)0x80000000;
+      } else {
+        j = ld_idx<HINT>(a.colidx + e, pol.stream);
+      }
+      w = a.values ? __ldg(a.values + e) : 1.f;
+      if (a.colw) w *= __ldg(a.colw + (j & 0x7fffffff));
+    }
+    const int cntw = min(L.G, maxlen - off);  // warp-uniform
+    for (int t = 0; t < cntw; t += U) {
+      int jj[U];
+      float ww[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        jj[u] = __shfl_sync(0xffffffffu, j, t + u, L.G);
+        ww[u] = __shfl_sync(0xffffffffu, w, t + u, L.G);
+      }
+      if (L.active) {
+        uint4 raw[U][CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const bool ok = t + u < cntw && off + t + u < len;
+          const char *src = inb + (size_t)(jj[u] & 0x7fffffff) * ldb;
+          const uint64_t pl = jj[u] < 0 ? pol.stream : pol.keep;
+          raw[u][0] = ok ? ld16<HINT>(src, pl) : zero;
+          if (CPL == 2) raw[u][CPL - 1] = (ok && L.active2) ? ld16<HINT>(src + off2, pl) : zero;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) {
+            float v[VN];
+            V::unpack(raw[u][c], v);
+#pragma unroll
+            for (int k = 0; k < VN; ++k) acc[c * VN + k] = fmaf(ww[u], v[k], acc[c * VN + k]);
+          }
+      }
+    }
+  }
+}
+
 template <int DT, bool HINT, int CPL>
 __device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int64_t r,
                                          const Policies &pol, float *acc_all) {
@@ -309,7 +373,10 @@ __device__ __forceinline__ void prefetch_next_row(const SpmmArgs &a, const SpmmS
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-template <int DT, bool HINT, int MINB, int CPL>
+// GROUPED: some slab of the launch has several row groups per warp (the
+// grouped gather is compiled in only then, so that one-group launches keep
+// their registers).
+template <int DT, bool HINT, int MINB, int CPL, bool GROUPED>
 __global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_constant__ SpmmArgs a) {
   constexpr int VN = Vec<DT>::N;
   const SpmmSlab &sl = a.slab[blockIdx.y];
@@ -320,19 +387,36 @@ __global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_const
   const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t base = warp * rpw; base < a.rows; base += nwarp * rpw) {
     const int64_t r = base + L.sub;
-    if (r >= a.rows) continue;  // uniform within the group
-    const int e0 = ld_idx<HINT>(a.rowptr + r, pol.stream), e1 = ld_idx<HINT>(a.rowptr + r + 1, pol.stream);
-    if (a.prefetch) prefetch_next_row<DT>(a, sl, L, r + nwarp * rpw);
-    if (e1 - e0 > a.heavy_threshold) continue;
-    float acc[CPL * VN];
+    if (!GROUPED || L.G == 32) {  // one row group per warp
+      if (r >= a.rows) continue;
+      const int e0 = ld_idx<HINT>(a.rowptr + r, pol.stream), e1 = ld_idx<HINT>(a.rowptr + r + 1, pol.stream);
+      if (a.prefetch) prefetch_next_row<DT>(a, sl, L, r + nwarp * rpw);
+      if (e1 - e0 > a.heavy_threshold) continue;  // heavy rows: chunks + finish
+      float acc[CPL * VN];
 #pragma unroll
-    for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
-    gather_range<DT, HINT, CPL>(a, sl, L, e0, e1, pol, acc);
-    epilogue<DT, HINT, CPL>(a, sl, L, r, pol, acc);
+      for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
+      gather_range<DT, HINT, CPL>(a, sl, L, e0, e1, pol, acc);
+      epilogue<DT, HINT, CPL>(a, sl, L, r, pol, acc);
+    } else {
+      const bool in_range = r < a.rows;  // uniform within the group
+      int e0 = 0, e1 = 0;
+      if (in_range) {
+        e0 = ld_idx<HINT>(a.rowptr + r, pol.stream);
+        e1 = ld_idx<HINT>(a.rowptr + r + 1, pol.stream);
+        if (a.prefetch) prefetch_next_row<DT>(a, sl, L, r + nwarp * rpw);
+      }
+      const bool mine = in_range && e1 - e0 <= a.heavy_threshold;
+      const int len = mine ? e1 - e0 : 0;
+      float acc[CPL * VN];
+#pragma unroll
+      for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
+      gather_range_grouped<DT, HINT, CPL>(a, sl, L, e0, len, __reduce_max_sync(0xffffffffu, len), pol, acc);
+      if (mine) epilogue<DT, HINT, CPL>(a, sl, L, r, pol, acc);
+    }
   }
 }
 
-template <int DT, bool HINT, int CPL>
+template <int DT, bool HINT, int CPL, bool GROUPED>
 __global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant__ SpmmArgs a,
                                                           const int2 *__restrict__ chunks,
                                                           const int32_t *__restrict__ chunk_end, int32_t n,
@@ -346,12 +430,18 @@ __global__ void __launch_bounds__(256) spmm_chunks_kernel(const __grid_constant_
   const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t base = warp * rpw; base < n; base += nwarp * rpw) {
     const int64_t c = base + L.sub;
-    if (c >= n) continue;
-    const int e0 = chunks[c].y, e1 = chunk_end[c];
     float acc[CPL * VN];
 #pragma unroll
     for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
-    gather_range<DT, HINT, CPL>(a, sl, L, e0, e1, pol, acc);
+    if (!GROUPED || L.G == 32) {  // one chunk group per warp
+      if (c >= n) continue;
+      gather_range<DT, HINT, CPL>(a, sl, L, chunks[c].y, chunk_end[c], pol, acc);
+    } else {
+      const bool in_range = c < n;  // uniform within the group
+      const int e0 = in_range ? chunks[c].y : 0, len = in_range ? chunk_end[c] - e0 : 0;
+      gather_range_grouped<DT, HINT, CPL>(a, sl, L, e0, len, __reduce_max_sync(0xffffffffu, len), pol, acc);
+      if (!in_range) continue;
+    }
 #pragma unroll
     for (int h = 0; h < CPL; ++h) {
       if (!(h == 0 ? L.active : L.active2)) break;
@@ -501,6 +591,7 @@ cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, i
   const int threads = 256;
   int gmin = 32;
   for (int i = 0; i < a.nslabs; ++i) gmin = gmin < a.slab[i].group ? gmin : a.slab[i].group;
+  const bool grouped = gmin < 32;
   const int64_t rows_per_block = (threads / 32) * (32 / gmin);
   int64_t bx = ceil_div(a.rows, rows_per_block);
   const int64_t cap = (int64_t)kNumSMs * 16;
@@ -519,16 +610,24 @@ cudaError_t launch_cpl(const SpmmArgs &a, const HeavyPlan &hp, float *partial, i
   if (hp.n_chunks > 0) {
     int64_t cx = ceil_div(hp.n_chunks, rows_per_block);
     if (cx > cap) cx = cap;
-    spmm_chunks_kernel<DT, HINT, CPL><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, hs>>>(
-        a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
+    if (grouped)
+      spmm_chunks_kernel<DT, HINT, CPL, true><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, hs>>>(
+          a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
+    else
+      spmm_chunks_kernel<DT, HINT, CPL, false><<<dim3((unsigned)cx, (unsigned)a.nslabs), threads, 0, hs>>>(
+          a, hp.chunks, hp.chunk_end, hp.n_chunks, partial, pw);
   }
   // high occupancy: 6 blocks of 256 threads per SM (40 registers) for FP32;
   // BF16 rows hold twice the accumulators and take 5 (48 registers, no spills)
   constexpr int kHighOcc = CPL == 2 ? ISVD_WIDE_MINB : DT == DT_F32 ? ISVD_ROWS_HIGH_OCC_F32 : 5;
-  if (a.rows_occupancy >= 3)
-    spmm_rows_kernel<DT, HINT, kHighOcc, CPL><<<grid, threads, 0, s>>>(a);
+  if (a.rows_occupancy >= 3 && grouped)
+    spmm_rows_kernel<DT, HINT, kHighOcc, CPL, true><<<grid, threads, 0, s>>>(a);
+  else if (a.rows_occupancy >= 3)
+    spmm_rows_kernel<DT, HINT, kHighOcc, CPL, false><<<grid, threads, 0, s>>>(a);
+  else if (grouped)
+    spmm_rows_kernel<DT, HINT, 1, CPL, true><<<grid, threads, 0, s>>>(a);
   else
-    spmm_rows_kernel<DT, HINT, 1, CPL><<<grid, threads, 0, s>>>(a);
+    spmm_rows_kernel<DT, HINT, 1, CPL, false><<<grid, threads, 0, s>>>(a);
   if (fork) {
     cudaError_t e = cudaEventRecord(side.join, side.stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side.join, 0);
