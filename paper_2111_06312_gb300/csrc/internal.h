@@ -83,6 +83,7 @@ struct SpmmArgs {
   const int32_t *tagged;    // nullable: colidx with degree buckets (RingTags), for the hints
   int32_t rows_occupancy;   // row kernel: 3 = compiled for 6 resident CTAs per SM (40 registers), else default
   int32_t prefetch;         // row kernel: L2 prefetch of the next row's first neighbour rows
+  const int32_t *row_order; // nullable: rows by degree, largest first (narrow slabs visit rows in this order)
   int32_t nslabs;
   SpmmSlab slab[kMaxSlabs];
 };
@@ -146,6 +147,7 @@ constexpr size_t kRingSmemBudget = 200 * 1024;
 constexpr int64_t kRingL2Budget = 64ll << 20;
 struct RingTags {
   const int32_t *tagged = nullptr;
+  const int32_t *row_order = nullptr;  // rows of A by degree, largest first (ties in row order)
   int64_t hist[32] = {};
   int64_t l2_budget = 0;
 };

@@ -304,6 +304,25 @@ isvd_status build_tags(isvd_operator *op, cudaStream_t s) {
   }
   op->tags_A.tagged = t;
   op->tags_A.l2_budget = kRingL2Budget;
+  // rows by degree, largest first: the row groups of one warp (narrow slabs)
+  // then get rows of about the same length
+  int32_t maxd = 0;
+  for (int64_t i = 0; i < op->n; ++i) maxd = std::max(maxd, rp[i + 1] - rp[i]);
+  std::vector<int64_t> pos((size_t)maxd + 1, 0);
+  for (int64_t i = 0; i < op->n; ++i) pos[rp[i + 1] - rp[i]] += 1;
+  int64_t acc = 0;
+  for (int64_t d = maxd; d >= 0; --d) {
+    const int64_t c = pos[d];
+    pos[d] = acc;
+    acc += c;
+  }
+  std::vector<int32_t> order((size_t)op->n);
+  for (int64_t i = 0; i < op->n; ++i) order[pos[rp[i + 1] - rp[i]]++] = (int32_t)i;
+  int32_t *o = (int32_t *)owned_alloc(op, sizeof(int32_t) * op->n, s);
+  if (!o) return fail(ISVD_ERR_WORKSPACE, "row order allocation failed");
+  ISVD_CUDA_TRY(cudaMemcpyAsync(o, order.data(), sizeof(int32_t) * op->n, cudaMemcpyHostToDevice, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  op->tags_A.row_order = o;
   return ISVD_OK;
 }
 
@@ -638,6 +657,7 @@ int slabs_needed(int dtype, int32_t b, int32_t scols) {
 }
 
 cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, const ChunkPlan &cp, int64_t pw) {
+  if (a.colidx == c.op->desc.A.colidx) a.row_order = c.op->tags_A.row_order;
   if (c.op->spmm_algo == 2) {
     static const RingTags none;
     const RingTags &tags = a.colidx == c.op->desc.A.colidx ? c.op->tags_A : none;

@@ -398,12 +398,15 @@ __global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_const
       gather_range<DT, HINT, CPL>(a, sl, L, e0, e1, pol, acc);
       epilogue<DT, HINT, CPL>(a, sl, L, r, pol, acc);
     } else {
+      // rows in degree order when there is one, so that a warp's groups have
+      // rows of about the same length
       const bool in_range = r < a.rows;  // uniform within the group
+      const int64_t rr = in_range && a.row_order ? (int64_t)__ldg(a.row_order + r) : r;
       int e0 = 0, e1 = 0;
       if (in_range) {
-        e0 = ld_idx<HINT>(a.rowptr + r, pol.stream);
-        e1 = ld_idx<HINT>(a.rowptr + r + 1, pol.stream);
-        if (a.prefetch) prefetch_next_row<DT>(a, sl, L, r + nwarp * rpw);
+        e0 = ld_idx<HINT>(a.rowptr + rr, pol.stream);
+        e1 = ld_idx<HINT>(a.rowptr + rr + 1, pol.stream);
+        if (a.prefetch && !a.row_order) prefetch_next_row<DT>(a, sl, L, r + nwarp * rpw);
       }
       const bool mine = in_range && e1 - e0 <= a.heavy_threshold;
       const int len = mine ? e1 - e0 : 0;
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(256, MINB) spmm_rows_kernel(const __grid_const
 #pragma unroll
       for (int k = 0; k < CPL * VN; ++k) acc[k] = 0.f;
       gather_range_grouped<DT, HINT, CPL>(a, sl, L, e0, len, __reduce_max_sync(0xffffffffu, len), pol, acc);
-      if (mine) epilogue<DT, HINT, CPL>(a, sl, L, r, pol, acc);
+      if (mine) epilogue<DT, HINT, CPL>(a, sl, L, rr, pol, acc);
     }
   }
 }
