@@ -252,8 +252,10 @@ isvd_status build_heavy(isvd_operator *op, const int32_t *rowptr_dev, int64_t ro
     }
     hrows.push_back(make_int4((int)i, first, (int)chunks.size() - first, 0));
   }
-  // rows with many chunks first (each then gets a whole CTA), row order kept within each part
-  std::stable_partition(hrows.begin(), hrows.end(), [](const int4 &h) { return h.z > kBigHubChunks; });
+  // rows by chunk count, most first (ties in row order): the rows with more than
+  // kBigHubChunks chunks form a prefix (a whole CTA each), and the row groups of a
+  // warp in the finish of the rest get about the same number of chunks
+  std::stable_sort(hrows.begin(), hrows.end(), [](const int4 &x, const int4 &y) { return x.z > y.z; });
   int32_t n_big = 0;
   for (const int4 &h : hrows) n_big += h.z > kBigHubChunks ? 1 : 0;
   free_heavy(op, hp, s);
