@@ -22,6 +22,11 @@
 
 namespace cg = cooperative_groups;
 
+// preferred cluster size of the Cholesky (16 or 8; 8 when 16 cannot be resident)
+#ifndef ISVD_CHOL_CLUSTER
+#define ISVD_CHOL_CLUSTER 16
+#endif
+
 namespace isvd {
 namespace {
 
@@ -284,7 +289,7 @@ int chol_cluster_size() {
     cudaError_t e = cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) cudaGetLastError();
     g_cluster = 1;
-    for (int cl : {16, 8}) {
+    for (int cl : {ISVD_CHOL_CLUSTER, 8}) {
       const size_t smem = chol_cluster_smem(ISVD_MAX_BLOCK, cl);
       if (smem > 227 * 1024) continue;
       e = cudaFuncSetAttribute(chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
