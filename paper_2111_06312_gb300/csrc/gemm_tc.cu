@@ -114,7 +114,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (gate_state && gate_pass > 2 && gate_state[0] + 2 < gate_pass) return;
   const Layout L = make_layout<DT>(l, o.w, o.tri);
   extern __shared__ __align__(1024) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], dfull[2], dfree[2], raw_full[kRaw];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], dfull[2], dfree[2], raw_full[kRaw], raw_empty[kRaw];
+  // BF16 panels need no transform: with TMA (zero-filled padding) the MMA reads
+  // them straight from the raw stage, which it releases itself
+  const bool direct = !C::F32 && use_tma;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   unsigned char *sm = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
@@ -154,7 +157,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&dfull[d], 1);
       mbar_init(&dfree[d], 128);
     }
-    for (int r = 0; r < kRaw; ++r) mbar_init(&raw_full[r], 1);  // TMA: one expect_tx arrive + the box bytes
+    for (int r = 0; r < kRaw; ++r) {
+      mbar_init(&raw_full[r], 1);  // TMA: one expect_tx arrive + the box bytes
+      mbar_init(&raw_empty[r], 1);  // direct form: the MMA's commit
+    }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -243,6 +249,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     };
+    if (direct) {
+      // one thread streams the panels into the raw ring as the MMA frees it
+      if (tid == 0) {
+        int64_t g = 0;
+        for (; g < G; ++g) {
+          if (g >= kRaw && !mbar_wait(&raw_empty[g % kRaw], (uint32_t)(((g / kRaw) - 1) & 1))) {
+            abort_flag = 1;
+            if (err_state) atomicExch(&err_state[2], 1);
+            break;
+          }
+          issue(g);
+        }
+        // after an abort, let the boxes already requested land before the CTA exits
+        for (int64_t j = std::max<int64_t>(0, g - kRaw); j < g; ++j)
+          mbar_wait(&raw_full[j % kRaw], (uint32_t)((j / kRaw) & 1));
+      }
+    } else {
     for (int64_t g = 0; g < kRaw - 1; ++g) issue(g);
     int64_t g = 0;
     for (; g < G; ++g) {
@@ -268,6 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t j = g; j < std::min<int64_t>(G, g + kRaw); ++j)
         mbar_wait(&raw_full[j % kRaw], (uint32_t)((j / kRaw) & 1));
     cp_async_wait<0>();
+    }
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
@@ -284,14 +308,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int p = 0; p < L.KP; ++p) {
           const int64_t g = lt * L.KP + p;
           const int s = (int)(g % kStages);
-          if (!mbar_wait(&full[s], (uint32_t)((g / kStages) & 1))) {
+          const bool ok = direct ? mbar_wait(&raw_full[g % kRaw], (uint32_t)((g / kRaw) & 1))
+                                 : mbar_wait(&full[s], (uint32_t)((g / kStages) & 1));
+          if (!ok) {
             if (err_state) atomicExch(&err_state[2], 1);
             abort_flag = 1;
             break;
           }
           fence_after();
           const uint32_t id = idesc(fmt, 128, L.np(p));
-          const uint32_t ahi = smem_u32(astage + (size_t)s * C::STAGE), alo = ahi + 128 * 128;
+          const uint32_t ahi = direct ? smem_u32(rawring + (size_t)(g % kRaw) * (128 * 128))
+                                      : smem_u32(astage + (size_t)s * C::STAGE);
+          const uint32_t alo = ahi + 128 * 128;
           const uint32_t b_hi = smem_u32(bhi + L.bo(p)), b_lo = smem_u32(blo + L.bo(p));
           const uint32_t dp = dcol + L.n_first(p);  // accumulator columns from n_first(p)
 #pragma unroll
@@ -306,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_bf16(dp, da, db, id, acc);
             }
           }
-          commit(&empty[s]);
+          commit(direct ? &raw_empty[g % kRaw] : &empty[s]);
         }
         commit(&dfull[d]);
       }
