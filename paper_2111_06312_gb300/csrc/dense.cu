@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(256) project_partial_kernel(const T *G, int64_
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc[t][k] = 0.f;
     if (inA) {
+      // unrolled: the loads of four rows are in flight together (the sums keep their order)
+#pragma unroll 4
       for (int64_t i = p * 8 + y; i < rows; i += stride) {
         float v[8];
         load4<T>(G + i * ldg + colA, v);
