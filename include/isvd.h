@@ -272,7 +272,9 @@ ISVD_API isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t 
  * library kernels).  slab_cols_*: columns of the dense block processed per
  * pass over the CSR (the gathered slab of the block should stay L2-resident);
  * heavy_threshold: rows with more nonzeros are split into chunks of
- * heavy_chunk nonzeros whose partial sums are combined in order. */
+ * heavy_chunk nonzeros whose partial sums are combined in order.  Slabs
+ * narrower than 32 lanes hold several rows per warp; their rows of A are
+ * visited in degree order (largest first, fixed at operator construction). */
 typedef struct {
   int32_t slab_cols_f32;   /* 4..256, multiple of 4 (above 128: two 16-byte chunks per lane) */
   int32_t slab_cols_bf16;  /* 8..512, multiple of 8 (above 256: two chunks per lane) */
@@ -292,7 +294,7 @@ enum {
   ISVD_TUNE_ROW_KERNEL = 2,
   ISVD_TUNE_RING_KERNEL = 4,
   ISVD_TUNE_HOT_TAGS = 8,    /* with CACHE_HINTS: keep priority only for hub columns (by degree) */
-  ISVD_TUNE_ROWS_OCC3 = 16,  /* row kernel compiled for high occupancy (6 CTAs of 256 threads per SM) */
+  ISVD_TUNE_ROWS_OCC3 = 16,  /* row kernel compiled for high occupancy (FP32: 6 CTAs of 256 threads per SM, BF16: 5) */
   ISVD_TUNE_PREFETCH = 32    /* row kernel: L2 prefetch of the next row's first neighbour rows */
 };
 
