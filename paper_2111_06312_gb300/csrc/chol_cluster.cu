@@ -6,7 +6,8 @@
 // GB300 runs FP64 at about 2 FMA per clock per SM, so the ~l^3/3 FMA of the
 // factorisation and the ~l^3/6 of the inverse take about a millisecond on one
 // SM; here CL CTAs (8 or 16) each own the columns c = rank (mod CL):
-//   - factorisation: right-looking, in panels of kNB rows.  Every CTA reads
+//   - factorisation: right-looking, in panels of kNB rows (8: measured
+//     faster than 16 and 32 at l = 144).  Every CTA reads
 //     the kNB x kNB diagonal block from its owners through distributed shared
 //     memory and factors it itself (identical arithmetic, so every CTA takes
 //     the same decisions about a failed pivot); each CTA solves the panel
@@ -31,7 +32,10 @@ namespace isvd {
 namespace {
 
 constexpr int kCholThreads = 512;
-constexpr int kNB = 16;
+#ifndef ISVD_CHOL_NB
+#define ISVD_CHOL_NB 8
+#endif
+constexpr int kNB = ISVD_CHOL_NB;  // panel rows (at most 32: the panel solve keeps one row per lane)
 constexpr double kReorthThreshold = 0.25;
 
 __host__ __device__ inline int cols_per_cta(int l, int cl) { return (l + cl - 1) / cl; }
