@@ -14,9 +14,13 @@
 // inside a slab `group` lanes cooperate on one row, each lane owning 16 bytes
 // of columns, so one gathered neighbour row is one coalesced 32..128-byte
 // read.  Slabs run one after another in launch order so that the slab of
-// the gathered block stays resident in L2.  Rows with more than
+// the gathered block stays resident in L2.  A slab narrower than 32 lanes
+// puts several row groups in a warp: they step through their rows together
+// and take rows in degree order, so their lengths match.  Rows with more than
 // `heavy_threshold` nonzeros are split into chunks whose partial sums are
-// combined in chunk order, so results are deterministic.
+// combined in chunk order (by a warp, or by a whole CTA for the largest hubs),
+// so results are deterministic; the chunks run on a second stream beside the
+// row kernel.
 #include "internal.h"
 
 // blocks per SM of the FP32 row kernel at high occupancy, and the nonzeros
