@@ -124,6 +124,11 @@ typedef struct {
   isvd_csr X;              /* sparse X (n x d), or all-null when X_dense is given */
   const float *X_dense;    /* dense X, row-major n x d (ld = d) */
   int32_t flags;           /* ISVD_FLAG_* */
+  /* Row gather (either form): the operator is M[gather_rows, :], the rows a
+   * closed-form fit uses (Thm. 1 on the training rows).  DEVICE int32,
+   * n_gather strictly increasing indices in [0, n); NULL = all rows. */
+  const int32_t *gather_rows;
+  int64_t n_gather;
 } isvd_operator_desc;
 
 /* Device-resident status of isvd_svd / isvd_orthonormalize, written by the
@@ -152,7 +157,8 @@ ISVD_API isvd_status isvd_create_operator(const isvd_operator_desc *desc, const 
 /* Free an operator and its workspace (after its last stream work).  NULL ok. */
 ISVD_API void isvd_destroy_operator(isvd_operator *op);
 
-/* (rows, cols) of M: (n, n) for POLY, (n, d (L+1)) for CONCAT (App. A.3: shape). */
+/* (rows, cols) of M: (n, n) for POLY, (n, d (L+1)) for CONCAT (App. A.3:
+ * shape); rows = n_gather with a row gather. */
 ISVD_API isvd_status isvd_operator_shape(const isvd_operator *op, int64_t *rows, int64_t *cols);
 
 /* out (rows x b) = M G, G (cols x b): App. A.3 `dot`.  dtype gives the

@@ -47,6 +47,7 @@ class _Op(C.Structure):
         ("xrowptr", C.c_void_p), ("xcolidx", C.c_void_p), ("xval", C.c_void_p),
         ("xdense", C.c_void_p),
         ("lr_rank", C.c_int32), ("lr_u", C.c_void_p), ("lr_v", C.c_void_p), ("lr_alpha", C.c_void_p),
+        ("grows", C.c_void_p), ("ngather", C.c_int64),
     ]
 
 
@@ -87,11 +88,13 @@ class Operator:
     beta A + sum_t a_t u_t v_t^T (Eq. 3 with alpha = -lambda, beta = +lambda;
     ``lowrank=(u, v, a)``).  ``form='concat'``:
     [X | NX | ... | N^L X] (Eq. 6).  ``norm='row'``: N = T = D^-1 A;
-    ``norm='sym'``: N = Â = (D+I)^-1/2 (A+I) (D+I)^-1/2 (Sec. 2)."""
+    ``norm='sym'``: N = Â = (D+I)^-1/2 (A+I) (D+I)^-1/2 (Sec. 2).
+    ``gather_rows``: the operator is M[gather_rows, :] (the training rows of
+    Thm. 1's fit)."""
 
     def __init__(self, n, rowptr, colidx, *, form="poly", norm="row", values=None,
                  coeffs=(), ones_coeff=0.0, adj_coeff=0.0, lowrank=None,
-                 X=None, L=0):
+                 X=None, L=0, gather_rows=None):
         self._keep = []
 
         def keep(a):
@@ -128,6 +131,10 @@ class Operator:
                 s.xrowptr = _p(keep(np.ascontiguousarray(xr, dtype=np.int32)))
                 s.xcolidx = _p(keep(np.ascontiguousarray(xc, dtype=np.int32)))
                 s.xval = _p(keep(_f64(xv)))
+        if gather_rows is not None:  # M[gather_rows, :] (training rows of Thm. 1's fit)
+            gr = keep(np.ascontiguousarray(gather_rows, dtype=np.int32))
+            s.grows = _p(gr)
+            s.ngather = len(gr)
         self.s = s
         self.form = form
         self.norm = norm

@@ -18,7 +18,8 @@
  *     optional low-rank terms sum_t a_t u_t v_t^T (the outer-product leaves
  *     of Sec. 4)
  *   - M_NC = [X | ÂX | ... | Â^L X]                               (Sec. 3.2, Eq. 6)
- *   - products M G and M^T G from those expressions                (Sec. 4; App. A.3)
+ *   - products M G and M^T G from those expressions                (Sec. 4; App. A.3),
+ *     also of a row selection M[rows, :] (the training rows of Thm. 1's fit)
  *   - orthonormOurs: L = chol(Q^T Q), Q <- Q (L^-1)^T              (Alg. 2, right)
  *     applied twice (CholeskyQR2) with a shift on breakdown
  *   - orthonormHalko: Householder QR                               (Alg. 2, left)
@@ -61,6 +62,9 @@ typedef struct {
   int32_t lr_rank;     /* extra terms sum_t a_t u_t v_t^T (polynomial form)     */
   const double *lr_u, *lr_v; /* n x lr_rank, row-major                         */
   const double *lr_alpha;
+  const int32_t *grows; /* row gather M[grows, :] (the training rows of Thm. 1's
+                           fit), NULL = all rows                             */
+  int64_t ngather;
 } orc_op;
 
 static double a_val(const orc_op *op, int64_t e) { return op->aval ? op->aval[e] : 1.0; }
@@ -74,7 +78,8 @@ static void degrees(const orc_op *op, double *deg) {
   }
 }
 
-int64_t orc_rows(const orc_op *op) { return op->n; }
+static int64_t full_rows(const orc_op *op) { return op->n; }
+int64_t orc_rows(const orc_op *op) { return op->grows ? op->ngather : full_rows(op); }
 int64_t orc_cols(const orc_op *op) { return op->form == 0 ? op->n : op->d * (op->L + 1); }
 
 /* ------------------------------------------------------------------------ */
@@ -187,8 +192,8 @@ static void x_apply_T(const orc_op *op, const double *P, double *out, int64_t ld
 /* Implicit products M G and M^T G (Sec. 4: only these are needed for SVD)   */
 /* ------------------------------------------------------------------------ */
 
-/* G is (cols x b), out is (rows x b), both row-major with ld = b. */
-int orc_apply(const orc_op *op, const double *G, int64_t b, double *out, int transpose) {
+/* G is (cols x b), out is (rows x b), both row-major with ld = b (the full M). */
+static int apply_full(const orc_op *op, const double *G, int64_t b, double *out, int transpose) {
   const int64_t n = op->n;
   double *deg = (double *)malloc(sizeof(double) * n);
   degrees(op, deg);
@@ -261,8 +266,40 @@ int orc_apply(const orc_op *op, const double *G, int64_t b, double *out, int tra
   return 0;
 }
 
+/* With a row gather S (rows grows of the identity): (S M) G = S (M G) and
+ * (S M)^T H = M^T (S^T H), S^T H placing row i of H at row grows[i]. */
+int orc_apply(const orc_op *op, const double *G, int64_t b, double *out, int transpose) {
+  if (!op->grows) return apply_full(op, G, b, out, transpose);
+  const int64_t nf = full_rows(op);
+  double *F = (double *)calloc((size_t)(nf * b), sizeof(double));
+  int rc;
+  if (!transpose) {
+    rc = apply_full(op, G, b, F, 0);
+    for (int64_t i = 0; i < op->ngather; ++i)
+      for (int64_t c = 0; c < b; ++c) out[i * b + c] = F[op->grows[i] * b + c];
+  } else {
+    for (int64_t i = 0; i < op->ngather; ++i)
+      for (int64_t c = 0; c < b; ++c) F[op->grows[i] * b + c] += G[i * b + c];
+    rc = apply_full(op, F, b, out, 1);
+  }
+  free(F);
+  return rc;
+}
+
+static int explicit_full(const orc_op *op, double *M);
+
 /* Dense M (rows x cols, row-major) built from its definition, tiny sizes. */
 int orc_explicit(const orc_op *op, double *M) {
+  if (!op->grows) return explicit_full(op, M);
+  const int64_t nf = full_rows(op), c = orc_cols(op);
+  double *F = (double *)malloc(sizeof(double) * nf * c);
+  const int rc = explicit_full(op, F);
+  for (int64_t i = 0; i < op->ngather; ++i) memcpy(M + i * c, F + op->grows[i] * c, sizeof(double) * c);
+  free(F);
+  return rc;
+}
+
+static int explicit_full(const orc_op *op, double *M) {
   const int64_t n = op->n;
   double *deg = (double *)malloc(sizeof(double) * n);
   degrees(op, deg);

@@ -315,6 +315,7 @@ struct ApplyScratch {
   double *lr_partial = nullptr;
   float *heavy_partial = nullptr;
   void *xdense = nullptr;  // dense-X products (CONCAT with dense X)
+  void *gz = nullptr;      // row gather: the full-height product (n x b)
 };
 size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool transpose);
 void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool transpose, char *base,

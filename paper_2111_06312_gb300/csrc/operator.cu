@@ -81,6 +81,30 @@ namespace {
 // ---- construction kernels ----------------------------------------------------
 // flags: [0] rowptr malformed  [1] column index out of range  [2] non-finite value
 //        [3] zero or negative degree where T = D^-1 A needs 1/d
+// Row gather indices: in [0, rows) and strictly increasing; flags[0] = 1 otherwise.
+__global__ void validate_rows_kernel(const int32_t *idx, int64_t count, int64_t rows, int32_t *flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const int32_t r = idx[i];
+    if (r < 0 || r >= rows || (i > 0 && idx[i - 1] >= r)) flags[0] = 1;
+  }
+}
+
+// out[i][:b] = full[idx[i]][:b] (gather) or full[idx[i]][:b] = in[i][:b]
+// (scatter into a zeroed block), element type T.
+template <typename T>
+__global__ void gather_rows_kernel(const T *src, int64_t lds, const int32_t *idx, int64_t count, int32_t b, T *dst,
+                                   int64_t ldd, int32_t scatter) {
+  const int64_t total = count * b;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t i = e / b, c = e - i * b;
+    const int64_t r = idx[i];
+    if (scatter) dst[r * ldd + c] = src[i * lds + c];
+    else dst[i * ldd + c] = src[r * lds + c];
+  }
+}
+
 __global__ void validate_csr_kernel(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rowptr,
                                     const int32_t *colidx, const float *values, int32_t *flags) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -518,6 +542,12 @@ isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaS
   } else {
     return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown form %d", (int)d.form);
   }
+  if (d.gather_rows) {
+    if (d.n_gather < 1 || d.n_gather > op->rows)
+      return fail(ISVD_ERR_INVALID_ARGUMENT, "n_gather must be in 1..%lld", (long long)op->rows);
+  } else if (d.n_gather != 0) {
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "n_gather without gather_rows");
+  }
   ISVD_CUDA_TRY(small_kernels_init());
   ISVD_CUDA_TRY(dense_kernels_init());
   ISVD_CUDA_TRY(cudaStreamCreateWithFlags(&op->capture_stream, cudaStreamNonBlocking));
@@ -547,6 +577,18 @@ isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaS
                   "a row of A has zero (or negative) degree: T = D^-1 A is undefined (add a self-loop)");
   }
   if (!(d.flags & ISVD_FLAG_SKIP_SYMMETRY_CHECK)) ISVD_TRY(check_symmetry(op, d.A, flags, s));
+  if (d.gather_rows) {
+    // strictly increasing row indices inside M; the operator has n_gather rows
+    ISVD_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 8, s));
+    validate_rows_kernel<<<grid_for(d.n_gather), 256, 0, s>>>(d.gather_rows, d.n_gather, op->rows, flags);
+    ISVD_CUDA_TRY(cudaGetLastError());
+    int32_t h[8];
+    ISVD_CUDA_TRY(cudaMemcpyAsync(h, flags, sizeof h, cudaMemcpyDeviceToHost, s));
+    ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h[0]) return fail(ISVD_ERR_INVALID_ARGUMENT, "gather_rows must be strictly increasing indices in [0, %lld)",
+                          (long long)op->rows);
+    op->rows = d.n_gather;
+  }
   ISVD_TRY(build_heavy(op, d.A.rowptr, n, &op->heavy_A, s));
   ISVD_TRY(build_chunks(op, d.A.rowptr, n, d.A.nnz, &op->chunk_A, s));
   ISVD_TRY(build_tags(op, s));
@@ -718,6 +760,7 @@ size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool t
   add(sizeof(float) * (size_t)chunks * pw);
   if (op->desc.form == ISVD_FORM_CONCAT && op->desc.X_dense)
     add(xdense_scratch_bytes((int32_t)op->desc.d, op->desc.L + 1, (int32_t)bseg, op->n));
+  if (op->desc.gather_rows) add(es * op->n * bseg);  // gz
   return total;
 }
 
@@ -743,6 +786,7 @@ void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool tra
   sc->heavy_partial = (float *)take(sizeof(float) * (size_t)chunks * pw);
   if (op->desc.form == ISVD_FORM_CONCAT && op->desc.X_dense)
     sc->xdense = take(xdense_scratch_bytes((int32_t)op->desc.d, op->desc.L + 1, (int32_t)bseg, op->n));
+  if (op->desc.gather_rows) sc->gz = take(es * op->n * bseg);
 }
 
 // Horner evaluation of sum_{k=1..K} c_k N^k G (+ corrections), Eq. 3 with the
@@ -945,10 +989,38 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
   return ISVD_OK;
 }
 
-isvd_status apply_impl(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo, int dtype,
-                       bool transpose, const ApplyScratch &sc, cudaStream_t s) {
+static isvd_status apply_form(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
+                              int dtype, bool transpose, const ApplyScratch &sc, cudaStream_t s) {
   if (op->desc.form == ISVD_FORM_POLY) return apply_poly(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
   return apply_concat(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
+}
+
+static cudaError_t gather_launch(const void *src, int64_t lds, const int32_t *idx, int64_t count, int32_t b,
+                                 void *dst, int64_t ldd, bool scatter, int dtype, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::min<int64_t>(std::max<int64_t>(ceil_div(count * b, 256), 1), kNumSMs * 16);
+  if (dtype == DT_F32)
+    gather_rows_kernel<float><<<grid, 256, 0, s>>>((const float *)src, lds, idx, count, b, (float *)dst, ldd,
+                                                   scatter ? 1 : 0);
+  else
+    gather_rows_kernel<uint16_t><<<grid, 256, 0, s>>>((const uint16_t *)src, lds, idx, count, b, (uint16_t *)dst,
+                                                      ldd, scatter ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// With a row gather S: (S M) G = S (M G) and (S M)^T H = M^T (S^T H).
+isvd_status apply_impl(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo, int dtype,
+                       bool transpose, const ApplyScratch &sc, cudaStream_t s) {
+  const isvd_operator_desc &d = op->desc;
+  if (!d.gather_rows) return apply_form(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
+  const int64_t ldz = round_up(b, 8);
+  if (!transpose) {
+    ISVD_TRY(apply_form(op, G, ldg, b, sc.gz, ldz, dtype, false, sc, s));
+    ISVD_CUDA_TRY(gather_launch(sc.gz, ldz, d.gather_rows, d.n_gather, b, out, ldo, false, dtype, s));
+    return ISVD_OK;
+  }
+  ISVD_CUDA_TRY(cudaMemsetAsync(sc.gz, 0, dtype_size(dtype) * (size_t)op->n * ldz, s));
+  ISVD_CUDA_TRY(gather_launch(G, ldg, d.gather_rows, d.n_gather, b, sc.gz, ldz, true, dtype, s));
+  return apply_form(op, sc.gz, ldz, b, out, ldo, dtype, true, sc, s);
 }
 
 }  // namespace isvd

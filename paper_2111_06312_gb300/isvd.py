@@ -47,7 +47,8 @@ class _Desc(C.Structure):
                 ("degree", C.c_int32), ("coeffs", C.c_void_p), ("ones_coeff", C.c_double),
                 ("adj_coeff", C.c_double), ("lr_rank", C.c_int32), ("lr_u", C.c_void_p),
                 ("lr_v", C.c_void_p), ("lr_alpha", C.c_void_p), ("d", C.c_int64), ("L", C.c_int32),
-                ("X", _Csr), ("X_dense", C.c_void_p), ("flags", C.c_int32)]
+                ("X", _Csr), ("X_dense", C.c_void_p), ("flags", C.c_int32),
+                ("gather_rows", C.c_void_p), ("n_gather", C.c_int64)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -173,12 +174,13 @@ class Operator:
     form='poly':   M = sum_k c_k N^k + ones_coeff 11^T + adj_coeff A + sum_t a_t u_t v_t^T  (Eq. 3)
     form='concat': M = [X | N X | ... | N^L X]                                              (Eq. 6)
     norm='row': N = D^-1 A;  norm='sym': N = (D+I)^-1/2 (A+I) (D+I)^-1/2  (Sec. 2).
+    gather_rows: the operator is M[gather_rows, :] (Thm. 1's fit on training rows).
     Arrays may be numpy or torch; they are copied to the device and kept
     alive for the operator's lifetime."""
 
     def __init__(self, n, rowptr, colidx, *, values=None, form="poly", norm="row", coeffs=(1.0,),
                  ones_coeff=0.0, adj_coeff=0.0, lowrank=None, X=None, L=0, check_symmetry=True,
-                 device="cuda", use_torch_allocator=True):
+                 gather_rows=None, device="cuda", use_torch_allocator=True):
         L_ = lib()
         dev = torch.device(device)
         self._keep = []
@@ -226,6 +228,10 @@ class Operator:
                 d.d = int(xt.shape[1])
                 d.X_dense = xt.data_ptr()
         d.flags = 0 if check_symmetry else FLAG_SKIP_SYMMETRY_CHECK
+        if gather_rows is not None:  # M[gather_rows, :] (strictly increasing rows)
+            gr = dev_t(gather_rows, torch.int32)
+            d.gather_rows = gr.data_ptr()
+            d.n_gather = int(gr.numel())
         self._desc = d
         self._handle = C.c_void_p()
         alloc = C.byref(_TORCH_ALLOCATOR) if use_torch_allocator else None

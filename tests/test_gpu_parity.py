@@ -327,6 +327,45 @@ def test_svd_concat_pubmed_sized(kernel):
     print(out)
 
 
+@pytest.mark.parametrize("form", ["poly", "concat"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_row_gather_apply(hub_graph, form, dtype):
+    """M[rows, :] (Thm. 1's fit on training rows): products through the
+    gather and the scatter against the oracle's row-selected operator."""
+    g = hub_graph
+    rows = np.sort(np.random.default_rng(31).choice(g.n, g.n * 3 // 5, replace=False)).astype(np.int32)
+    if form == "poly":
+        kw_g = kw_o = dict(norm="sym", coeffs=C5, ones_coeff=-LAM)
+    else:
+        x = synth.tfidf_features(g.n, 30, 0.05, 32)
+        kw_g = dict(form="concat", norm="sym", X=(30, x.rowptr, x.colidx, x.values), L=2)
+        kw_o = dict(form="concat", norm="sym", X=(30, x.rowptr, x.colidx, x.values.astype(np.float64)), L=2)
+    with isvd.graph_operator(g, gather_rows=rows, **kw_g) as gpu:
+        ref = oracle.graph_operator(g, gather_rows=rows, **kw_o)
+        assert gpu.shape == ref.shape and gpu.shape[0] == len(rows)
+        tol = 1e-5 if dtype == torch.float32 else 2e-2
+        for transpose in (False, True):
+            G = isvd.gaussian(8, gpu.shape[0] if transpose else gpu.shape[1], 21, dtype=dtype)
+            Y = gpu.apply(G, transpose=transpose)
+            Yr = ref.apply(npy(G), transpose=transpose)
+            assert np.abs(npy(Y) - Yr).max() <= tol * np.abs(Yr).max()
+
+
+def test_row_gather_svd(hub_graph):
+    g = hub_graph
+    rows = np.sort(np.random.default_rng(33).choice(g.n, g.n // 2, replace=False)).astype(np.int32)
+    with isvd.graph_operator(g, norm="sym", coeffs=C5, ones_coeff=-LAM, gather_rows=rows) as gpu:
+        ref = oracle.graph_operator(g, norm="sym", coeffs=C5, ones_coeff=-LAM, gather_rows=rows)
+        check_svd(gpu, ref, 16, 8, 4, 34)
+
+
+def test_row_gather_rejects_bad_rows(hub_graph):
+    g = hub_graph
+    for bad in (np.array([3, 3, 5], np.int32), np.array([5, 2], np.int32), np.array([0, g.n], np.int32)):
+        with pytest.raises(isvd.IsvdError, match="gather_rows"):
+            isvd.graph_operator(g, coeffs=C5, gather_rows=bad)
+
+
 def test_svd_is_deterministic(ne_small):
     with isvd.graph_operator(ne_small, coeffs=C5, ones_coeff=-LAM) as gpu:
         U1, S1, V1, _ = gpu.svd(16, 8, 3, 5)

@@ -430,3 +430,28 @@ def test_lowrank_term_closed_form():
     a1 = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM).apply(G)
     a2 = oracle.graph_operator(g, coeffs=C5, lowrank=(one, one, [-LAM])).apply(G)
     assert np.allclose(a1, a2, rtol=1e-13, atol=1e-12)
+
+
+@pytest.mark.parametrize("form", ["poly", "concat"])
+def test_row_gather_is_a_row_selection(form):
+    # M[rows, :] (the training-row fit of Thm. 1): a row selection of the
+    # explicit matrix, whose products follow from the selection S (S M G and
+    # M^T S^T H) and whose SVD is LAPACK's on the selected rows
+    g = _irregular(120, 500, 26)
+    rows = np.sort(np.random.default_rng(27).choice(g.n, 70, replace=False))
+    kw = dict(norm="sym", coeffs=C5, ones_coeff=-LAM) if form == "poly" else dict(
+        form="concat", norm="sym", X=np.random.default_rng(28).standard_normal((g.n, 9)), L=2)
+    full = oracle.graph_operator(g, **kw)
+    sub = oracle.graph_operator(g, gather_rows=rows, **kw)
+    M = full.explicit()
+    assert sub.shape == (70, M.shape[1])
+    assert np.array_equal(sub.explicit(), M[rows])
+    rng = np.random.default_rng(29)
+    G = rng.standard_normal((M.shape[1], 5))
+    H = rng.standard_normal((70, 5))
+    assert np.allclose(sub.apply(G), M[rows] @ G, rtol=1e-12, atol=1e-12)
+    assert np.allclose(sub.apply(H, transpose=True), M[rows].T @ H, rtol=1e-12, atol=1e-12)
+    Sr = np.linalg.svd(M[rows], compute_uv=False)
+    k = int(np.argmax(np.diff(-Sr[:8]))) + 1  # largest gap among the top 8
+    _, S, _, _ = sub.isvd(k, 8, 12, 30)
+    assert np.allclose(S, Sr[:k], rtol=1e-8)
