@@ -5,7 +5,7 @@
   python -m paper_2111_06312_gb300.kernel_bench sweep [--workload ne_large] [--width 144] [--dtype f32]
   python -m paper_2111_06312_gb300.kernel_bench orth  [--rows 1000000] [--width 144] [--reps 5]
   python -m paper_2111_06312_gb300.kernel_bench svd   [--workload ne_large] [--k 128 --p 16 --q 6]
-                                                      [--kernel rows|chunks] [--precision fp32|mixed]
+                                                      [--kernel rows|chunks] [--precision fp32|mixed] [--gather-frac 0.1]
   python -m paper_2111_06312_gb300.kernel_bench equal_error [--workload ne_large] [--k 128 --p 16 --q 6]
   python -m paper_2111_06312_gb300.kernel_bench batched [--count 256]
   python -m paper_2111_06312_gb300.kernel_bench finetune [--epochs 20]
@@ -104,6 +104,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--q-ref", type=int, default=0)
     ap.add_argument("--q-extra", type=int, default=4)
+    ap.add_argument("--gather-frac", type=float, default=0.0)  # svd of M[rows, :] on this fraction of rows
     a = ap.parse_args()
     build.build()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -155,13 +156,18 @@ def main():
         op.close()
     elif a.what == "svd":
         g = synth.cached(a.workload)
-        with isvd.graph_operator(g, coeffs=C5, ones_coeff=-LAM) as op:
+        rows = None
+        if a.gather_frac > 0:  # seeded row subset (a training mask)
+            rng = np.random.default_rng(synth.BASE_SEED + 7)
+            rows = np.sort(rng.choice(g.n, int(a.gather_frac * g.n), replace=False)).astype(np.int32)
+        with isvd.graph_operator(g, coeffs=C5, ones_coeff=-LAM, gather_rows=rows) as op:
             if a.kernel:
                 op.set_tuning(kernel=a.kernel, chunk_nnz=a.chunk_nnz or 512)
             op.svd(a.k, a.p, a.q, 1, precision=a.precision)
             ts = _time(lambda: op.svd(a.k, a.p, a.q, 1, precision=a.precision, check=False), a.reps, flush)
             print(json.dumps({"what": "svd", "workload": a.workload, "k": a.k, "p": a.p, "q": a.q,
-                              "precision": a.precision, "ms": float(np.median(ts)), "tuning": op.tuning(),
+                              "precision": a.precision, "gather_rows": 0 if rows is None else len(rows),
+                              "ms": float(np.median(ts)), "tuning": op.tuning(),
                               "kernels": op.graph_kernel_nodes()}))
     elif a.what == "equal_error":
         equal_error(a, flush)
