@@ -211,6 +211,19 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------------------------
 
+def slowest_rank_ms(ms, world, device):
+    """The step time reported for N replicas: the slowest rank's (all-reduce MAX;
+    the replicas share no data, so this is the only collective)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -278,11 +291,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(float(np.mean(step_ms)), world, dev)
     kernels_per_step = op.graph_kernel_nodes()
 
     # ---- SpMM step roofline: one M.Q apply of this operator at the SVD's block width ----
