@@ -57,7 +57,7 @@ typedef enum {
   ISVD_ERR_TIMEOUT = 5,            /* a bounded device wait expired */
   ISVD_ERR_WORKSPACE = 6,          /* the allocator returned NULL */
   ISVD_ERR_CUDA = 7,               /* a CUDA runtime call failed (detail in last_error) */
-  ISVD_ERR_UNSUPPORTED = 8         /* valid request outside what this build implements */
+  ISVD_ERR_UNSUPPORTED = 8         /* valid request outside what this library implements */
 } isvd_status;
 
 typedef enum { ISVD_F32 = 0, ISVD_BF16 = 1 } isvd_dtype;
