@@ -25,6 +25,10 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
 
+# N in Sec. 2: "row" T = D^-1 A; "sym" Â = (D+I)^-1/2 (A+I) (D+I)^-1/2;
+# "sym_noself" Â - (D+I)^-1, label re-use's adjacency (Sec. 5.3)
+NORMS = {"row": 0, "sym": 1, "sym_noself": 2}
+
 
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, -O2, OpenMP, strict IEEE) and return the path."""
@@ -103,7 +107,7 @@ class Operator:
 
         s = _Op()
         s.form = 0 if form == "poly" else 1
-        s.norm = 0 if norm == "row" else 1
+        s.norm = NORMS[norm]
         s.n = int(n)
         s.rowptr = _p(keep(np.ascontiguousarray(rowptr, dtype=np.int32)))
         s.colidx = _p(keep(np.ascontiguousarray(colidx, dtype=np.int32)))
@@ -269,6 +273,25 @@ def closed_form(U, S, V, Y, rcond=1e-6):
     smax = S.max() if S.size else 0.0
     inv = np.where((S > 0) & (S > rcond * smax), 1.0 / np.where(S > 0, S, 1.0), 0.0)
     return V @ (inv[:, None] * (U.T @ Y))
+
+
+def embeddings(U, S, V):
+    """Network-embedding outputs of a rank-k SVD (Sec. 3.1): L = U S^1/2 and
+    R = V S^1/2, so that L R^T = U diag(S) V^T.  FP64."""
+    U, S, V = (np.asarray(a, dtype=np.float64) for a in (U, S, V))
+    h = np.sqrt(S)
+    return U * h[None, :], V * h[None, :]
+
+
+def pair_scores(Lm, Rm, src, dst):
+    """Similarity of the node at row i and the node at column j (Sec. 3.1):
+    f(i, j) = <L_i, R_j>, for each pair (src[p], dst[p]).  FP64 loop."""
+    Lm = np.asarray(Lm, dtype=np.float64)
+    Rm = np.asarray(Rm, dtype=np.float64)
+    out = np.empty(len(src))
+    for p, (i, j) in enumerate(zip(src, dst)):
+        out[p] = float(np.dot(Lm[i], Rm[j]))
+    return out
 
 
 # ---- metrics ----------------------------------------------------------------

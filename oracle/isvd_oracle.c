@@ -13,6 +13,8 @@
  *
  * What is computed, and where it is defined:
  *   - T = D^-1 A and  Â = (D+I)^-1/2 (A+I) (D+I)^-1/2            (Sec. 2)
+ *   - Â - (D+I)^-1, the adjacency of label re-use, whose diagonal is
+ *     zero on a graph without self-loops                           (Sec. 5.3)
  *   - M_NE = sum_q c_q T^q - lambda (1 1^T - A)                    (Sec. 3.1, Eq. 3)
  *     with the all-ones and adjacency coefficients given separately, plus
  *     optional low-rank terms sum_t a_t u_t v_t^T (the outer-product leaves
@@ -47,7 +49,7 @@
 
 typedef struct {
   int32_t form;        /* 0: polynomial  sum_k c_k N^k ; 1: concatenation     */
-  int32_t norm;        /* 0: N = T = D^-1 A ; 1: N = Â                         */
+  int32_t norm;        /* 0: N = T = D^-1 A ; 1: N = Â ; 2: N = Â - (D+I)^-1    */
   int64_t n;           /* nodes                                                */
   const int32_t *rowptr, *colidx; /* CSR of A (n x n)                          */
   const double *aval;  /* edge weights, NULL = all ones                        */
@@ -87,7 +89,8 @@ int64_t orc_cols(const orc_op *op) { return op->form == 0 ? op->n : op->d * (op-
 /* ------------------------------------------------------------------------ */
 
 /* out = N P  (n x b).  N = T:  out_i = (1/d_i) sum_j A_ij P_j.
- * N = Â: out_i = sum_j (A+I)_ij P_j / sqrt((d_i+1)(d_j+1)).                 */
+ * N = Â: out_i = sum_j (A+I)_ij P_j / sqrt((d_i+1)(d_j+1)).
+ * N = Â - (D+I)^-1: the same without the identity term (norm 2).           */
 static void norm_apply(const orc_op *op, const double *deg, const double *P, double *out, int64_t b) {
   const int64_t n = op->n;
 #pragma omp parallel for schedule(dynamic, 256)
@@ -106,8 +109,10 @@ static void norm_apply(const orc_op *op, const double *deg, const double *P, dou
         const double t = a_val(op, e) / sqrt((deg[i] + 1.0) * (deg[j] + 1.0));
         for (int64_t c = 0; c < b; ++c) o[c] += t * P[j * b + c];
       }
-      const double t = 1.0 / (deg[i] + 1.0); /* the identity term, (I)_ii */
-      for (int64_t c = 0; c < b; ++c) o[c] += t * P[i * b + c];
+      if (op->norm == 1) {
+        const double t = 1.0 / (deg[i] + 1.0); /* the identity term, (I)_ii */
+        for (int64_t c = 0; c < b; ++c) o[c] += t * P[i * b + c];
+      }
     }
   }
 }

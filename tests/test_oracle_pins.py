@@ -116,6 +116,67 @@ def test_cycle_spectrum_sym(n):
     assert np.allclose(S, np.sort(np.abs(ev))[::-1], rtol=1e-12, atol=1e-13)
 
 
+@pytest.mark.parametrize("n", [7, 10])
+def test_cycle_spectrum_noself(n):
+    # label re-use's adjacency Â - (D+I)^-1 (Sec. 5.3) on C_n: A/3, with
+    # eigenvalues 2 cos(2 pi j/n) / 3; Â itself does not match
+    g = synth.cycle(n)
+    mu = 2 * np.cos(2 * np.pi * np.arange(n) / n) / 3
+    ev = poly(C5, mu)
+    ev[0] -= LAM * n
+    want = np.sort(np.abs(ev))[::-1]
+    _, S, _ = oracle.jacobi_svd(oracle.graph_operator(g, norm="sym_noself", coeffs=C5, ones_coeff=-LAM).explicit())
+    assert np.allclose(S, want, rtol=1e-12, atol=1e-13)
+    _, S1, _ = oracle.jacobi_svd(oracle.graph_operator(g, norm="sym", coeffs=C5, ones_coeff=-LAM).explicit())
+    assert not np.allclose(S1, want, rtol=1e-6)
+
+
+@pytest.mark.parametrize("n", [5, 8])
+def test_complete_graph_spectrum_noself(n):
+    # K_n: d = n - 1, so Â - (D+I)^-1 = (J - I)/n, eigenvalues (n-1)/n on 1
+    # and -1/n (n - 1 times)
+    g = synth.complete(n)
+    op = oracle.graph_operator(g, norm="sym_noself", coeffs=C5, ones_coeff=-LAM)
+    ev = np.array([poly(C5, (n - 1) / n) - LAM * n] + [poly(C5, -1.0 / n)] * (n - 1))
+    _, S, _ = oracle.jacobi_svd(op.explicit())
+    assert np.allclose(S, np.sort(np.abs(ev))[::-1], rtol=1e-12, atol=1e-13)
+
+
+def test_noself_is_sym_minus_the_identity_term():
+    # Â - (Â - (D+I)^-1) = diag(1/(d_i+1)); the diagonal of Â - (D+I)^-1 is
+    # zero on a graph without self-loops (no label leakage from row i of Y
+    # into row i of the propagated block, Sec. 5.3)
+    g = synth.chung_lu(150, 700, 41, isolated_self_loops=False)
+    d = np.diff(g.rowptr).astype(np.float64)
+    assert (d > 0).any() and not np.any(np.repeat(np.arange(g.n), np.diff(g.rowptr)) == g.colidx)
+    Ms = oracle.graph_operator(g, norm="sym", coeffs=[1.0]).explicit()
+    M0 = oracle.graph_operator(g, norm="sym_noself", coeffs=[1.0]).explicit()
+    assert np.allclose(Ms - M0, np.diag(1.0 / (d + 1.0)), rtol=0, atol=1e-15)
+    assert np.all(np.diag(M0) == 0.0)
+    assert np.allclose(M0, M0.T, rtol=0, atol=1e-15)
+
+
+def test_label_reuse_blocks_do_not_leak():
+    # [Y | N0 Y | N0^2 Y] with N0 = Â - (D+I)^-1 and Y one-hot on training
+    # rows: row i of N0 Y does not depend on Y_i; with Â it does
+    g = synth.chung_lu(200, 1000, 42, isolated_self_loops=False)
+    rng = np.random.default_rng(43)
+    y = 5
+    Y = np.zeros((g.n, y))
+    train = rng.choice(g.n, 120, replace=False)
+    Y[train, rng.integers(0, y, 120)] = 1.0
+    i = int(train[np.argmax(np.diff(g.rowptr)[train])])
+    Y2 = Y.copy()
+    Y2[i] = np.roll(Y[i], 1)
+    for norm, leaks in (("sym_noself", False), ("sym", True)):
+        m1 = oracle.graph_operator(g, form="concat", norm=norm, X=Y, L=2).explicit()
+        m2 = oracle.graph_operator(g, form="concat", norm=norm, X=Y2, L=2).explicit()
+        assert m1.shape == (g.n, 3 * y)
+        assert np.array_equal(m1[i, :y] != m2[i, :y], Y[i] != Y2[i])  # block 0 is Y itself
+        changed = not np.allclose(m1[i, y:2 * y], m2[i, y:2 * y], rtol=0, atol=0)
+        assert changed == leaks
+
+
 @pytest.mark.parametrize("L", [1, 2, 3])
 def test_concat_identity_features(L):
     # X = I: M M^T = sum_l Â^(2l), sigma_j = sqrt(sum_l mu_j^(2l))
@@ -173,7 +234,8 @@ def test_weighted_row_operator():
     assert np.allclose(op.apply(dw, transpose=True), dw, rtol=1e-12)
 
 
-@pytest.mark.parametrize("form,norm", [("poly", "row"), ("poly", "sym"), ("concat", "sym"), ("concat", "row")])
+@pytest.mark.parametrize("form,norm", [("poly", "row"), ("poly", "sym"), ("concat", "sym"), ("concat", "row"),
+                                       ("poly", "sym_noself"), ("concat", "sym_noself")])
 def test_adjoint_identity(form, norm):
     g = _irregular(120, 500, 9)
     rng = np.random.default_rng(1)
@@ -207,14 +269,14 @@ def test_implicit_matches_explicit_all_graphs_n4():
     rng = np.random.default_rng(2)
     count = 0
     for g in _all_graphs(4):
-        for norm in ("row", "sym"):
+        for norm in ("row", "sym", "sym_noself"):
             op = oracle.graph_operator(g, norm=norm, coeffs=C5, ones_coeff=-LAM, adj_coeff=0.3)
             M = op.explicit()
             G = rng.standard_normal((4, 3))
             assert np.abs(op.apply(G) - M @ G).max() <= 1e-13
             assert np.abs(op.apply(G, transpose=True) - M.T @ G).max() <= 1e-13
             count += 1
-    assert count == 2 * 64
+    assert count == 3 * 64
 
 
 def test_implicit_matches_explicit_concat():
@@ -455,3 +517,47 @@ def test_row_gather_is_a_row_selection(form):
     k = int(np.argmax(np.diff(-Sr[:8]))) + 1  # largest gap among the top 8
     _, S, _, _ = sub.isvd(k, 8, 12, 30)
     assert np.allclose(S, Sr[:k], rtol=1e-8)
+
+
+# ---- embeddings and pair scores (Sec. 3.1) -----------------------------------
+
+def test_embeddings_reach_the_eckart_young_error():
+    # L R^T = U_k S_k V_k^T: ||M - L R^T||_F^2 is the tail sum of sigma^2
+    # (LAPACK's SVD of the explicit matrix)
+    g = _irregular(80, 360, 44)
+    M = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM).explicit()
+    U, S, Vt = np.linalg.svd(M)
+    for k in (1, 5, 20):
+        Lm, Rm = oracle.embeddings(U[:, :k], S[:k], Vt[:k].T)
+        err = np.linalg.norm(M - Lm @ Rm.T) ** 2
+        assert abs(err - np.sum(S[k:] ** 2)) <= 1e-10 * np.sum(S ** 2)
+        # both sides carry S^1/2: the column norms of L and R are sqrt(S)
+        assert np.allclose(np.linalg.norm(Lm, axis=0), np.sqrt(S[:k]), rtol=1e-12)
+        assert np.allclose(np.linalg.norm(Rm, axis=0), np.sqrt(S[:k]), rtol=1e-12)
+
+
+def test_embeddings_coincide_for_a_psd_matrix():
+    # Â^2 is symmetric PSD: its SVD has U = V, hence L = R (Sec. 3.1 on the
+    # symmetric variant)
+    g = _irregular(60, 260, 45)
+    M = oracle.graph_operator(g, norm="sym", coeffs=[0.0, 1.0]).explicit()
+    U, S, Vt = np.linalg.svd(M)
+    k = 6
+    assert S[k - 1] > S[k] * (1 + 1e-6)
+    Lm, Rm = oracle.embeddings(U[:, :k], S[:k], Vt[:k].T)
+    assert np.allclose(Lm, Rm, rtol=0, atol=1e-10)
+
+
+def test_pair_scores_recover_entries_at_full_rank():
+    # f(i, j) = <L_i, R_j> equals M_ij when k = rank(M); M = T (row
+    # normalised, not symmetric) so that f(i, j) != f(j, i)
+    g = _irregular(50, 220, 46)
+    M = oracle.graph_operator(g, coeffs=[1.0]).explicit()
+    U, S, Vt = np.linalg.svd(M)
+    Lm, Rm = oracle.embeddings(U, S, Vt.T)
+    rng = np.random.default_rng(47)
+    src = rng.integers(0, g.n, 200)
+    dst = rng.integers(0, g.n, 200)
+    f = oracle.pair_scores(Lm, Rm, src, dst)
+    assert np.allclose(f, M[src, dst], rtol=0, atol=1e-12)
+    assert not np.allclose(oracle.pair_scores(Lm, Rm, dst, src), M[src, dst], rtol=0, atol=1e-6)
