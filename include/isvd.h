@@ -69,7 +69,10 @@ typedef enum { ISVD_PREC_FP32 = 0, ISVD_PREC_MIXED = 1 } isvd_precision;
 
 typedef enum {
   ISVD_NORM_ROW = 0,          /* N = T = D^-1 A                   (Sec. 2) */
-  ISVD_NORM_SYM_SELFLOOP = 1  /* N = Â = (D+I)^-1/2 (A+I) (D+I)^-1/2  (Sec. 2) */
+  ISVD_NORM_SYM_SELFLOOP = 1, /* N = Â = (D+I)^-1/2 (A+I) (D+I)^-1/2  (Sec. 2) */
+  ISVD_NORM_SYM_NOSELF = 2    /* N = Â - (D+I)^-1 = (D+I)^-1/2 A (D+I)^-1/2: label
+                                 re-use's adjacency, zero diagonal on a graph
+                                 without self-loops (Sec. 5.3)                  */
 } isvd_norm;
 
 typedef enum {
@@ -266,6 +269,29 @@ ISVD_API isvd_status isvd_orthonormalize_noalloc(float *Q, int64_t rows, int32_t
 ISVD_API isvd_status isvd_closed_form(isvd_operator *op, const float *U, int64_t ldu, const float *S, const float *V,
                                       int64_t ldv, int32_t k, const float *Y, int64_t ldy, int32_t m, double rcond,
                                       float *W, int64_t ldw, void *stream);
+
+/* Network-embedding outputs of a rank-k SVD (Sec. 3.1): the rows and columns
+ * of M are embedded as L = U diag(S)^1/2 and R = V diag(S)^1/2, so that
+ * L R^T = U diag(S) V^T.  One call scales one factor: out = X diag(S)^1/2.
+ * DEVICE, FP32, row-major: X (rows x k, ld ldx), S (k, >= 0; a negative
+ * entry gives NaN columns), out (rows x k, ld ldo).  out == X scales in place;
+ * other overlaps are undefined.  rows == 0 is a no-op.  Asynchronous on
+ * `stream`.  Errors: INVALID_ARGUMENT (null pointer, ld < k), SHAPE (k < 1). */
+ISVD_API isvd_status isvd_embed(const float *X, int64_t ldx, int64_t rows, int32_t k, const float *S, float *out,
+                                int64_t ldo, void *stream);
+
+/* Similarity of the node at row i and the node at column j (Sec. 3.1):
+ * f(i, j) = <L_i, R_j> = U_i^T diag(S) V_j, for each pair p:
+ * out[p] = f(src[p], dst[p]).  DEVICE: L (rows x k, ld ldl), R (cols x k,
+ * ld ldr) FP32 row-major; src, dst (n_pairs, int32); out (n_pairs, FP32).
+ * Products in FP32 per lane, summed across the warp in FP64 in a fixed order
+ * (bitwise reproducible).  A pair with src outside [0, rows) or dst outside
+ * [0, cols) gets NaN and, if dev_info is not NULL, dev_info->status =
+ * ISVD_ERR_INVALID_ARGUMENT (left unchanged otherwise).  n_pairs == 0 is a
+ * no-op.  Asynchronous on `stream`. */
+ISVD_API isvd_status isvd_pair_scores(const float *L, int64_t ldl, int64_t rows, const float *R, int64_t ldr,
+                                      int64_t cols, int32_t k, const int32_t *src, const int32_t *dst,
+                                      int64_t n_pairs, float *out, isvd_info *dev_info, void *stream);
 
 /* SVD of a small square upper-triangular-or-dense FP64 matrix by one-sided
  * Jacobi on its transpose (the Rayleigh-Ritz step of Alg. 1, done as

@@ -4,6 +4,10 @@
 // U^T Y is a tall-skinny transposed product over the r rows of U and Y
 // (split over row parts, FP32 products summed per 64-row step, FP64 across
 // steps and parts); the k x m result is scaled by S^+ and multiplied into V.
+// Also the network-embedding outputs of Sec. 3.1: L = U S^1/2, R = V S^1/2
+// and the pair scores f(i, j) = <L_i, R_j>.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace isvd {
@@ -73,7 +77,66 @@ __global__ void closed_form_reduce_kernel(const double *__restrict__ partial, in
   }
 }
 
+// out = X diag(S)^1/2, one element per thread (grid-stride; out may be X)
+__global__ void embed_kernel(const float *X, int64_t ldx, int64_t rows, int32_t k, const float *__restrict__ S,
+                             float *out, int64_t ldo) {
+  const int64_t total = rows * k;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / k;
+    const int j = (int)(idx - r * k);
+    out[r * ldo + j] = X[r * ldx + j] * sqrtf(__ldg(S + j));
+  }
+}
+
+// One warp per pair: lane t multiplies columns t, t + 32, ... in FP32, the
+// 32 lane sums are added in FP64 by a butterfly (fixed order).
+__global__ void __launch_bounds__(256) pair_scores_kernel(const float *__restrict__ L, int64_t ldl, int64_t rows,
+                                                          const float *__restrict__ R, int64_t ldr, int64_t cols,
+                                                          int32_t k, const int32_t *__restrict__ src,
+                                                          const int32_t *__restrict__ dst, int64_t n_pairs,
+                                                          float *__restrict__ out, isvd_info *info) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_pairs; p += nwarp) {
+    const int64_t i = __ldg(src + p), j = __ldg(dst + p);
+    if (i < 0 || i >= rows || j < 0 || j >= cols) {
+      if (lane == 0) {
+        out[p] = __int_as_float(0x7fc00000);
+        if (info) atomicCAS(&info->status, 0, (int)ISVD_ERR_INVALID_ARGUMENT);
+      }
+      continue;
+    }
+    const float *li = L + i * ldl;
+    const float *rj = R + j * ldr;
+    float acc = 0.f;
+    for (int c = lane; c < k; c += 32) acc = fmaf(__ldg(li + c), __ldg(rj + c), acc);
+    double t = (double)acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) out[p] = (float)t;
+  }
+}
+
 }  // namespace
+
+cudaError_t embed_launch(const float *X, int64_t ldx, int64_t rows, int32_t k, const float *S, float *out,
+                         int64_t ldo, cudaStream_t s) {
+  const int64_t total = rows * k;
+  if (total == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>(ceil_div(total, 256), (int64_t)kNumSMs * 8);
+  embed_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, rows, k, S, out, ldo);
+  return cudaGetLastError();
+}
+
+cudaError_t pair_scores_launch(const float *L, int64_t ldl, int64_t rows, const float *R, int64_t ldr, int64_t cols,
+                               int32_t k, const int32_t *src, const int32_t *dst, int64_t n_pairs, float *out,
+                               isvd_info *info, cudaStream_t s) {
+  if (n_pairs == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>(ceil_div(n_pairs, 8), (int64_t)kNumSMs * 8);
+  pair_scores_kernel<<<(unsigned)blocks, 256, 0, s>>>(L, ldl, rows, R, ldr, cols, k, src, dst, n_pairs, out, info);
+  return cudaGetLastError();
+}
 
 int32_t tn_tiles(int32_t p, int32_t q) { return ((p + kTnTile - 1) / kTnTile) * ((q + kTnTile - 1) / kTnTile); }
 

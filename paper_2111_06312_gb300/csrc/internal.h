@@ -198,6 +198,14 @@ cudaError_t closed_form_launch(const float *U, int64_t ldu, const float *S, cons
                                int64_t c, int32_t k, const float *Y, int64_t ldy, int32_t m, double rcond,
                                float *W, int64_t ldw, double *partial, int32_t nparts, float *Z, cudaStream_t s);
 
+// out = X diag(S)^1/2 (Sec. 3.1 embeddings; out may equal X) and
+// out[p] = <L_src[p], R_dst[p]> with range-checked indices (closed_form.cu).
+cudaError_t embed_launch(const float *X, int64_t ldx, int64_t rows, int32_t k, const float *S, float *out,
+                         int64_t ldo, cudaStream_t s);
+cudaError_t pair_scores_launch(const float *L, int64_t ldl, int64_t rows, const float *R, int64_t ldr, int64_t cols,
+                               int32_t k, const int32_t *src, const int32_t *dst, int64_t n_pairs, float *out,
+                               isvd_info *info, cudaStream_t s);
+
 // C (p x q, FP64 partials per row part) = A^T B over `rows` rows (closed_form.cu).
 int32_t tn_tiles(int32_t p, int32_t q);
 cudaError_t tn_partial_launch(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t rows, int32_t p,

@@ -506,7 +506,7 @@ isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaS
   const isvd_operator_desc &d = *desc;
   ISVD_TRY(check_csr_host(d.A, "A"));
   if (d.A.rows != d.A.cols) return fail(ISVD_ERR_SHAPE, "A must be square");
-  if (d.norm != ISVD_NORM_ROW && d.norm != ISVD_NORM_SYM_SELFLOOP)
+  if (d.norm != ISVD_NORM_ROW && d.norm != ISVD_NORM_SYM_SELFLOOP && d.norm != ISVD_NORM_SYM_NOSELF)
     return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown normalisation %d", (int)d.norm);
   op->n = d.A.rows;
   if (d.form == ISVD_FORM_POLY) {
@@ -794,12 +794,14 @@ void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool tra
 // K sparse products per apply).  N^T for N = D^-1 A is A D^-1 (A symmetric),
 // evaluated on D^-1-scaled iterates; Â is symmetric and evaluated on
 // (D+I)^-1/2-scaled iterates so that only the first product gathers a weight.
+// Â - (D+I)^-1 (label re-use, Sec. 5.3) is Â without its identity term.
 static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
                               int dtype, bool transpose, const ApplyScratch &sc, cudaStream_t s) {
   const isvd_operator_desc &d = op->desc;
   const int K = d.degree;
   const std::vector<double> &c = op->coeffs;  // c[k-1] = c_k
   const bool row = d.norm == ISVD_NORM_ROW;
+  const int32_t selfloop = d.norm == ISVD_NORM_SYM_SELFLOOP ? 1 : 0;  // Â's identity term
   const int64_t bseg = round_up(b, 8);
   const int scols = slab_cols(op, dtype);
   const Chain ch{op, dtype, s, &sc};
@@ -850,7 +852,7 @@ static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int
       a.ax_rowscale = op->inv_d;
     } else {  // Â
       if (first) a.colw = op->s;
-      a.self_term = 1;
+      a.self_term = selfloop;
       a.rowscale = last ? op->s : op->s2;
       a.ax_rowscale = op->s;
     }
@@ -881,6 +883,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
   const isvd_operator_desc &d = op->desc;
   const int L = d.L;
   const bool row = d.norm == ISVD_NORM_ROW;
+  const int32_t selfloop = d.norm == ISVD_NORM_SYM_SELFLOOP ? 1 : 0;  // Â's identity term
   const int64_t bseg = round_up(b, 8);
   const int64_t ldp = bseg * (L + 1);
   const size_t es = dtype_size(dtype);
@@ -934,7 +937,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
         a.rowscale = op->inv_d;
       } else {
         if (first) a.colw = op->s;
-        a.self_term = 1;
+        a.self_term = selfloop;
         a.rowscale = last ? op->s : op->s2;
         a.ax_rowscale = last ? nullptr : op->s;
       }
@@ -955,7 +958,7 @@ static isvd_status apply_concat(isvd_operator *op, const void *G, int64_t ldg, i
       a.colw = op->inv_d;  // T^T = A D^-1
     } else {
       a.colw = op->s;
-      a.self_term = 1;
+      a.self_term = selfloop;
       a.rowscale = op->s;
     }
     ISVD_SLABS(add_slabs(a, dtype, b, scols, 0, cur, ldcur, seg(l), ldp, nullptr, 0));

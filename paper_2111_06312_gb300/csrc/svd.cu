@@ -496,6 +496,30 @@ isvd_status isvd_closed_form(isvd_operator *op, const float *U, int64_t ldu, con
   return ISVD_OK;
 }
 
+isvd_status isvd_embed(const float *X, int64_t ldx, int64_t rows, int32_t k, const float *S, float *out,
+                       int64_t ldo, void *stream) {
+  if (!X || !S || !out) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (k < 1) return fail(ISVD_ERR_SHAPE, "need k >= 1");
+  if (rows < 0) return fail(ISVD_ERR_INVALID_ARGUMENT, "rows must be >= 0");
+  if (ldx < k || ldo < k) return fail(ISVD_ERR_INVALID_ARGUMENT, "leading dimension too small");
+  ISVD_CUDA_TRY(embed_launch(X, ldx, rows, k, S, out, ldo, (cudaStream_t)stream));
+  return ISVD_OK;
+}
+
+isvd_status isvd_pair_scores(const float *L, int64_t ldl, int64_t rows, const float *R, int64_t ldr, int64_t cols,
+                             int32_t k, const int32_t *src, const int32_t *dst, int64_t n_pairs, float *out,
+                             isvd_info *dev_info, void *stream) {
+  if (n_pairs < 0) return fail(ISVD_ERR_INVALID_ARGUMENT, "n_pairs must be >= 0");
+  if (n_pairs == 0) return ISVD_OK;
+  if (!L || !R || !src || !dst || !out) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (k < 1) return fail(ISVD_ERR_SHAPE, "need k >= 1");
+  if (rows < 0 || cols < 0) return fail(ISVD_ERR_INVALID_ARGUMENT, "rows and cols must be >= 0");
+  if (ldl < k || ldr < k) return fail(ISVD_ERR_INVALID_ARGUMENT, "leading dimension too small");
+  ISVD_CUDA_TRY(pair_scores_launch(L, ldl, rows, R, ldr, cols, k, src, dst, n_pairs, out, dev_info,
+                                   (cudaStream_t)stream));
+  return ISVD_OK;
+}
+
 isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double *Uo, double *S, double *Vo,
                            isvd_info *dev_info, void *stream) {
   if (!op || !A || !Uo || !S || !Vo) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");

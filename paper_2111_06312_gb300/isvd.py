@@ -24,7 +24,7 @@ STATUS_NAMES = {
 }
 F32, BF16 = 0, 1
 PREC = {"fp32": 0, "mixed": 1}
-NORM = {"row": 0, "sym": 1}
+NORM = {"row": 0, "sym": 1, "sym_noself": 2}
 FORM = {"poly": 0, "concat": 1}
 FLAG_SKIP_SYMMETRY_CHECK = 1
 MAX_BLOCK = 160
@@ -107,6 +107,8 @@ def lib():
             L.isvd_orthonormalize.argtypes = [P, P, I64, I32, I64, P, P, P]
             L.isvd_small_svd.argtypes = [P, P, I32, P, P, P, P, P]
             L.isvd_closed_form.argtypes = [P, P, I64, P, P, I64, I32, P, I64, I32, C.c_double, P, I64, P]
+            L.isvd_embed.argtypes = [P, I64, I64, I32, P, P, I64, P]
+            L.isvd_pair_scores.argtypes = [P, I64, I64, P, I64, I64, I32, P, P, I64, P, P, P]
             L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
             L.isvd_autotune.argtypes = [P, I32, C.c_int, C.c_char_p, P, P]
             L.isvd_selftest_wait.argtypes = [I32, P, P]
@@ -120,7 +122,8 @@ def lib():
             L.isvd_last_error.restype = C.c_char_p
             for name in ("isvd_create_operator", "isvd_operator_shape", "isvd_apply", "isvd_apply_T", "isvd_svd",
                          "isvd_gaussian", "isvd_philox_words", "isvd_orthonormalize", "isvd_small_svd",
-                         "isvd_closed_form", "isvd_svd_batched", "isvd_autotune", "isvd_selftest_wait"):
+                         "isvd_closed_form", "isvd_embed", "isvd_pair_scores", "isvd_svd_batched", "isvd_autotune",
+                         "isvd_selftest_wait"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -173,7 +176,8 @@ class Operator:
 
     form='poly':   M = sum_k c_k N^k + ones_coeff 11^T + adj_coeff A + sum_t a_t u_t v_t^T  (Eq. 3)
     form='concat': M = [X | N X | ... | N^L X]                                              (Eq. 6)
-    norm='row': N = D^-1 A;  norm='sym': N = (D+I)^-1/2 (A+I) (D+I)^-1/2  (Sec. 2).
+    norm='row': N = D^-1 A;  norm='sym': N = (D+I)^-1/2 (A+I) (D+I)^-1/2  (Sec. 2);
+    norm='sym_noself': N = (D+I)^-1/2 A (D+I)^-1/2, label re-use's adjacency (Sec. 5.3).
     gather_rows: the operator is M[gather_rows, :] (Thm. 1's fit on training rows).
     Arrays may be numpy or torch; they are copied to the device and kept
     alive for the operator's lifetime."""
@@ -424,6 +428,47 @@ def closed_form(op: Operator, U: torch.Tensor, S: torch.Tensor, V: torch.Tensor,
     _check(lib().isvd_closed_form(op._handle, _ptr(U), U.stride(0), _ptr(S), _ptr(V), V.stride(0), k, _ptr(Y),
                                   Y.stride(0), m, float(rcond), _ptr(W), W.stride(0), _stream()), "isvd_closed_form")
     return W
+
+
+def embeddings(U: torch.Tensor, S: torch.Tensor, V: torch.Tensor):
+    """Network-embedding outputs of a rank-k SVD (Sec. 3.1): L = U S^1/2 and
+    R = V S^1/2 (new FP32 blocks)."""
+    for t in (U, S, V):
+        if t.dtype != torch.float32 or not t.is_cuda:
+            raise TypeError("embeddings takes FP32 CUDA tensors")
+    k = S.numel()
+    if U.dim() != 2 or V.dim() != 2 or U.shape[1] != k or V.shape[1] != k:
+        raise ValueError("U and V need k = len(S) columns")
+    S = S.contiguous()
+    outs = []
+    for X in (U, V):
+        X = _as_block(X)
+        out = new_block(X.shape[0], k, device=X.device)
+        _check(lib().isvd_embed(_ptr(X), X.stride(0), X.shape[0], k, _ptr(S), _ptr(out), out.stride(0), _stream()),
+               "isvd_embed")
+        outs.append(out)
+    return outs[0], outs[1]
+
+
+def pair_scores(Lm: torch.Tensor, Rm: torch.Tensor, src: torch.Tensor, dst: torch.Tensor,
+                info: torch.Tensor | None = None) -> torch.Tensor:
+    """f(i, j) = <L_i, R_j> for each pair (src[p], dst[p]) (Sec. 3.1).  Pairs
+    out of range score NaN and set info[0] (if given) to INVALID_ARGUMENT."""
+    for t in (Lm, Rm):
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2:
+            raise TypeError("pair_scores takes FP32 CUDA blocks")
+    if Lm.shape[1] != Rm.shape[1]:
+        raise ValueError("L and R need the same width")
+    Lm, Rm = _as_block(Lm), _as_block(Rm)
+    src = src.to(device=Lm.device, dtype=torch.int32).contiguous()
+    dst = dst.to(device=Lm.device, dtype=torch.int32).contiguous()
+    if src.shape != dst.shape or src.dim() != 1:
+        raise ValueError("src and dst must be 1-D of equal length")
+    out = torch.empty(src.numel(), dtype=torch.float32, device=Lm.device)
+    _check(lib().isvd_pair_scores(_ptr(Lm), Lm.stride(0), Lm.shape[0], _ptr(Rm), Rm.stride(0), Rm.shape[0],
+                                  Lm.shape[1], _ptr(src), _ptr(dst), src.numel(), _ptr(out),
+                                  _ptr(info) if info is not None else None, _stream()), "isvd_pair_scores")
+    return out
 
 
 class Batch:

@@ -75,3 +75,24 @@ def test_orthonormalize_noalloc_rejects_bad_layouts_on_the_host(libisvd):
     assert fn(C.c_void_p((1 << 20) + 4), 100, 8, 8, None, None, None) == 1  # base not 16-byte aligned
     assert fn(fake, 100, 8, 4, None, None, None) == 1  # pitch below the width
     assert fn(fake, 4, 8, 8, None, None, None) == 3  # fewer rows than columns: ISVD_ERR_SHAPE
+
+
+def test_embed_and_pair_scores_reject_bad_arguments_on_the_host(libisvd):
+    # argument checks of the Sec. 3.1 outputs run before any launch (no GPU here)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    emb = libisvd.isvd_embed
+    emb.argtypes = [P, I64, I64, I32, P, P, I64, P]
+    emb.restype = C.c_int
+    ps = libisvd.isvd_pair_scores
+    ps.argtypes = [P, I64, I64, P, I64, I64, I32, P, P, I64, P, P, P]
+    ps.restype = C.c_int
+    fake = C.c_void_p(1 << 20)  # never dereferenced
+    assert emb(None, 8, 10, 8, fake, fake, 8, None) == 1
+    assert emb(fake, 8, 10, 0, fake, fake, 8, None) == 3  # k < 1: ISVD_ERR_SHAPE
+    assert emb(fake, 4, 10, 8, fake, fake, 8, None) == 1  # ld below k
+    assert emb(fake, 8, -1, 8, fake, fake, 8, None) == 1
+    assert ps(fake, 8, 10, fake, 8, 10, 8, fake, fake, -1, fake, None, None) == 1
+    assert ps(None, 8, 10, None, 8, 10, 8, None, None, 0, None, None, None) == 0  # no pairs: nothing to do
+    assert ps(fake, 8, 10, None, 8, 10, 8, fake, fake, 5, fake, None, None) == 1
+    assert ps(fake, 8, 10, fake, 8, 10, 0, fake, fake, 5, fake, None, None) == 3
+    assert ps(fake, 8, 10, fake, 4, 10, 8, fake, fake, 5, fake, None, None) == 1
