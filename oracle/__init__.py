@@ -52,6 +52,7 @@ class _Op(C.Structure):
         ("xdense", C.c_void_p),
         ("lr_rank", C.c_int32), ("lr_u", C.c_void_p), ("lr_v", C.c_void_p), ("lr_alpha", C.c_void_p),
         ("grows", C.c_void_p), ("ngather", C.c_int64),
+        ("kind", C.c_int32), ("nchild", C.c_int32), ("child", C.c_void_p), ("weight", C.c_void_p),
     ]
 
 
@@ -179,6 +180,43 @@ class Operator:
         if rc != 0:
             raise RuntimeError(f"oracle isvd failed ({rc})")
         return U, S, V, int(info[0])
+
+
+# composite nodes (Sec. 4, App. A.3)
+COMPOSE = {"sum": 1, "hcat": 2, "vcat": 3, "product": 4}
+
+
+def compose(kind: str, ops, weights=None) -> Operator:
+    """Composite operator: ``'sum'`` sum_i w_i M_i (``weights``, default all
+    ones), ``'hcat'`` [M_1 | M_2 | ...], ``'vcat'`` [M_1 ; M_2 ; ...],
+    ``'product'`` M_1 M_2 ... (Sec. 4).  The children stay referenced."""
+    ops = list(ops)
+    if not ops:
+        raise ValueError("compose needs at least one operator")
+    op = Operator.__new__(Operator)
+    op._keep = list(ops)
+    s = _Op()
+    s.kind = COMPOSE[kind]
+    s.nchild = len(ops)
+    arr = (C.c_void_p * len(ops))(*[o._ptr for o in ops])
+    op._keep.append(arr)
+    s.child = C.cast(arr, C.c_void_p)
+    if weights is not None:
+        w = _f64(np.asarray(weights, dtype=np.float64).reshape(-1))
+        if len(w) != len(ops):
+            raise ValueError("one weight per operator")
+        op._keep.append(w)
+        s.weight = _p(w)
+    op.s = s
+    op.form = "composite"
+    op.norm = None
+    rows = [o.shape for o in ops]
+    ok = {"sum": all(r == rows[0] for r in rows), "hcat": all(r[0] == rows[0][0] for r in rows),
+          "vcat": all(r[1] == rows[0][1] for r in rows),
+          "product": all(rows[i][1] == rows[i + 1][0] for i in range(len(rows) - 1))}[kind]
+    if not ok:
+        raise ValueError(f"shapes {rows} do not fit a {kind} node")
+    return op
 
 
 def graph_operator(g, **kw) -> Operator:

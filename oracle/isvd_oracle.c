@@ -22,6 +22,9 @@
  *   - M_NC = [X | ÂX | ... | Â^L X]                               (Sec. 3.2, Eq. 6)
  *   - products M G and M^T G from those expressions                (Sec. 4; App. A.3),
  *     also of a row selection M[rows, :] (the training rows of Thm. 1's fit)
+ *   - composite nodes: weighted sums, side-by-side and stacked
+ *     concatenations and products of operators                     (Sec. 4, App. A.3;
+ *     label re-use and pseudo-dropout of Sec. 5.3 are built from them)
  *   - orthonormOurs: L = chol(Q^T Q), Q <- Q (L^-1)^T              (Alg. 2, right)
  *     applied twice (CholeskyQR2) with a shift on breakdown
  *   - orthonormHalko: Householder QR                               (Alg. 2, left)
@@ -47,7 +50,7 @@
 /* Operator description                                                      */
 /* ------------------------------------------------------------------------ */
 
-typedef struct {
+typedef struct orc_op_s {
   int32_t form;        /* 0: polynomial  sum_k c_k N^k ; 1: concatenation     */
   int32_t norm;        /* 0: N = T = D^-1 A ; 1: N = Â ; 2: N = Â - (D+I)^-1    */
   int64_t n;           /* nodes                                                */
@@ -67,6 +70,14 @@ typedef struct {
   const int32_t *grows; /* row gather M[grows, :] (the training rows of Thm. 1's
                            fit), NULL = all rows                             */
   int64_t ngather;
+  /* Composite nodes of the symbolic representation (Sec. 4, App. A.3): kind
+   * 0 is a leaf (the fields above); 1: sum_i w_i M_i ; 2: [M_1 | M_2 | ...]
+   * (columns side by side, equal row counts) ; 3: [M_1 ; M_2 ; ...] (rows
+   * stacked, equal column counts) ; 4: the product M_1 M_2 ... M_m.         */
+  int32_t kind;
+  int32_t nchild;
+  const struct orc_op_s *const *child;
+  const double *weight; /* kind 1: w_i, NULL = all ones                       */
 } orc_op;
 
 static double a_val(const orc_op *op, int64_t e) { return op->aval ? op->aval[e] : 1.0; }
@@ -81,8 +92,27 @@ static void degrees(const orc_op *op, double *deg) {
 }
 
 static int64_t full_rows(const orc_op *op) { return op->n; }
-int64_t orc_rows(const orc_op *op) { return op->grows ? op->ngather : full_rows(op); }
-int64_t orc_cols(const orc_op *op) { return op->form == 0 ? op->n : op->d * (op->L + 1); }
+
+int64_t orc_rows(const orc_op *op) {
+  if (op->kind == 0) return op->grows ? op->ngather : full_rows(op);
+  if (op->kind == 3) {
+    int64_t r = 0;
+    for (int i = 0; i < op->nchild; ++i) r += orc_rows(op->child[i]);
+    return r;
+  }
+  return orc_rows(op->child[0]); /* sum, side by side, product: the first factor's rows */
+}
+
+int64_t orc_cols(const orc_op *op) {
+  if (op->kind == 0) return op->form == 0 ? op->n : op->d * (op->L + 1);
+  if (op->kind == 2) {
+    int64_t c = 0;
+    for (int i = 0; i < op->nchild; ++i) c += orc_cols(op->child[i]);
+    return c;
+  }
+  if (op->kind == 4) return orc_cols(op->child[op->nchild - 1]);
+  return orc_cols(op->child[0]);
+}
 
 /* ------------------------------------------------------------------------ */
 /* Leaf products                                                             */
@@ -271,9 +301,12 @@ static int apply_full(const orc_op *op, const double *G, int64_t b, double *out,
   return 0;
 }
 
+static int composite_apply(const orc_op *op, const double *G, int64_t b, double *out, int transpose);
+
 /* With a row gather S (rows grows of the identity): (S M) G = S (M G) and
  * (S M)^T H = M^T (S^T H), S^T H placing row i of H at row grows[i]. */
 int orc_apply(const orc_op *op, const double *G, int64_t b, double *out, int transpose) {
+  if (op->kind != 0) return composite_apply(op, G, b, out, transpose);
   if (!op->grows) return apply_full(op, G, b, out, transpose);
   const int64_t nf = full_rows(op);
   double *F = (double *)calloc((size_t)(nf * b), sizeof(double));
@@ -291,10 +324,119 @@ int orc_apply(const orc_op *op, const double *G, int64_t b, double *out, int tra
   return rc;
 }
 
+/* Products of a composite node from its children's products:
+ *   (sum_i w_i M_i) G = sum_i w_i (M_i G), and the same for the transpose;
+ *   [M_1 | ... | M_m] G = sum_i M_i G_i, G_i the rows of G that meet M_i's
+ *     columns;  [M_1 | ... | M_m]^T H = [M_1^T H ; ... ; M_m^T H];
+ *   [M_1 ; ... ; M_m] G = [M_1 G ; ... ; M_m G];  [M_1 ; ... ; M_m]^T H =
+ *     sum_i M_i^T H_i, H_i the rows of H that meet M_i's rows;
+ *   (M_1 ... M_m) G = M_1 (... (M_m G));  (M_1 ... M_m)^T H = M_m^T (... (M_1^T H)). */
+static int composite_apply(const orc_op *op, const double *G, int64_t b, double *out, int transpose) {
+  const int64_t rout = transpose ? orc_cols(op) : orc_rows(op);
+  const int m = op->nchild;
+  int rc = 0;
+  if (op->kind == 1 || (op->kind == 2 && !transpose) || (op->kind == 3 && transpose)) {
+    double *T = (double *)malloc(sizeof(double) * (rout > 0 ? rout : 1) * b);
+    memset(out, 0, sizeof(double) * rout * b);
+    int64_t off = 0; /* first row of G_i (side by side / stacked) */
+    for (int i = 0; i < m; ++i) {
+      const orc_op *ci = op->child[i];
+      const double *Gi = op->kind == 1 ? G : G + off * b;
+      rc |= orc_apply(ci, Gi, b, T, transpose);
+      const double w = (op->kind == 1 && op->weight) ? op->weight[i] : 1.0;
+      for (int64_t x = 0; x < rout * b; ++x) out[x] += w * T[x];
+      off += op->kind == 2 ? orc_cols(ci) : orc_rows(ci);
+    }
+    free(T);
+  } else if (op->kind == 2 || op->kind == 3) {
+    int64_t off = 0; /* first row of child i's block of the output */
+    for (int i = 0; i < m; ++i) {
+      const orc_op *ci = op->child[i];
+      rc |= orc_apply(ci, G, b, out + off * b, transpose);
+      off += op->kind == 2 ? orc_cols(ci) : orc_rows(ci);
+    }
+  } else if (op->kind == 4) {
+    const double *cur = G;
+    double *prev = NULL;
+    for (int step = 0; step < m; ++step) {
+      const orc_op *ci = op->child[transpose ? step : m - 1 - step];
+      const int64_t ro = transpose ? orc_cols(ci) : orc_rows(ci);
+      double *dst = step == m - 1 ? out : (double *)malloc(sizeof(double) * (ro > 0 ? ro : 1) * b);
+      rc |= orc_apply(ci, cur, b, dst, transpose);
+      free(prev);
+      prev = step == m - 1 ? NULL : dst;
+      cur = dst;
+    }
+  } else {
+    rc = -1;
+  }
+  return rc;
+}
+
 static int explicit_full(const orc_op *op, double *M);
+int orc_explicit(const orc_op *op, double *M);
+
+/* Dense composite: the children's dense matrices combined by the node's
+ * definition (weighted sum, placement side by side or stacked, product). */
+static int composite_explicit(const orc_op *op, double *M) {
+  const int64_t r = orc_rows(op), c = orc_cols(op);
+  const int m = op->nchild;
+  int rc = 0;
+  if (op->kind == 1) {
+    memset(M, 0, sizeof(double) * r * c);
+    double *E = (double *)malloc(sizeof(double) * r * c);
+    for (int i = 0; i < m; ++i) {
+      rc |= orc_explicit(op->child[i], E);
+      const double w = op->weight ? op->weight[i] : 1.0;
+      for (int64_t x = 0; x < r * c; ++x) M[x] += w * E[x];
+    }
+    free(E);
+  } else if (op->kind == 2) {
+    int64_t off = 0; /* first column of child i */
+    for (int i = 0; i < m; ++i) {
+      const int64_t ci = orc_cols(op->child[i]);
+      double *E = (double *)malloc(sizeof(double) * r * ci);
+      rc |= orc_explicit(op->child[i], E);
+      for (int64_t a = 0; a < r; ++a)
+        for (int64_t j = 0; j < ci; ++j) M[a * c + off + j] = E[a * ci + j];
+      free(E);
+      off += ci;
+    }
+  } else if (op->kind == 3) {
+    int64_t off = 0; /* first row of child i */
+    for (int i = 0; i < m; ++i) {
+      rc |= orc_explicit(op->child[i], M + off * c);
+      off += orc_rows(op->child[i]);
+    }
+  } else if (op->kind == 4) {
+    /* P <- P E_i, left to right */
+    int64_t pc = orc_cols(op->child[0]);
+    double *P = (double *)malloc(sizeof(double) * r * pc);
+    rc |= orc_explicit(op->child[0], P);
+    for (int i = 1; i < m; ++i) {
+      const int64_t ec = orc_cols(op->child[i]);
+      double *E = (double *)malloc(sizeof(double) * pc * ec);
+      rc |= orc_explicit(op->child[i], E);
+      double *Pn = (double *)calloc((size_t)(r * ec), sizeof(double));
+      for (int64_t a = 0; a < r; ++a)
+        for (int64_t t = 0; t < pc; ++t)
+          for (int64_t j = 0; j < ec; ++j) Pn[a * ec + j] += P[a * pc + t] * E[t * ec + j];
+      free(E);
+      free(P);
+      P = Pn;
+      pc = ec;
+    }
+    memcpy(M, P, sizeof(double) * r * c);
+    free(P);
+  } else {
+    rc = -1;
+  }
+  return rc;
+}
 
 /* Dense M (rows x cols, row-major) built from its definition, tiny sizes. */
 int orc_explicit(const orc_op *op, double *M) {
+  if (op->kind != 0) return composite_explicit(op, M);
   if (!op->grows) return explicit_full(op, M);
   const int64_t nf = full_rows(op), c = orc_cols(op);
   double *F = (double *)malloc(sizeof(double) * nf * c);

@@ -561,3 +561,118 @@ def test_pair_scores_recover_entries_at_full_rank():
     f = oracle.pair_scores(Lm, Rm, src, dst)
     assert np.allclose(f, M[src, dst], rtol=0, atol=1e-12)
     assert not np.allclose(oracle.pair_scores(Lm, Rm, dst, src), M[src, dst], rtol=0, atol=1e-6)
+
+
+# ---- composite nodes (Sec. 4, App. A.3; Sec. 5.3's add-ons) ------------------------
+
+C2 = np.array([0.3, -0.2])
+
+
+@pytest.mark.parametrize("kind", ["sum", "hcat", "vcat", "product"])
+def test_composite_cycle_spectra(kind):
+    # on C_n, T = A/2 is symmetric with eigenvalues mu_j = cos(2 pi j/n) and
+    # p(T), q(T) share its eigenvectors: sum -> |w1 p + w2 q|; [P | Q] and
+    # [P ; Q] -> sqrt(p^2 + q^2); P Q -> |p q|
+    n = 11
+    g = synth.cycle(n)
+    P = oracle.graph_operator(g, coeffs=C5)
+    Q = oracle.graph_operator(g, coeffs=C2)
+    mu = np.cos(2 * np.pi * np.arange(n) / n)
+    p, q = poly(C5, mu), poly(C2, mu)
+    w = (1.5, -0.7)
+    want = {"sum": np.abs(w[0] * p + w[1] * q), "hcat": np.hypot(p, q), "vcat": np.hypot(p, q),
+            "product": np.abs(p * q)}[kind]
+    op = oracle.compose(kind, [P, Q], w if kind == "sum" else None)
+    _, S, _ = oracle.svd_any(op.explicit())
+    assert np.allclose(S[:n], np.sort(want)[::-1], rtol=1e-12, atol=1e-14)
+
+
+def _mixed_children(g, seed):
+    x = synth.tfidf_features(g.n, 11, 0.2, seed)
+    X = (x.d, x.rowptr, x.colidx, x.values)
+    a = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+    b = oracle.graph_operator(g, norm="sym", coeffs=C2, adj_coeff=0.1)
+    c = oracle.graph_operator(g, form="concat", norm="sym", X=X, L=2)
+    d = oracle.graph_operator(g, form="concat", norm="sym_noself", X=X, L=1)
+    return a, b, c, d
+
+
+def test_composite_explicit_is_the_block_arrangement():
+    # the C recursion against numpy's own stacking and matmul of the children
+    g = _irregular(70, 300, 50)
+    a, b, c, d = _mixed_children(g, 51)
+    A, B, Cm, Dm = (o.explicit() for o in (a, b, c, d))
+    assert np.allclose(oracle.compose("sum", [a, b], [2.0, -3.0]).explicit(), 2 * A - 3 * B, rtol=0, atol=1e-15)
+    assert np.array_equal(oracle.compose("hcat", [a, c, d]).explicit(), np.hstack([A, Cm, Dm]))
+    assert np.array_equal(oracle.compose("vcat", [a, b]).explicit(), np.vstack([A, B]))
+    assert np.allclose(oracle.compose("product", [a, b, c]).explicit(), A @ B @ Cm, rtol=1e-13, atol=1e-15)
+    nested = oracle.compose("hcat", [oracle.compose("sum", [a, b]), oracle.compose("product", [b, c])])
+    assert np.allclose(nested.explicit(), np.hstack([A + B, B @ Cm]), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", ["sum", "hcat", "vcat", "product", "nested"])
+def test_composite_products_match_explicit(kind):
+    g = _irregular(90, 400, 52)
+    a, b, c, d = _mixed_children(g, 53)
+    op = {"sum": lambda: oracle.compose("sum", [a, b], [0.5, 2.0]),
+          "hcat": lambda: oracle.compose("hcat", [a, c, d]),
+          "vcat": lambda: oracle.compose("vcat", [c, oracle.compose("product", [b, c])]),
+          "product": lambda: oracle.compose("product", [a, b, d]),
+          "nested": lambda: oracle.compose("vcat", [oracle.compose("hcat", [a, c]), oracle.compose("hcat", [b, c])]),
+          }[kind]()
+    M = op.explicit()
+    assert op.shape == M.shape
+    rng = np.random.default_rng(54)
+    G = rng.standard_normal((M.shape[1], 4))
+    H = rng.standard_normal((M.shape[0], 4))
+    assert np.allclose(op.apply(G), M @ G, rtol=1e-12, atol=1e-12)
+    assert np.allclose(op.apply(H, transpose=True), M.T @ H, rtol=1e-12, atol=1e-12)
+    lhs, rhs = np.sum(op.apply(G) * H), np.sum(G * op.apply(H, transpose=True))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1)
+
+
+def test_composite_shapes_are_checked():
+    g = _irregular(40, 160, 55)
+    a, _, c, _ = _mixed_children(g, 56)
+    for kind in ("sum", "vcat"):
+        with pytest.raises(ValueError):
+            oracle.compose(kind, [a, c])
+    with pytest.raises(ValueError):
+        oracle.compose("product", [c, a])  # 33 columns against n rows
+    assert oracle.compose("hcat", [a, c]).shape == (g.n, g.n + c.shape[1])
+    assert oracle.compose("product", [a, c]).shape == c.shape
+
+
+def test_label_reuse_design_matrix():
+    # Sec. 5.3: M_LR = [X | ÂX | Â^2 X | N0 Y | N0^2 Y], N0 = Â - (D+I)^-1, as
+    # a side-by-side node whose second child is the product N0 [Y | N0 Y]
+    g = synth.chung_lu(120, 500, 57, isolated_self_loops=False)
+    X = np.random.default_rng(58).standard_normal((g.n, 6))
+    y, mask = synth.labels(g.n, 4, 0.4, 59)
+    Y = np.zeros((g.n, 4))
+    Y[mask, y[mask]] = 1.0
+    nc = oracle.graph_operator(g, form="concat", norm="sym", X=X, L=2)
+    n0 = oracle.graph_operator(g, norm="sym_noself", coeffs=[1.0])
+    lr = oracle.compose("hcat", [nc, oracle.compose("product", [n0, oracle.graph_operator(
+        g, form="concat", norm="sym_noself", X=Y, L=1)])])
+    N0 = n0.explicit()
+    Ah = oracle.graph_operator(g, norm="sym", coeffs=[1.0]).explicit()
+    want = np.hstack([X, Ah @ X, Ah @ Ah @ X, N0 @ Y, N0 @ N0 @ Y])
+    assert np.allclose(lr.explicit(), want, rtol=1e-13, atol=1e-15)
+    Sr = np.linalg.svd(want, compute_uv=False)
+    k = int(np.argmax(-np.diff(Sr[:8]))) + 1
+    _, S, _, _ = lr.isvd(k, 6, 10, 60)
+    assert np.allclose(S, Sr[:k], rtol=1e-8)
+
+
+def test_pseudo_dropout_rows_keep_the_width():
+    # Sec. 5.3: [M ; PD(M)] has M's column count (the model keeps its
+    # parameters); here PD drops feature entries of X at random
+    g = _irregular(80, 320, 61)
+    X = np.random.default_rng(62).standard_normal((g.n, 5))
+    Xd = X * (np.random.default_rng(63).random(X.shape) >= 0.5) / 0.5
+    m = oracle.graph_operator(g, form="concat", norm="sym", X=X, L=2)
+    pd = oracle.graph_operator(g, form="concat", norm="sym", X=Xd, L=2)
+    op = oracle.compose("vcat", [m, pd])
+    assert op.shape == (2 * g.n, m.shape[1])
+    assert np.array_equal(op.explicit(), np.vstack([m.explicit(), pd.explicit()]))
