@@ -270,6 +270,38 @@ ISVD_API isvd_status isvd_closed_form(isvd_operator *op, const float *U, int64_t
                                       int64_t ldv, int32_t k, const float *Y, int64_t ldy, int32_t m, double rcond,
                                       float *W, int64_t ldw, void *stream);
 
+/* Composite nodes of the symbolic representation (Sec. 4, App. A.3):
+ *   SUM      M = sum_i w_i M_i          (all children of one shape)
+ *   HCAT     M = [M_1 | M_2 | ...]      (columns side by side; equal row counts)
+ *   VCAT     M = [M_1 ; M_2 ; ...]      (rows stacked; equal column counts)
+ *   PRODUCT  M = M_1 M_2 ... M_m        (cols(M_i) == rows(M_{i+1}))
+ * Label re-use (Sec. 5.3) is HCAT(M_NC, PRODUCT(N0, [Y | N0 Y])) with N0 =
+ * ISVD_NORM_SYM_NOSELF; pseudo-dropout is VCAT(M, PD(M)). */
+typedef enum {
+  ISVD_COMPOSE_SUM = 0,
+  ISVD_COMPOSE_HCAT = 1,
+  ISVD_COMPOSE_VCAT = 2,
+  ISVD_COMPOSE_PRODUCT = 3
+} isvd_compose;
+
+#define ISVD_MAX_CHILDREN 16
+
+/* Build a composite operator over `count` (1..ISVD_MAX_CHILDREN) existing
+ * operators, leaves or composites.  The children are referenced, not
+ * copied or owned: they must outlive the composite and keep their tuning
+ * (a change of a child's tuning or workspace is picked up at the next call).
+ * weights: HOST, SUM only (count values, finite; NULL = all ones); must be
+ * NULL for the other kinds.  The result works with isvd_apply, isvd_apply_T,
+ * isvd_svd, isvd_closed_form, isvd_orthonormalize; products are formed from
+ * the children's products in child order (sums and accumulations of the
+ * concatenations through one extra block pass each).  Not accepted by
+ * isvd_svd_batched, isvd_set_tuning or isvd_autotune (UNSUPPORTED): tune the
+ * children.  Errors: INVALID_ARGUMENT (null pointers, bad count or
+ * weights), SHAPE (children that do not fit the kind), CUDA. */
+ISVD_API isvd_status isvd_compose_operators(isvd_compose kind, isvd_operator *const *ops, int32_t count,
+                                            const double *weights, const isvd_allocator *alloc, void *stream,
+                                            isvd_operator **out);
+
 /* Network-embedding outputs of a rank-k SVD (Sec. 3.1): the rows and columns
  * of M are embedded as L = U diag(S)^1/2 and R = V diag(S)^1/2, so that
  * L R^T = U diag(S) V^T.  One call scales one factor: out = X diag(S)^1/2.

@@ -103,6 +103,7 @@ isvd_status isvd_selftest_wait(int32_t spin_limit, isvd_info *dev_info, void *st
 isvd_status isvd_autotune(isvd_operator *op, int32_t b, isvd_dtype dtype, const char *cache_path, isvd_tuning *out,
                           void *stream) {
   if (!op) return fail(ISVD_ERR_INVALID_ARGUMENT, "null operator");
+  if (op->compose >= 0) return fail(ISVD_ERR_UNSUPPORTED, "a composite operator has no launch shapes: tune its children");
   if (b < 1 || b > ISVD_MAX_BLOCK) return fail(ISVD_ERR_INVALID_ARGUMENT, "block width must be in 1..%d", ISVD_MAX_BLOCK);
   if (dtype != ISVD_F32 && dtype != ISVD_BF16) return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown dtype");
   cudaStream_t s = (cudaStream_t)stream;

@@ -303,6 +303,11 @@ struct isvd_operator {
   int64_t last_kernel_nodes = -1;
   uint64_t serial = 0;      // unique per operator in the process
   uint64_t generation = 0;  // bumped whenever captured graphs become stale
+  // composite node (Sec. 4): compose >= 0 is an isvd_compose kind over the
+  // referenced children; -1 is a leaf described by desc
+  int32_t compose = -1;
+  std::vector<isvd_operator *> child;
+  std::vector<double> weight;
 };
 
 namespace isvd {
@@ -324,7 +329,13 @@ struct ApplyScratch {
   float *heavy_partial = nullptr;
   void *xdense = nullptr;  // dense-X products (CONCAT with dense X)
   void *gz = nullptr;      // row gather: the full-height product (n x b)
+  // composite nodes: two block temporaries and the children's scratch
+  void *ct1 = nullptr, *ct2 = nullptr;
+  char *child_base = nullptr;
 };
+// Generation of an operator and everything below it (composite graphs go
+// stale when a child's workspace or launch shapes change).
+uint64_t tree_generation(const isvd_operator *op);
 size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool transpose);
 void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool transpose, char *base,
                          ApplyScratch *sc);

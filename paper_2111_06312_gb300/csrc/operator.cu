@@ -105,6 +105,25 @@ __global__ void gather_rows_kernel(const T *src, int64_t lds, const int32_t *idx
   }
 }
 
+__device__ __forceinline__ float blk_load(const float *p) { return *p; }
+__device__ __forceinline__ float blk_load(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void blk_store(float *p, float v) { *p = v; }
+__device__ __forceinline__ void blk_store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+// y = w x (first) or y + w x over a rows x b block, in FP32 (x may be y).
+template <typename T>
+__global__ void axpy_block_kernel(const T *x, int64_t ldx, T *y, int64_t ldy, int64_t rows, int32_t b, float w,
+                                  int32_t first) {
+  const int64_t total = rows * b;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t i = e / b, c = e - i * b;
+    const float xv = w * blk_load(x + i * ldx + c);
+    T *py = y + i * ldy + c;
+    blk_store(py, first ? xv : blk_load(py) + xv);
+  }
+}
+
 __global__ void validate_csr_kernel(int64_t rows, int64_t cols, int64_t nnz, const int32_t *rowptr,
                                     const int32_t *colidx, const float *values, int32_t *flags) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -740,10 +759,24 @@ int64_t partial_rows(const isvd_operator *op) {
 
 }  // namespace
 
+// Rows of a composite's two block temporaries: the node's own rows and
+// columns and those of each child (the intermediates of a product).
+static int64_t composite_span(const isvd_operator *op) {
+  int64_t m = std::max(op->rows, op->cols);
+  for (const isvd_operator *c : op->child) m = std::max(m, std::max(c->rows, c->cols));
+  return m;
+}
+
 size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool transpose) {
-  (void)transpose;
   const size_t es = dtype_size(dtype);
   const int64_t bseg = round_up(b, 8);
+  if (op->compose >= 0) {
+    // two temporaries, then one region the children use in turn
+    const size_t t = (size_t)round_up((int64_t)(es * composite_span(op) * bseg), 256);
+    size_t cmax = 0;
+    for (const isvd_operator *c : op->child) cmax = std::max(cmax, apply_scratch_bytes(c, b, dtype, transpose));
+    return 2 * t + cmax;
+  }
   size_t total = 0;
   auto add = [&](size_t x) { total += (size_t)round_up((int64_t)x, 256); };
   add(es * op->n * bseg);  // z1
@@ -769,6 +802,13 @@ void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool tra
   (void)transpose;
   const size_t es = dtype_size(dtype);
   const int64_t bseg = round_up(b, 8);
+  if (op->compose >= 0) {
+    const size_t t = (size_t)round_up((int64_t)(es * composite_span(op) * bseg), 256);
+    sc->ct1 = base;
+    sc->ct2 = base + t;
+    sc->child_base = base + 2 * t;
+    return;
+  }
   size_t off = 0;
   auto take = [&](size_t x) {
     char *p = base + off;
@@ -1010,9 +1050,92 @@ static cudaError_t gather_launch(const void *src, int64_t lds, const int32_t *id
   return cudaGetLastError();
 }
 
+static cudaError_t axpy_launch(const void *x, int64_t ldx, void *y, int64_t ldy, int64_t rows, int32_t b, double w,
+                               bool first, int dtype, cudaStream_t s) {
+  if (rows * b == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(rows * b, 256), kNumSMs * 16);
+  if (dtype == DT_F32)
+    axpy_block_kernel<float><<<grid, 256, 0, s>>>((const float *)x, ldx, (float *)y, ldy, rows, b, (float)w,
+                                                  first ? 1 : 0);
+  else
+    axpy_block_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)x, ldx, (__nv_bfloat16 *)y, ldy,
+                                                          rows, b, (float)w, first ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Products of a composite node from its children's (Sec. 4, App. A.3):
+//   (sum_i w_i M_i) G = sum_i w_i (M_i G), and likewise for the transpose;
+//   [M_1 | ...] G = sum_i M_i G_i (G_i: the rows of G meeting M_i's columns),
+//   [M_1 | ...]^T H = [M_1^T H ; ...];  [M_1 ; ...] G = [M_1 G ; ...],
+//   [M_1 ; ...]^T H = sum_i M_i^T H_i;  (M_1 ... M_m) G = M_1 (... (M_m G)),
+//   (M_1 ... M_m)^T H = M_m^T (... (M_1^T H)).
+// Children run one after another on the stream and share one scratch region;
+// sums accumulate into `out` through one block pass per extra child.
+static isvd_status apply_composite(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
+                                   int dtype, bool transpose, const ApplyScratch &sc, cudaStream_t s) {
+  const size_t es = dtype_size(dtype);
+  const int64_t ldz = round_up(b, 8);
+  const int m = (int)op->child.size();
+  auto child_apply = [&](isvd_operator *c, const void *in, int64_t ldi, void *o, int64_t ldoo) {
+    ApplyScratch cs;
+    apply_scratch_carve(c, b, dtype, transpose, sc.child_base, &cs);
+    return apply_impl(c, in, ldi, b, o, ldoo, dtype, transpose, cs, s);
+  };
+  auto rows_at = [&](const void *p, int64_t ld, int64_t r0) { return (char *)p + (size_t)r0 * ld * es; };
+  const int64_t rows_out = transpose ? op->cols : op->rows;
+  const bool summing = op->compose == ISVD_COMPOSE_SUM || (op->compose == ISVD_COMPOSE_HCAT && !transpose) ||
+                       (op->compose == ISVD_COMPOSE_VCAT && transpose);
+  if (summing) {
+    int64_t off = 0;  // first row of G_i (concatenations)
+    for (int i = 0; i < m; ++i) {
+      isvd_operator *c = op->child[i];
+      const void *in = op->compose == ISVD_COMPOSE_SUM ? G : (const void *)rows_at(G, ldg, off);
+      const double w = op->weight[i];
+      if (i == 0) {
+        ISVD_TRY(child_apply(c, in, ldg, out, ldo));
+        if (w != 1.0) ISVD_CUDA_TRY(axpy_launch(out, ldo, out, ldo, rows_out, b, w, true, dtype, s));
+      } else {
+        ISVD_TRY(child_apply(c, in, ldg, sc.ct1, ldz));
+        ISVD_CUDA_TRY(axpy_launch(sc.ct1, ldz, out, ldo, rows_out, b, w, false, dtype, s));
+      }
+      off += op->compose == ISVD_COMPOSE_HCAT ? c->cols : c->rows;
+    }
+    return ISVD_OK;
+  }
+  if (op->compose == ISVD_COMPOSE_HCAT || op->compose == ISVD_COMPOSE_VCAT) {
+    int64_t off = 0;  // first row of child i's block of out
+    for (int i = 0; i < m; ++i) {
+      isvd_operator *c = op->child[i];
+      ISVD_TRY(child_apply(c, G, ldg, rows_at(out, ldo, off), ldo));
+      off += op->compose == ISVD_COMPOSE_HCAT ? c->cols : c->rows;
+    }
+    return ISVD_OK;
+  }
+  // product: right to left (transpose: left to right), two temporaries in turn
+  const void *cur = G;
+  int64_t ldc = ldg;
+  void *tmp[2] = {sc.ct1, sc.ct2};
+  for (int step = 0; step < m; ++step) {
+    isvd_operator *c = op->child[transpose ? step : m - 1 - step];
+    const bool last = step == m - 1;
+    void *dst = last ? out : tmp[step & 1];
+    ISVD_TRY(child_apply(c, cur, ldc, dst, last ? ldo : ldz));
+    cur = dst;
+    ldc = ldz;
+  }
+  return ISVD_OK;
+}
+
+uint64_t tree_generation(const isvd_operator *op) {
+  uint64_t g = op->generation * 0x9E3779B97F4A7C15ull + op->serial;
+  for (const isvd_operator *c : op->child) g = (g * 1000003ull) ^ tree_generation(c);
+  return g;
+}
+
 // With a row gather S: (S M) G = S (M G) and (S M)^T H = M^T (S^T H).
 isvd_status apply_impl(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo, int dtype,
                        bool transpose, const ApplyScratch &sc, cudaStream_t s) {
+  if (op->compose >= 0) return apply_composite(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
   const isvd_operator_desc &d = op->desc;
   if (!d.gather_rows) return apply_form(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
   const int64_t ldz = round_up(b, 8);
@@ -1029,6 +1152,8 @@ isvd_status apply_impl(isvd_operator *op, const void *G, int64_t ldg, int32_t b,
 }  // namespace isvd
 
 using namespace isvd;
+
+static std::atomic<uint64_t> g_next_serial{1};  // operator serials, unique in the process
 
 extern "C" {
 
@@ -1054,8 +1179,7 @@ isvd_status isvd_create_operator(const isvd_operator_desc *desc, const isvd_allo
   if (!desc || !out) return fail(ISVD_ERR_INVALID_ARGUMENT, "null descriptor or output");
   *out = nullptr;
   isvd_operator *op = new isvd_operator();
-  static std::atomic<uint64_t> next_serial{1};
-  op->serial = next_serial.fetch_add(1);
+  op->serial = g_next_serial.fetch_add(1);
   op->desc = *desc;
   if (alloc) {
     if (!alloc->alloc || !alloc->free) {
@@ -1078,6 +1202,66 @@ isvd_status isvd_create_operator(const isvd_operator_desc *desc, const isvd_allo
   // descriptor copies must not keep pointers into caller-owned host arrays
   op->desc.coeffs = nullptr;
   op->desc.lr_alpha = nullptr;
+  *out = op;
+  return ISVD_OK;
+}
+
+isvd_status isvd_compose_operators(isvd_compose kind, isvd_operator *const *ops, int32_t count,
+                                   const double *weights, const isvd_allocator *alloc, void *stream,
+                                   isvd_operator **out) {
+  if (!ops || !out) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  *out = nullptr;
+  if (kind < ISVD_COMPOSE_SUM || kind > ISVD_COMPOSE_PRODUCT)
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown composite kind %d", (int)kind);
+  if (count < 1 || count > ISVD_MAX_CHILDREN)
+    return fail(ISVD_ERR_INVALID_ARGUMENT, "count must be in 1..%d", ISVD_MAX_CHILDREN);
+  if (weights && kind != ISVD_COMPOSE_SUM) return fail(ISVD_ERR_INVALID_ARGUMENT, "weights are for SUM nodes only");
+  if (alloc && (!alloc->alloc || !alloc->free)) return fail(ISVD_ERR_INVALID_ARGUMENT, "allocator with null callbacks");
+  for (int i = 0; i < count; ++i) {
+    if (!ops[i]) return fail(ISVD_ERR_INVALID_ARGUMENT, "null operator %d", i);
+    if (weights && !std::isfinite(weights[i])) return fail(ISVD_ERR_INVALID_ARGUMENT, "weight %d is not finite", i);
+  }
+  int64_t rows = ops[0]->rows, cols = ops[0]->cols;
+  for (int i = 1; i < count; ++i) {
+    const isvd_operator *c = ops[i];
+    switch (kind) {
+      case ISVD_COMPOSE_SUM:
+        if (c->rows != rows || c->cols != cols) return fail(ISVD_ERR_SHAPE, "SUM: operator %d has another shape", i);
+        break;
+      case ISVD_COMPOSE_HCAT:
+        if (c->rows != rows) return fail(ISVD_ERR_SHAPE, "HCAT: operator %d has another row count", i);
+        cols += c->cols;
+        break;
+      case ISVD_COMPOSE_VCAT:
+        if (c->cols != cols) return fail(ISVD_ERR_SHAPE, "VCAT: operator %d has another column count", i);
+        rows += c->rows;
+        break;
+      case ISVD_COMPOSE_PRODUCT:
+        if (ops[i - 1]->cols != c->rows)
+          return fail(ISVD_ERR_SHAPE, "PRODUCT: operator %d has %lld columns, operator %d %lld rows", i - 1,
+                      (long long)ops[i - 1]->cols, i, (long long)c->rows);
+        cols = c->cols;
+        break;
+    }
+  }
+  isvd_operator *op = new isvd_operator();
+  op->serial = g_next_serial.fetch_add(1);
+  op->compose = (int32_t)kind;
+  op->child.assign(ops, ops + count);
+  op->weight = weights ? std::vector<double>(weights, weights + count) : std::vector<double>(count, 1.0);
+  op->rows = rows;
+  op->cols = cols;
+  if (alloc) {
+    op->alloc = *alloc;
+    op->has_alloc = true;
+  }
+  (void)stream;
+  const cudaError_t e = cudaStreamCreateWithFlags(&op->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    op->capture_stream = nullptr;
+    isvd_destroy_operator(op);
+    return fail(ISVD_ERR_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
+  }
   *out = op;
   return ISVD_OK;
 }
@@ -1153,6 +1337,7 @@ isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
 
 isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *stream) {
   if (!op || !t) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
+  if (op->compose >= 0) return fail(ISVD_ERR_UNSUPPORTED, "a composite operator has no launch shapes: tune its children");
   if (t->slab_cols_f32 < 4 || t->slab_cols_f32 > 256 || t->slab_cols_f32 % 4 || t->slab_cols_bf16 < 8 ||
       t->slab_cols_bf16 > 512 || t->slab_cols_bf16 % 8 || t->heavy_threshold < 32 || t->heavy_chunk < 32 ||
       t->chunk_nnz < 32 || t->chunk_nnz > (1 << 20) || t->l2_budget_mb < 1 || t->l2_budget_mb > 1024)

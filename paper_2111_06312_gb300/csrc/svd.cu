@@ -296,7 +296,7 @@ isvd_status isvd_svd(isvd_operator *op, int32_t k, int32_t oversample, int32_t i
   uint64_t key[16] = {(uint64_t)k,      (uint64_t)oversample, (uint64_t)iters,     seed,
                       (uint64_t)precision, (uint64_t)(uintptr_t)U, (uint64_t)ldu, (uint64_t)(uintptr_t)S,
                       (uint64_t)(uintptr_t)V, (uint64_t)ldv, (uint64_t)(uintptr_t)dev_info,
-                      (uint64_t)(uintptr_t)op->arena, 0, 0, 0, 0};
+                      (uint64_t)(uintptr_t)op->arena, tree_generation(op), 0, 0, 0};
   for (auto &g : op->graphs) {
     if (memcmp(g.key, key, sizeof key) == 0) {
       op->last_kernel_nodes = g.kernel_nodes;
@@ -354,6 +354,8 @@ isvd_status isvd_svd_batched(isvd_operator *const *ops, const int32_t *k, int32_
   for (int i = 0; i < count; ++i) {
     isvd_operator *op = ops[i];
     if (!op || !U[i] || !S[i] || !V[i]) return fail(ISVD_ERR_INVALID_ARGUMENT, "null pointer for problem %d", i);
+    if (op->compose >= 0)
+      return fail(ISVD_ERR_UNSUPPORTED, "problem %d: composite operators are not batched (children may be shared)", i);
     if (!seen.insert(op).second)
       return fail(ISVD_ERR_INVALID_ARGUMENT, "problem %d repeats an operator (each needs its own workspace)", i);
     const int64_t l = (int64_t)k[i] + oversample;

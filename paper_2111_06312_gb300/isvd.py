@@ -107,6 +107,7 @@ def lib():
             L.isvd_orthonormalize.argtypes = [P, P, I64, I32, I64, P, P, P]
             L.isvd_small_svd.argtypes = [P, P, I32, P, P, P, P, P]
             L.isvd_closed_form.argtypes = [P, P, I64, P, P, I64, I32, P, I64, I32, C.c_double, P, I64, P]
+            L.isvd_compose_operators.argtypes = [C.c_int, P, I32, P, P, P, P]
             L.isvd_embed.argtypes = [P, I64, I64, I32, P, P, I64, P]
             L.isvd_pair_scores.argtypes = [P, I64, I64, P, I64, I64, I32, P, P, I64, P, P, P]
             L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
@@ -122,7 +123,7 @@ def lib():
             L.isvd_last_error.restype = C.c_char_p
             for name in ("isvd_create_operator", "isvd_operator_shape", "isvd_apply", "isvd_apply_T", "isvd_svd",
                          "isvd_gaussian", "isvd_philox_words", "isvd_orthonormalize", "isvd_small_svd",
-                         "isvd_closed_form", "isvd_embed", "isvd_pair_scores", "isvd_svd_batched", "isvd_autotune",
+                         "isvd_closed_form", "isvd_compose_operators", "isvd_embed", "isvd_pair_scores", "isvd_svd_batched", "isvd_autotune",
                          "isvd_selftest_wait"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -363,6 +364,37 @@ class Operator:
 def graph_operator(g, **kw) -> Operator:
     """Operator on a ``synth.Graph`` (undirected CSR)."""
     return Operator(g.n, g.rowptr, g.colidx, **kw)
+
+
+COMPOSE = {"sum": 0, "hcat": 1, "vcat": 2, "product": 3}
+
+
+def compose(kind: str, ops, weights=None, use_torch_allocator=True) -> Operator:
+    """Composite operator (Sec. 4): ``'sum'`` sum_i w_i M_i, ``'hcat'``
+    [M_1 | M_2 | ...], ``'vcat'`` [M_1 ; M_2 ; ...], ``'product'`` M_1 M_2 ...
+    The children stay referenced by the result and must not be closed before
+    it; tune them, not the composite."""
+    ops = list(ops)
+    if not ops:
+        raise ValueError("compose needs at least one operator")
+    op = Operator.__new__(Operator)
+    op._keep = list(ops)
+    arr = (C.c_void_p * len(ops))(*[o._handle.value for o in ops])
+    w = None
+    if weights is not None:
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+        if len(w) != len(ops):
+            raise ValueError("one weight per operator")
+    op._handle = C.c_void_p()
+    alloc = C.byref(_TORCH_ALLOCATOR) if use_torch_allocator else None
+    _check(lib().isvd_compose_operators(COMPOSE[kind], arr, len(ops), w.ctypes.data if w is not None else None,
+                                        alloc, _stream(), C.byref(op._handle)), "isvd_compose_operators")
+    r, c = C.c_int64(), C.c_int64()
+    _check(lib().isvd_operator_shape(op._handle, C.byref(r), C.byref(c)), "isvd_operator_shape")
+    op.shape = (r.value, c.value)
+    op.device = ops[0].device
+    op.n = ops[0].n
+    return op
 
 
 def info_dict(info: torch.Tensor) -> dict:

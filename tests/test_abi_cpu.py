@@ -96,3 +96,21 @@ def test_embed_and_pair_scores_reject_bad_arguments_on_the_host(libisvd):
     assert ps(fake, 8, 10, None, 8, 10, 8, fake, fake, 5, fake, None, None) == 1
     assert ps(fake, 8, 10, fake, 8, 10, 0, fake, fake, 5, fake, None, None) == 3
     assert ps(fake, 8, 10, fake, 4, 10, 8, fake, fake, 5, fake, None, None) == 1
+
+
+def test_compose_rejects_bad_arguments_on_the_host(libisvd):
+    # kind, count and weight checks come before any child is read (no GPU here)
+    P, I32 = C.c_void_p, C.c_int32
+    fn = libisvd.isvd_compose_operators
+    fn.argtypes = [C.c_int, P, I32, P, P, P, P]
+    fn.restype = C.c_int
+    out = C.c_void_p()
+    one = (C.c_void_p * 1)(None)
+    assert fn(0, None, 1, None, None, None, C.byref(out)) == 1
+    assert fn(7, one, 1, None, None, None, C.byref(out)) == 1  # unknown kind
+    assert fn(0, one, 0, None, None, None, C.byref(out)) == 1  # count < 1
+    assert fn(0, one, 17, None, None, None, C.byref(out)) == 1  # count > ISVD_MAX_CHILDREN
+    w = (C.c_double * 1)(1.0)
+    assert fn(1, one, 1, C.cast(w, P), None, None, C.byref(out)) == 1  # weights on a non-SUM node
+    assert fn(0, one, 1, None, None, None, C.byref(out)) == 1  # null child
+    assert out.value is None

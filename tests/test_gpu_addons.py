@@ -153,3 +153,140 @@ def test_pair_scores_flag_out_of_range_pairs():
     isvd.pair_scores(Lm, Rm, src[[0, 4]], dst[[0, 4]], info=info)
     assert isvd.info_dict(info)["status"] == "OK"
     assert isvd.pair_scores(Lm, Rm, src[:0], dst[:0]).numel() == 0
+
+
+# ---- composite nodes (Sec. 4; label re-use and pseudo-dropout of Sec. 5.3) ------------
+
+def _children(g, seed=90):
+    """Leaves on both sides (GPU, oracle): two polynomials and two
+    concatenations with the same sparse features."""
+    x = synth.tfidf_features(g.n, 11, 0.05, seed)
+    Xg = (x.d, x.rowptr, x.colidx, x.values)
+    Xo = (x.d, x.rowptr, x.colidx, x.values.astype(np.float64))
+    specs = [dict(coeffs=C5, ones_coeff=-LAM, norm="sym"),
+             dict(norm="sym", coeffs=[0.3, -0.2], adj_coeff=0.05),
+             dict(form="concat", norm="sym", L=2),
+             dict(form="concat", norm="sym_noself", L=2)]
+    gpu, ref = [], []
+    for sp in specs:
+        if sp.get("form") == "concat":
+            gpu.append(isvd.graph_operator(g, X=Xg, **sp))
+            ref.append(oracle.graph_operator(g, X=Xo, **sp))
+        else:
+            gpu.append(isvd.graph_operator(g, **sp))
+            ref.append(oracle.graph_operator(g, **sp))
+    return gpu, ref
+
+
+def _tree(lib, kind, a, b, c, d):
+    if kind == "sum":
+        return lib.compose("sum", [a, b], [0.5, -2.0])
+    if kind == "hcat":
+        return lib.compose("hcat", [a, c, d])
+    if kind == "vcat":
+        return lib.compose("vcat", [c, lib.compose("product", [b, d])])
+    if kind == "product":
+        return lib.compose("product", [a, b, c])
+    # nested: [[A | C] ; [B | C]] + weights
+    return lib.compose("vcat", [lib.compose("hcat", [a, c]), lib.compose("hcat", [lib.compose("sum", [b, a], [1.0, 0.25]), c])])
+
+
+@pytest.fixture(scope="module")
+def children(hub_graph):
+    gpu, ref = _children(hub_graph)
+    yield gpu, ref
+    for o in gpu:
+        o.close()
+
+
+@pytest.mark.parametrize("kind", ["sum", "hcat", "vcat", "product", "nested"])
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("b", [5, 42])
+def test_composite_apply(children, kind, transpose, b):
+    gpu, ref = children
+    cg = _tree(isvd, kind, *gpu)
+    co = _tree(oracle, kind, *ref)
+    assert cg.shape == co.shape
+    r, c = cg.shape
+    G = isvd.gaussian(9, r if transpose else c, b)
+    Y = cg.apply(G, transpose=transpose)
+    Yr = co.apply(npy(G), transpose=transpose)
+    assert np.abs(npy(Y) - Yr).max() <= 1e-5 * np.abs(Yr).max()
+    cg.close()
+
+
+def test_composite_apply_bf16(children):
+    gpu, ref = children
+    cg = _tree(isvd, "nested", *gpu)
+    co = _tree(oracle, "nested", *ref)
+    G = isvd.gaussian(10, cg.shape[1], 24, dtype=torch.bfloat16)
+    Y = cg.apply(G)
+    Yr = co.apply(npy(G))
+    assert np.abs(npy(Y) - Yr).max() <= 3e-2 * np.abs(Yr).max()
+    cg.close()
+
+
+def test_label_reuse_svd(hub_graph):
+    """M_LR = [X | ÂX | Â^2 X | N0 Y | N0^2 Y] as HCAT(M_NC, PRODUCT(N0, [Y | N0 Y]))."""
+    g = hub_graph
+    x = synth.tfidf_features(g.n, 40, 0.05, 91)
+    y, mask = synth.labels(g.n, 6, 0.5, 92)
+    Y = np.zeros((g.n, 6), np.float32)
+    Y[mask, y[mask]] = 1.0
+    ncg = isvd.graph_operator(g, form="concat", norm="sym", X=(x.d, x.rowptr, x.colidx, x.values), L=2)
+    n0g = isvd.graph_operator(g, norm="sym_noself", coeffs=[1.0])
+    yg = isvd.graph_operator(g, form="concat", norm="sym_noself", X=Y, L=1)
+    lrg = isvd.compose("hcat", [ncg, isvd.compose("product", [n0g, yg])])
+    nco = oracle.graph_operator(g, form="concat", norm="sym", X=(x.d, x.rowptr, x.colidx, x.values.astype(np.float64)), L=2)
+    lro = oracle.compose("hcat", [nco, oracle.compose("product", [
+        oracle.graph_operator(g, norm="sym_noself", coeffs=[1.0]),
+        oracle.graph_operator(g, form="concat", norm="sym_noself", X=Y.astype(np.float64), L=1)])])
+    assert lrg.shape == lro.shape == (g.n, 3 * 40 + 2 * 6)
+    check_svd(lrg, lro, 16, 10, 4, 93)
+    lrg.close()
+    for o in (ncg, n0g, yg):
+        o.close()
+
+
+def test_pseudo_dropout_svd(hub_graph):
+    g = hub_graph
+    X = synth.dense_features(g.n, 24, 94)
+    Xd = (X * (np.random.default_rng(95).random(X.shape) >= 0.3) / 0.7).astype(np.float32)
+    kids = [isvd.graph_operator(g, form="concat", norm="sym", X=a, L=2) for a in (X, Xd)]
+    pdg = isvd.compose("vcat", kids)
+    pdo = oracle.compose("vcat", [oracle.graph_operator(g, form="concat", norm="sym", X=a.astype(np.float64), L=2)
+                                  for a in (X, Xd)])
+    assert pdg.shape == (2 * g.n, 72)
+    check_svd(pdg, pdo, 12, 8, 4, 96)
+    pdg.close()
+    for o in kids:
+        o.close()
+
+
+def test_composite_follows_child_tuning(children):
+    gpu, ref = children
+    cg = _tree(isvd, "hcat", *gpu)
+    _, S1, _, _ = cg.svd(8, 8, 2, 97)
+    S1 = S1.clone()
+    before = gpu[0].tuning()["kernel"]
+    gpu[0].set_tuning(kernel="ring")
+    _, S2, _, _ = cg.svd(8, 8, 2, 97)  # the cached graph holds the old launch shapes: recaptured
+    gpu[0].set_tuning(kernel=before)
+    assert torch.allclose(S1, S2, rtol=1e-5)
+    cg.close()
+
+
+def test_composite_rejections(children):
+    gpu, _ = children
+    a, b, c, d = gpu
+    for kind, ops in (("sum", [a, c]), ("vcat", [a, c]), ("product", [c, a])):
+        with pytest.raises(isvd.IsvdError, match="SHAPE"):
+            isvd.compose(kind, ops)
+    with pytest.raises(isvd.IsvdError, match="INVALID_ARGUMENT"):
+        isvd.compose("hcat", [a, c], weights=[1.0, 2.0])
+    cg = isvd.compose("sum", [a, b])
+    with pytest.raises(isvd.IsvdError, match="UNSUPPORTED"):
+        cg.set_tuning(kernel="ring")
+    with pytest.raises(isvd.IsvdError, match="UNSUPPORTED"):
+        isvd.Batch([cg], [4]).run()
+    cg.close()
