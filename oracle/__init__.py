@@ -332,6 +332,61 @@ def pair_scores(Lm, Rm, src, dst):
     return out
 
 
+# ---- Gaussian-kernel edge function (Sec. 5.1, App. A.4) ----------------------
+
+def edge_kernel_grid(lo=0.5, hi=2.0, count=301):
+    """The discretised truncation interval of App. A.4: 301 points from 0.5
+    to 2.0, step 0.005."""
+    return lo + (hi - lo) * np.arange(count, dtype=np.float64) / (count - 1)
+
+
+def edge_kernel_weights(S, mu, s_bar, grid=None):
+    """E_x[S^x] for x on the grid, weighted by softmax_x(-(x - mu)^2 exp(s_bar))
+    (App. A.4, with s_bar = log(1 / (2 s^2))), and its derivatives in mu and
+    s_bar.  Returns w, dw/dmu, dw/ds_bar (each of length k).  FP64, plain."""
+    S = np.asarray(S, dtype=np.float64)
+    x = edge_kernel_grid() if grid is None else np.asarray(grid, dtype=np.float64)
+    e = np.exp(s_bar)
+    z = -((x - mu) ** 2) * e
+    ez = np.exp(z - z.max())
+    pi = ez / ez.sum()  # softmax over the grid
+    Sx = S[None, :] ** x[:, None]  # the constant tensor {S^x}, grid x k
+    dz_mu = 2.0 * (x - mu) * e
+    dz_s = z
+    dpi_mu = pi * (dz_mu - np.dot(pi, dz_mu))  # softmax Jacobian applied to dz
+    dpi_s = pi * (dz_s - np.dot(pi, dz_s))
+    return pi @ Sx, dpi_mu @ Sx, dpi_s @ Sx
+
+
+def edge_scores(U, V, w, src, dst):
+    """f(i, j) = U_i^T diag(w) V_j for each pair (Eq. 8 with w = E_x[S^x])."""
+    U = np.asarray(U, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    out = np.empty(len(src))
+    for p, (i, j) in enumerate(zip(src, dst)):
+        out[p] = float(np.sum(U[i] * w * V[j]))
+    return out
+
+
+def edge_kernel_loss(U, S, V, mu, s_bar, pos, neg, k_neg=10.0):
+    """Eq. 9: -mean_pos log sigma(f) - k_n mean_neg log(1 - sigma(f)), and its
+    gradient in (mu, s_bar) through f = U_i^T diag(w(mu, s_bar)) V_j.
+    pos, neg: (src, dst) index arrays.  Returns (loss, dL/dmu, dL/ds_bar)."""
+    w, dw_mu, dw_s = edge_kernel_weights(S, mu, s_bar)
+    total = np.zeros(3)
+    for (src, dst), sign, scale in ((pos, 1.0, 1.0 / len(pos[0])), (neg, -1.0, k_neg / len(neg[0]))):
+        f = edge_scores(U, V, w, src, dst)
+        a = edge_scores(U, V, dw_mu, src, dst)
+        b = edge_scores(U, V, dw_s, src, dst)
+        # -log sigma(sign f) = softplus(-sign f); d/df = -sign sigma(-sign f)
+        total[0] += scale * np.sum(np.logaddexp(0.0, -sign * f))
+        g = -sign / (1.0 + np.exp(sign * f)) * scale
+        total[1] += np.sum(g * a)
+        total[2] += np.sum(g * b)
+    return total[0], total[1], total[2]
+
+
 # ---- metrics ----------------------------------------------------------------
 
 def sin_principal_angles(U_ref, U):

@@ -676,3 +676,73 @@ def test_pseudo_dropout_rows_keep_the_width():
     op = oracle.compose("vcat", [m, pd])
     assert op.shape == (2 * g.n, m.shape[1])
     assert np.array_equal(op.explicit(), np.vstack([m.explicit(), pd.explicit()]))
+
+
+# ---- Gaussian-kernel edge function (Sec. 5.1, App. A.4) --------------------------------
+
+def test_edge_kernel_grid_has_301_points():
+    x = oracle.edge_kernel_grid()
+    assert len(x) == 301 and x[0] == 0.5 and x[-1] == 2.0
+    assert np.allclose(np.diff(x), 0.005, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("mu,s", [(1.2, 0.1), (1.0, 0.07), (1.5, 0.08)])
+def test_edge_kernel_weights_match_the_truncated_normal_moment(mu, s):
+    # E[S^X] = E[exp(a X)], a = log S, for X ~ N(mu, s) truncated to [0.5, 2]:
+    # exp(a mu + a^2 s^2 / 2) (Phi(beta - a s) - Phi(alpha - a s)) / (Phi(beta) - Phi(alpha)).
+    # The 301-point sum is a rectangle rule: exact to rounding when the density
+    # is negligible at both ends of the interval (the cases here), O(h) otherwise.
+    from scipy.special import ndtr
+    S = np.array([3.0, 1.0, 0.4, 0.05, 1e-3])
+    s_bar = np.log(1.0 / (2 * s * s))
+    w, _, _ = oracle.edge_kernel_weights(S, mu, s_bar)
+    a = np.log(S)
+    al, be = (0.5 - mu) / s, (2.0 - mu) / s
+    want = np.exp(a * mu + a * a * s * s / 2) * (ndtr(be - a * s) - ndtr(al - a * s)) / (ndtr(be) - ndtr(al))
+    assert np.allclose(w, want, rtol=2e-8, atol=0)
+
+
+def test_edge_kernel_reduces_to_the_svd_score():
+    # mu = 1, s -> 0: w -> S, so f(i, j) = <U_i, V_j>_S (the no-op start of Sec. 5.1)
+    S = np.array([5.0, 2.0, 0.7, 0.01])
+    w, _, _ = oracle.edge_kernel_weights(S, 1.0, np.log(1.0 / (2 * 1e-4 ** 2)))
+    assert np.allclose(w, S, rtol=1e-12, atol=0)
+
+
+def test_edge_kernel_gradient_is_the_derivative():
+    # central differences of the loss (and of w) in mu and s_bar
+    rng = np.random.default_rng(70)
+    n, k = 60, 6
+    U = rng.standard_normal((n, k)) / 3
+    V = rng.standard_normal((n, k)) / 3
+    S = np.sort(rng.uniform(0.2, 4.0, k))[::-1]
+    pos = (rng.integers(0, n, 40), rng.integers(0, n, 40))
+    neg = (rng.integers(0, n, 90), rng.integers(0, n, 90))
+    mu, sb = 1.1, np.log(1.0 / (2 * 0.2 ** 2))
+    _, gm, gs = oracle.edge_kernel_loss(U, S, V, mu, sb, pos, neg, 10.0)
+    h = 1e-5
+    Lp = oracle.edge_kernel_loss(U, S, V, mu + h, sb, pos, neg, 10.0)[0]
+    Lm = oracle.edge_kernel_loss(U, S, V, mu - h, sb, pos, neg, 10.0)[0]
+    assert abs((Lp - Lm) / (2 * h) - gm) <= 1e-7 * (abs(gm) + 1e-3)
+    Lp = oracle.edge_kernel_loss(U, S, V, mu, sb + h, pos, neg, 10.0)[0]
+    Lm = oracle.edge_kernel_loss(U, S, V, mu, sb - h, pos, neg, 10.0)[0]
+    assert abs((Lp - Lm) / (2 * h) - gs) <= 1e-7 * (abs(gs) + 1e-3)
+    w0, dwm, dws = oracle.edge_kernel_weights(S, mu, sb)
+    wp = oracle.edge_kernel_weights(S, mu + h, sb)[0]
+    wm = oracle.edge_kernel_weights(S, mu - h, sb)[0]
+    assert np.allclose((wp - wm) / (2 * h), dwm, rtol=1e-7, atol=1e-10)
+
+
+def test_edge_kernel_loss_is_the_cross_entropy_of_the_svd_scores():
+    # at the no-op start and full rank, f = M_ij: Eq. 9 on the explicit entries
+    g = _irregular(40, 160, 71)
+    M = oracle.graph_operator(g, norm="sym", coeffs=[1.0]).explicit()
+    U, S, Vt = np.linalg.svd(M)
+    rng = np.random.default_rng(72)
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    pos = (rows[:50], g.colidx[:50])  # edges of A
+    neg = (rng.integers(0, g.n, 70), rng.integers(0, g.n, 70))
+    L, _, _ = oracle.edge_kernel_loss(U, S, Vt.T, 1.0, np.log(1.0 / (2 * 1e-4 ** 2)), pos, neg, 10.0)
+    fp, fn = M[pos], M[neg]
+    want = np.mean(-np.log(1 / (1 + np.exp(-fp)))) + 10.0 * np.mean(-np.log(1 - 1 / (1 + np.exp(-fn))))
+    assert abs(L - want) <= 1e-12 * abs(want)
