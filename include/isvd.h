@@ -325,6 +325,42 @@ ISVD_API isvd_status isvd_pair_scores(const float *L, int64_t ldl, int64_t rows,
                                       int64_t cols, int32_t k, const int32_t *src, const int32_t *dst,
                                       int64_t n_pairs, float *out, isvd_info *dev_info, void *stream);
 
+/* Gaussian-kernel edge function (Sec. 5.1, App. A.4).  With U (rows x k),
+ * S (k, >= 0) and V (cols x k) from a rank-k SVD, a pair (i, j) scores
+ *     f(i, j) = U_i^T diag(w) V_j,   w_c = sum_x pi_x S_c^x,
+ * x on the 301-point grid 0.5, 0.505, ..., 2.0 (the truncation interval
+ * [0.5, 2]) and pi = softmax_x(-(x - mu)^2 exp(s_bar)), s_bar = log(1/(2 s^2)):
+ * the expectation of S^x under N(mu, s) truncated to the interval.  mu = 1
+ * with s -> 0 gives w = S (the plain SVD score).  All factors DEVICE, FP32,
+ * row-major.  `work`: DEVICE scratch of isvd_edge_kernel_work_doubles(k)
+ * doubles, owned by the caller; calls that share it must be ordered on one
+ * stream.  Pairs out of range: NaN score (loss: NaN), and dev_info->status =
+ * ISVD_ERR_INVALID_ARGUMENT when dev_info is not NULL.  Sums are in a fixed
+ * order (bitwise repeatable).  Asynchronous on `stream`. */
+ISVD_API int64_t isvd_edge_kernel_work_doubles(int32_t k);
+
+/* w3 (DEVICE, 3k doubles, written) = [w | dw/dmu | dw/ds_bar], in FP64. */
+ISVD_API isvd_status isvd_edge_kernel_weights(const float *S, int32_t k, double mu, double s_bar, double *w3,
+                                              void *stream);
+
+/* out[p] = f(src[p], dst[p]) (FP32), src in [0, rows), dst in [0, cols). */
+ISVD_API isvd_status isvd_edge_kernel_scores(const float *U, int64_t ldu, int64_t rows, const float *V,
+                                             int64_t ldv, int64_t cols, int32_t k, const float *S, double mu,
+                                             double s_bar, const int32_t *src, const int32_t *dst, int64_t n_pairs,
+                                             float *out, double *work, int64_t work_doubles, isvd_info *dev_info,
+                                             void *stream);
+
+/* Link-prediction objective of Eq. 9 over n_pos edges (pos_src[p], pos_dst[p])
+ * and n_neg non-edges:  L = -mean_pos log sigma(f) - k_neg mean_neg
+ * log(1 - sigma(f)), and its gradient.  out (DEVICE, 3 doubles, written) =
+ * [L, dL/dmu, dL/ds_bar].  n_pos >= 1, n_neg >= 0, k_neg >= 0. */
+ISVD_API isvd_status isvd_edge_kernel_loss(const float *U, int64_t ldu, int64_t rows, const float *V, int64_t ldv,
+                                           int64_t cols, int32_t k, const float *S, double mu, double s_bar,
+                                           const int32_t *pos_src, const int32_t *pos_dst, int64_t n_pos,
+                                           const int32_t *neg_src, const int32_t *neg_dst, int64_t n_neg,
+                                           double k_neg, double *out, double *work, int64_t work_doubles,
+                                           isvd_info *dev_info, void *stream);
+
 /* SVD of a small square upper-triangular-or-dense FP64 matrix by one-sided
  * Jacobi on its transpose (the Rayleigh-Ritz step of Alg. 1, done as
  * SVD(R^T) after a QR of B^T).  A (l x l, row-major, DEVICE) = Uo diag(S) Vo^T

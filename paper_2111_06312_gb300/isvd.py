@@ -109,6 +109,13 @@ def lib():
             L.isvd_closed_form.argtypes = [P, P, I64, P, P, I64, I32, P, I64, I32, C.c_double, P, I64, P]
             L.isvd_compose_operators.argtypes = [C.c_int, P, I32, P, P, P, P]
             L.isvd_embed.argtypes = [P, I64, I64, I32, P, P, I64, P]
+            L.isvd_edge_kernel_work_doubles.argtypes = [I32]
+            L.isvd_edge_kernel_work_doubles.restype = C.c_int64
+            L.isvd_edge_kernel_weights.argtypes = [P, I32, C.c_double, C.c_double, P, P]
+            L.isvd_edge_kernel_scores.argtypes = [P, I64, I64, P, I64, I64, I32, P, C.c_double, C.c_double, P, P,
+                                                  I64, P, P, I64, P, P]
+            L.isvd_edge_kernel_loss.argtypes = [P, I64, I64, P, I64, I64, I32, P, C.c_double, C.c_double, P, P,
+                                                I64, P, P, I64, C.c_double, P, P, I64, P, P]
             L.isvd_pair_scores.argtypes = [P, I64, I64, P, I64, I64, I32, P, P, I64, P, P, P]
             L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
             L.isvd_autotune.argtypes = [P, I32, C.c_int, C.c_char_p, P, P]
@@ -123,7 +130,8 @@ def lib():
             L.isvd_last_error.restype = C.c_char_p
             for name in ("isvd_create_operator", "isvd_operator_shape", "isvd_apply", "isvd_apply_T", "isvd_svd",
                          "isvd_gaussian", "isvd_philox_words", "isvd_orthonormalize", "isvd_small_svd",
-                         "isvd_closed_form", "isvd_compose_operators", "isvd_embed", "isvd_pair_scores", "isvd_svd_batched", "isvd_autotune",
+                         "isvd_closed_form", "isvd_compose_operators", "isvd_embed", "isvd_pair_scores",
+                         "isvd_edge_kernel_weights", "isvd_edge_kernel_scores", "isvd_edge_kernel_loss", "isvd_svd_batched", "isvd_autotune",
                          "isvd_selftest_wait"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -501,6 +509,69 @@ def pair_scores(Lm: torch.Tensor, Rm: torch.Tensor, src: torch.Tensor, dst: torc
                                   Lm.shape[1], _ptr(src), _ptr(dst), src.numel(), _ptr(out),
                                   _ptr(info) if info is not None else None, _stream()), "isvd_pair_scores")
     return out
+
+
+class EdgeKernel:
+    """Gaussian-kernel edge function of Sec. 5.1 (App. A.4) on a rank-k SVD:
+    f(i, j) = U_i^T E_x[S^x] V_j with x ~ N(mu, s) truncated to [0.5, 2],
+    parameterised by (mu, s_bar = log(1/(2 s^2))).  Starts at the plain SVD
+    score (mu = 1, s -> 0) as the paper does."""
+
+    def __init__(self, U: torch.Tensor, S: torch.Tensor, V: torch.Tensor, mu: float = 1.0, s: float = 1e-3):
+        for t in (U, S, V):
+            if t.dtype != torch.float32 or not t.is_cuda:
+                raise TypeError("EdgeKernel takes FP32 CUDA tensors")
+        self.k = S.numel()
+        if U.shape[1] != self.k or V.shape[1] != self.k:
+            raise ValueError("U and V need k = len(S) columns")
+        self.U, self.V, self.S = _as_block(U), _as_block(V), S.contiguous()
+        self.mu = float(mu)
+        self.s_bar = float(np.log(1.0 / (2.0 * s * s)))
+        self.work = torch.empty(int(lib().isvd_edge_kernel_work_doubles(self.k)), dtype=torch.float64,
+                                device=U.device)
+
+    def _pairs(self, a):
+        return torch.as_tensor(a).to(device=self.U.device, dtype=torch.int32).contiguous()
+
+    def weights(self) -> torch.Tensor:
+        """(3, k) FP64: w = E_x[S^x], dw/dmu, dw/ds_bar."""
+        w3 = torch.empty((3, self.k), dtype=torch.float64, device=self.U.device)
+        _check(lib().isvd_edge_kernel_weights(_ptr(self.S), self.k, self.mu, self.s_bar, _ptr(w3), _stream()),
+               "isvd_edge_kernel_weights")
+        return w3
+
+    def scores(self, src, dst, info: torch.Tensor | None = None) -> torch.Tensor:
+        src, dst = self._pairs(src), self._pairs(dst)
+        out = torch.empty(src.numel(), dtype=torch.float32, device=self.U.device)
+        _check(lib().isvd_edge_kernel_scores(_ptr(self.U), self.U.stride(0), self.U.shape[0], _ptr(self.V),
+                                             self.V.stride(0), self.V.shape[0], self.k, _ptr(self.S), self.mu,
+                                             self.s_bar, _ptr(src), _ptr(dst), src.numel(), _ptr(out),
+                                             _ptr(self.work), self.work.numel(), _ptr(info), _stream()),
+               "isvd_edge_kernel_scores")
+        return out
+
+    def loss(self, pos, neg, k_neg: float = 10.0, info: torch.Tensor | None = None) -> torch.Tensor:
+        """Eq. 9 over edges pos = (src, dst) and non-edges neg: a (3,) FP64
+        device tensor [loss, dL/dmu, dL/ds_bar]."""
+        ps, pd = self._pairs(pos[0]), self._pairs(pos[1])
+        ns, nd = self._pairs(neg[0]), self._pairs(neg[1])
+        out = torch.empty(3, dtype=torch.float64, device=self.U.device)
+        _check(lib().isvd_edge_kernel_loss(_ptr(self.U), self.U.stride(0), self.U.shape[0], _ptr(self.V),
+                                           self.V.stride(0), self.V.shape[0], self.k, _ptr(self.S), self.mu,
+                                           self.s_bar, _ptr(ps), _ptr(pd), ps.numel(), _ptr(ns), _ptr(nd),
+                                           ns.numel(), float(k_neg), _ptr(out), _ptr(self.work), self.work.numel(),
+                                           _ptr(info), _stream()), "isvd_edge_kernel_loss")
+        return out
+
+    def fit(self, pos, neg, k_neg: float = 10.0, steps: int = 50, lr: float = 0.05) -> list:
+        """Gradient descent on (mu, s_bar) (Eq. 9); returns the loss per step."""
+        hist = []
+        for _ in range(steps):
+            L, gm, gs = self.loss(pos, neg, k_neg).tolist()
+            hist.append(L)
+            self.mu -= lr * gm
+            self.s_bar -= lr * gs
+        return hist
 
 
 class Batch:

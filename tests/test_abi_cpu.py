@@ -114,3 +114,21 @@ def test_compose_rejects_bad_arguments_on_the_host(libisvd):
     assert fn(1, one, 1, C.cast(w, P), None, None, C.byref(out)) == 1  # weights on a non-SUM node
     assert fn(0, one, 1, None, None, None, C.byref(out)) == 1  # null child
     assert out.value is None
+
+
+def test_edge_kernel_rejects_bad_arguments_on_the_host(libisvd):
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    wd = libisvd.isvd_edge_kernel_work_doubles
+    wd.argtypes = [I32]
+    wd.restype = C.c_int64
+    assert wd(0) == 0 and wd(128) > 3 * 128
+    fn = libisvd.isvd_edge_kernel_loss
+    fn.argtypes = [P, I64, I64, P, I64, I64, I32, P, D, D, P, P, I64, P, P, I64, D, P, P, I64, P, P]
+    fn.restype = C.c_int
+    f = C.c_void_p(1 << 20)  # never dereferenced
+    n = wd(8)
+    assert fn(f, 8, 10, f, 8, 10, 8, f, 1.0, 5.0, f, f, 4, f, f, 4, 10.0, f, f, n - 1, None, None) == 1  # small work
+    assert fn(f, 8, 10, f, 8, 10, 8, f, 1.0, float("nan"), f, f, 4, f, f, 4, 10.0, f, f, n, None, None) == 1
+    assert fn(f, 8, 10, f, 8, 10, 8, f, 1.0, 5.0, f, f, 0, f, f, 4, 10.0, f, f, n, None, None) == 1  # no edges
+    assert fn(f, 8, 10, f, 8, 10, 0, f, 1.0, 5.0, f, f, 4, f, f, 4, 10.0, f, f, n, None, None) == 3  # k < 1
+    assert fn(f, 8, 10, f, 8, 10, 8, f, 1.0, 5.0, f, f, 4, f, f, 4, -1.0, f, f, n, None, None) == 1  # k_neg < 0

@@ -290,3 +290,82 @@ def test_composite_rejections(children):
     with pytest.raises(isvd.IsvdError, match="UNSUPPORTED"):
         isvd.Batch([cg], [4]).run()
     cg.close()
+
+
+# ---- Gaussian-kernel edge function (Sec. 5.1, App. A.4) -------------------------------
+
+def _factors(rows, cols, k, seed):
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((rows, k)).astype(np.float32) / np.sqrt(k)
+    V = rng.standard_normal((cols, k)).astype(np.float32) / np.sqrt(k)
+    S = np.sort(rng.uniform(0.05, 6.0, k)).astype(np.float32)[::-1].copy()
+    Ug, Vg = isvd.new_block(rows, k), isvd.new_block(cols, k)
+    Ug.copy_(torch.from_numpy(U))
+    Vg.copy_(torch.from_numpy(V))
+    return U, S, V, Ug, torch.from_numpy(S).cuda(), Vg
+
+
+@pytest.mark.parametrize("k", [1, 33, 160])
+@pytest.mark.parametrize("mu,s", [(1.0, 1e-3), (1.1, 0.2), (0.7, 0.5)])
+def test_edge_kernel_weights_match_oracle(k, mu, s):
+    U, S, V, Ug, Sg, Vg = _factors(10, 10, k, 100 + k)
+    ek = isvd.EdgeKernel(Ug, Sg, Vg, mu=mu, s=s)
+    w3 = ek.weights().cpu().numpy()
+    want = oracle.edge_kernel_weights(S.astype(np.float64), mu, ek.s_bar)
+    # scale of the summed terms: S^x <= max(S)^2 on [0.5, 2]; the mu-derivative's
+    # weights grow like sqrt(exp(s_bar)) (cancelling sums need an absolute bound)
+    scale = max(1.0, float(S.max()) ** 2) * (1.0 + np.sqrt(np.exp(ek.s_bar)))
+    for got, ref in zip(w3, want):
+        assert np.allclose(got, ref, rtol=1e-11, atol=1e-13 * scale)
+
+
+def test_edge_kernel_scores_and_loss_match_oracle():
+    rows, cols, k = 3001, 2999, 72
+    U, S, V, Ug, Sg, Vg = _factors(rows, cols, k, 101)
+    rng = np.random.default_rng(102)
+    pos = (rng.integers(0, rows, 4000), rng.integers(0, cols, 4000))
+    neg = (rng.integers(0, rows, 9000), rng.integers(0, cols, 9000))
+    ek = isvd.EdgeKernel(Ug, Sg, Vg, mu=1.15, s=0.25)
+    w = oracle.edge_kernel_weights(S.astype(np.float64), ek.mu, ek.s_bar)[0]
+    f = ek.scores(*pos)
+    want = oracle.edge_scores(U, V, w, *pos)
+    bound = 1e-6 * np.sum(np.abs(U[pos[0]].astype(np.float64) * w * V[pos[1]]), axis=1) + 1e-30
+    assert np.all(np.abs(npy(f) - want) <= bound)
+    out = ek.loss(pos, neg, 10.0)
+    L, gm, gs = oracle.edge_kernel_loss(U, S, V, ek.mu, ek.s_bar, pos, neg, 10.0)
+    got = out.cpu().numpy()
+    assert abs(got[0] - L) <= 1e-6 * abs(L)
+    assert abs(got[1] - gm) <= 1e-5 * (abs(gm) + 1e-3 * abs(L))
+    assert abs(got[2] - gs) <= 1e-5 * (abs(gs) + 1e-3 * abs(L))
+    assert torch.equal(out, ek.loss(pos, neg, 10.0))
+
+
+def test_edge_kernel_flags_pairs_out_of_range():
+    U, S, V, Ug, Sg, Vg = _factors(50, 40, 8, 103)
+    ek = isvd.EdgeKernel(Ug, Sg, Vg)
+    info = torch.zeros(4, dtype=torch.int32, device="cuda")
+    f = ek.scores([0, 50, 3], [0, 1, 40], info=info)
+    assert torch.isnan(f.cpu()[1:]).all() and torch.isfinite(f.cpu()[0])
+    assert isvd.info_dict(info)["status"] == "INVALID_ARGUMENT"
+    info.zero_()
+    out = ek.loss(([0, 1], [2, 3]), ([-1], [0]), info=info)
+    assert torch.isnan(out.cpu()).all()
+    assert isvd.info_dict(info)["status"] == "INVALID_ARGUMENT"
+
+
+def test_edge_kernel_fit_lowers_the_link_loss(hub_graph):
+    """From the SVD of the NE operator, a few descent steps on (mu, s_bar)
+    lower Eq. 9 on the graph's edges against random pairs (Sec. 5.1)."""
+    g = hub_graph
+    with isvd.graph_operator(g, norm="sym", coeffs=C5, ones_coeff=-LAM) as op:
+        U, S, V, _ = op.svd(32, 10, 4, 104)
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    rng = np.random.default_rng(105)
+    e = rng.choice(len(rows), 5000, replace=False)
+    pos = (rows[e], g.colidx[e])
+    neg = (rng.integers(0, g.n, 20000), rng.integers(0, g.n, 20000))
+    ek = isvd.EdgeKernel(U, S, V)
+    hist = ek.fit(pos, neg, 10.0, steps=30, lr=0.5)
+    assert np.all(np.isfinite(hist)) and hist[-1] < hist[0]
+    L, _, _ = oracle.edge_kernel_loss(npy(U), npy(S), npy(V), ek.mu, ek.s_bar, pos, neg, 10.0)
+    assert abs(ek.loss(pos, neg, 10.0)[0].item() - L) <= 1e-5 * abs(L)
