@@ -387,6 +387,70 @@ def edge_kernel_loss(U, S, V, mu, s_bar, pos, neg, k_neg=10.0):
     return total[0], total[1], total[2]
 
 
+# ---- Split-ReLU graph network (Sec. 5.2) --------------------------------------
+
+def _relu(t):
+    return np.maximum(t, 0.0)
+
+
+def split_relu(X, Wp, Wn):
+    """SplitReLU(X; Wp, Wn) = [X Wp]_+ - [X Wn]_+ (Sec. 5.2)."""
+    return _relu(X @ Wp) - _relu(X @ Wn)
+
+
+def splitrelu_init(W_star, d, L):
+    """The initialisation of Sec. 5.2: Wp = I, Wn = -I for every message-
+    passing layer, Wop_l = W*[dl : d(l+1)], Won_l = -W*[dl : d(l+1)]."""
+    W_star = np.asarray(W_star, dtype=np.float64)
+    Wp = [np.eye(d) for _ in range(L)]
+    Wn = [-np.eye(d) for _ in range(L)]
+    Wop = [W_star[d * l:d * (l + 1)].copy() for l in range(L + 1)]
+    Won = [-W_star[d * l:d * (l + 1)] for l in range(L + 1)]
+    return Wp, Wn, Wop, Won
+
+
+def splitrelu_forward(prop, X, Wp, Wn, Wop, Won):
+    """H_0 = X; H_{l+1} = [Â H_l Wp_l]_+ - [Â H_l Wn_l]_+ (message passing);
+    output sum_{l=0..L} [H_l Wop_l]_+ - [H_l Won_l]_+ (Sec. 5.2).  prop(H) =
+    Â H.  Returns the output and the layer inputs (H_l, and P_l = Â H_l)."""
+    L = len(Wp)
+    H = [np.asarray(X, dtype=np.float64)]
+    P = []
+    for l in range(L):
+        P.append(prop(H[l]))
+        H.append(split_relu(P[l], Wp[l], Wn[l]))
+    out = sum(split_relu(H[l], Wop[l], Won[l]) for l in range(L + 1))
+    return out, (H, P)
+
+
+def splitrelu_backward(prop_T, cache, weights, dOut):
+    """Gradients of sum(out * dOut) in every weight, by the chain rule
+    through the forward pass above ([t]_+ has derivative 1 for t > 0, else 0).
+    prop_T(G) = Â^T G.  Returns dWp, dWn, dWop, dWon (lists)."""
+    H, P = cache
+    Wp, Wn, Wop, Won = weights
+    L = len(Wp)
+    dWp, dWn = [None] * L, [None] * L
+    dWop, dWon = [None] * (L + 1), [None] * (L + 1)
+    dOut = np.asarray(dOut, dtype=np.float64)
+    dH_up = None  # gradient reaching H_l from layer l + 1
+    for l in range(L, -1, -1):
+        gp = dOut * (H[l] @ Wop[l] > 0)
+        gn = dOut * (H[l] @ Won[l] > 0)
+        dWop[l] = H[l].T @ gp
+        dWon[l] = -(H[l].T @ gn)
+        dH = gp @ Wop[l].T - gn @ Won[l].T
+        if dH_up is not None:
+            dH = dH + dH_up
+        if l >= 1:
+            hp = dH * (P[l - 1] @ Wp[l - 1] > 0)
+            hn = dH * (P[l - 1] @ Wn[l - 1] > 0)
+            dWp[l - 1] = P[l - 1].T @ hp
+            dWn[l - 1] = -(P[l - 1].T @ hn)
+            dH_up = prop_T(hp @ Wp[l - 1].T - hn @ Wn[l - 1].T)
+    return dWp, dWn, dWop, dWon
+
+
 # ---- metrics ----------------------------------------------------------------
 
 def sin_principal_angles(U_ref, U):

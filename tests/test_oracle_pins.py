@@ -746,3 +746,62 @@ def test_edge_kernel_loss_is_the_cross_entropy_of_the_svd_scores():
     fp, fn = M[pos], M[neg]
     want = np.mean(-np.log(1 / (1 + np.exp(-fp)))) + 10.0 * np.mean(-np.log(1 - 1 / (1 + np.exp(-fn))))
     assert abs(L - want) <= 1e-12 * abs(want)
+
+
+# ---- Split-ReLU network (Sec. 5.2, Thm. 2) ----------------------------------------------
+
+def test_split_relu_is_linear_on_the_hyperplane():
+    rng = np.random.default_rng(80)
+    X = rng.standard_normal((30, 7))
+    W = rng.standard_normal((7, 4))
+    assert np.allclose(oracle.split_relu(X, W, -W), X @ W, rtol=0, atol=1e-14)
+    # Wn = 0: a plain ReLU layer
+    assert np.array_equal(oracle.split_relu(X, W, np.zeros_like(W)), np.maximum(X @ W, 0))
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_splitrelu_network_at_init_is_the_linear_model(L):
+    # Thm. 2: with Wp = I, Wn = -I, Wop = W*_l, Won = -W*_l the network equals
+    # [X | ÂX | ... | Â^L X] W*, the explicit design matrix of Eq. 6 times W*
+    g = _irregular(80, 320, 81)
+    d, y = 5, 3
+    rng = np.random.default_rng(82)
+    X = rng.standard_normal((g.n, d))
+    W_star = rng.standard_normal((d * (L + 1), y))
+    Ah = oracle.graph_operator(g, norm="sym", coeffs=[1.0])
+    out, _ = oracle.splitrelu_forward(Ah.apply, X, *oracle.splitrelu_init(W_star, d, L))
+    M = oracle.graph_operator(g, form="concat", norm="sym", X=X, L=L).explicit()
+    assert np.allclose(out, M @ W_star, rtol=1e-12, atol=1e-12)
+
+
+def test_splitrelu_gradients_are_the_derivative():
+    g = _irregular(40, 160, 83)
+    d, y, L = 4, 3, 2
+    rng = np.random.default_rng(84)
+    X = rng.standard_normal((g.n, d))
+    Ah = oracle.graph_operator(g, norm="sym", coeffs=[1.0])
+    prop = Ah.apply
+    prop_T = lambda G: Ah.apply(G, transpose=True)  # noqa: E731
+    Wp = [rng.standard_normal((d, d)) for _ in range(L)]
+    Wn = [rng.standard_normal((d, d)) for _ in range(L)]
+    Wop = [rng.standard_normal((d, y)) for _ in range(L + 1)]
+    Won = [rng.standard_normal((d, y)) for _ in range(L + 1)]
+    R = rng.standard_normal((g.n, y))
+    weights = (Wp, Wn, Wop, Won)
+    out, cache = oracle.splitrelu_forward(prop, X, *weights)
+    grads = oracle.splitrelu_backward(prop_T, cache, weights, R)
+
+    def loss():
+        return float(np.sum(oracle.splitrelu_forward(prop, X, *weights)[0] * R))
+
+    h = 1e-6
+    for group, ggroup in zip(weights, grads):
+        for W, dW in zip(group, ggroup):
+            for (a, b) in [(0, 0), (W.shape[0] - 1, W.shape[1] - 1), (1, 2)]:
+                old = W[a, b]
+                W[a, b] = old + h
+                lp = loss()
+                W[a, b] = old - h
+                lm = loss()
+                W[a, b] = old
+                assert abs((lp - lm) / (2 * h) - dW[a, b]) <= 1e-6 * (1 + abs(dW[a, b]))
