@@ -369,3 +369,70 @@ def test_edge_kernel_fit_lowers_the_link_loss(hub_graph):
     assert np.all(np.isfinite(hist)) and hist[-1] < hist[0]
     L, _, _ = oracle.edge_kernel_loss(npy(U), npy(S), npy(V), ek.mu, ek.s_bar, pos, neg, 10.0)
     assert abs(ek.loss(pos, neg, 10.0)[0].item() - L) <= 1e-5 * abs(L)
+
+
+# ---- Split-ReLU network (Sec. 5.2, Thm. 2) ------------------------------------------------
+
+def _splitrelu_setup(g, d=16, y=5, L=2, seed=110):
+    X = synth.dense_features(g.n, d, seed)
+    W_star = (np.random.default_rng(seed + 1).standard_normal((d * (L + 1), y)) / 4).astype(np.float32)
+    return X, W_star
+
+
+def test_splitrelu_network_at_init_is_the_linear_model(hub_graph):
+    from paper_2111_06312_gb300.splitrelu import SplitReLUNet
+    g = hub_graph
+    L = 2
+    X, W_star = _splitrelu_setup(g, L=L)
+    with isvd.graph_operator(g, norm="sym", coeffs=[1.0]) as prop:
+        net = SplitReLUNet(prop, torch.from_numpy(X).cuda(), torch.from_numpy(W_star).cuda(), L)
+        out = net()
+    ref = oracle.graph_operator(g, form="concat", norm="sym", X=X.astype(np.float64), L=L).apply(
+        W_star.astype(np.float64))
+    assert np.abs(npy(out) - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_splitrelu_gradients_match_oracle(hub_graph):
+    from paper_2111_06312_gb300.splitrelu import SplitReLUNet
+    g = hub_graph
+    d, y, L = 16, 5, 2
+    X, W_star = _splitrelu_setup(g, d, y, L)
+    rng = np.random.default_rng(112)
+    with isvd.graph_operator(g, norm="sym", coeffs=[1.0]) as prop:
+        net = SplitReLUNet(prop, torch.from_numpy(X).cuda(), torch.from_numpy(W_star).cuda(), L)
+        with torch.no_grad():  # move off the linear start: mixed ReLU signs
+            for p in net.parameters():
+                p.add_(torch.from_numpy((rng.standard_normal(tuple(p.shape)) * 0.3).astype(np.float32)).cuda())
+        R = rng.standard_normal((g.n, y)).astype(np.float32)
+        out = net()
+        (out * torch.from_numpy(R).cuda()).sum().backward()
+    weights = tuple([npy(p.detach()) for p in group] for group in (net.Wp, net.Wn, net.Wop, net.Won))
+    Ah = oracle.graph_operator(g, norm="sym", coeffs=[1.0])
+    out_ref, cache = oracle.splitrelu_forward(Ah.apply, X.astype(np.float64), *weights)
+    assert np.abs(npy(out) - out_ref).max() <= 1e-5 * np.abs(out_ref).max()
+    grads = oracle.splitrelu_backward(lambda G: Ah.apply(G, transpose=True), cache, weights, R.astype(np.float64))
+    for group, ggroup in zip((net.Wp, net.Wn, net.Wop, net.Won), grads):
+        for p, dW in zip(group, ggroup):
+            assert np.linalg.norm(npy(p.grad) - dW) <= 1e-4 * np.linalg.norm(dW) + 1e-6
+
+
+def test_splitrelu_finetune_starts_at_the_closed_form_fit(hub_graph):
+    """W* from Thm. 1 on the rank-k SVD of [X | ÂX | Â^2 X]; the network's
+    first cross-entropy equals the linear model's, and Adam lowers it."""
+    from paper_2111_06312_gb300 import adjoint
+    from paper_2111_06312_gb300.splitrelu import SplitReLUNet, finetune
+    g = hub_graph
+    d, y, L = 16, 5, 2
+    X, _ = _splitrelu_setup(g, d, y, L)
+    lab, mask = synth.labels(g.n, y, 0.3, 113)
+    labels = torch.from_numpy(lab).cuda()
+    train = torch.from_numpy(mask).cuda()
+    Xg = torch.from_numpy(X).cuda()
+    with isvd.graph_operator(g, form="concat", norm="sym", X=X, L=L) as m, \
+            isvd.graph_operator(g, norm="sym", coeffs=[1.0]) as prop:
+        W, _ = adjoint.closed_form_init(m, adjoint.one_hot_train(labels, train, y), 24, seed=114)
+        lin = torch.nn.functional.cross_entropy(m.apply(W)[train], labels[train]).item()
+        net = SplitReLUNet(prop, Xg, W, L)
+        hist = finetune(net, labels, train, epochs=15, lr=3e-3)
+    assert abs(hist[0] - lin) <= 1e-5 * lin
+    assert hist[-1] < hist[0]
