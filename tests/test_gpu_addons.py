@@ -25,7 +25,7 @@ def built():
 
 
 def npy(t):
-    return t.double().cpu().numpy()
+    return t.detach().double().cpu().numpy()
 
 
 @pytest.fixture(scope="module")
