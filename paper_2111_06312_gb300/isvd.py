@@ -117,6 +117,9 @@ def lib():
             L.isvd_edge_kernel_loss.argtypes = [P, I64, I64, P, I64, I64, I32, P, C.c_double, C.c_double, P, P,
                                                 I64, P, P, I64, C.c_double, P, P, I64, P, P]
             L.isvd_pair_scores.argtypes = [P, I64, I64, P, I64, I64, I32, P, P, I64, P, P, P]
+            L.isvd_get_tuning.argtypes = [P, P]
+            L.isvd_set_tuning.argtypes = [P, P, P]
+            L.isvd_orthonormalize_noalloc.argtypes = [P, I64, I32, I64, P, P, P]
             L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
             L.isvd_autotune.argtypes = [P, I32, C.c_int, C.c_char_p, P, P]
             L.isvd_selftest_wait.argtypes = [I32, P, P]
@@ -131,7 +134,8 @@ def lib():
             for name in ("isvd_create_operator", "isvd_operator_shape", "isvd_apply", "isvd_apply_T", "isvd_svd",
                          "isvd_gaussian", "isvd_philox_words", "isvd_orthonormalize", "isvd_small_svd",
                          "isvd_closed_form", "isvd_compose_operators", "isvd_embed", "isvd_pair_scores",
-                         "isvd_edge_kernel_weights", "isvd_edge_kernel_scores", "isvd_edge_kernel_loss", "isvd_svd_batched", "isvd_autotune",
+                         "isvd_edge_kernel_weights", "isvd_edge_kernel_scores", "isvd_edge_kernel_loss",
+                         "isvd_get_tuning", "isvd_set_tuning", "isvd_orthonormalize_noalloc", "isvd_svd_batched", "isvd_autotune",
                          "isvd_selftest_wait"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -301,8 +305,6 @@ class Operator:
 
     def tuning(self) -> dict:
         t = (C.c_int32 * 7)()
-        lib().isvd_get_tuning.argtypes = [C.c_void_p, C.c_void_p]
-        lib().isvd_get_tuning.restype = C.c_int
         _check(lib().isvd_get_tuning(self._handle, t), "isvd_get_tuning")
         d = dict(zip(self._TUNING_FIELDS, list(t)))
         d["cache_hints"] = bool(d["flags"] & 1)
@@ -332,8 +334,6 @@ class Operator:
                 raise ValueError(f"unknown kernel {kernel!r}")
             vals[4] = (vals[4] & ~6) | {"ring": 4, "rows": 2, "chunks": 0}[kernel]
         t = (C.c_int32 * 7)(*vals)
-        lib().isvd_set_tuning.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
-        lib().isvd_set_tuning.restype = C.c_int
         _check(lib().isvd_set_tuning(self._handle, t, _stream()), "isvd_set_tuning")
         return self.tuning()
 

@@ -132,3 +132,17 @@ def test_edge_kernel_rejects_bad_arguments_on_the_host(libisvd):
     assert fn(f, 8, 10, f, 8, 10, 8, f, 1.0, 5.0, f, f, 0, f, f, 4, 10.0, f, f, n, None, None) == 1  # no edges
     assert fn(f, 8, 10, f, 8, 10, 0, f, 1.0, 5.0, f, f, 4, f, f, 4, 10.0, f, f, n, None, None) == 3  # k < 1
     assert fn(f, 8, 10, f, 8, 10, 8, f, 1.0, 5.0, f, f, 4, f, f, 4, -1.0, f, f, n, None, None) == 1  # k_neg < 0
+
+
+def test_binding_declares_every_entry_point():
+    # the ctypes binding gives every function of isvd.h its argument types, and
+    # every isvd_status function an int result (loaded without a GPU)
+    from paper_2111_06312_gb300 import isvd
+
+    L = isvd.lib()
+    src = open(os.path.join(ROOT, "include", "isvd.h")).read()
+    for name in declared_functions():
+        assert getattr(L, name).argtypes is not None, f"{name} has no argtypes in isvd.lib()"
+    for name in re.findall(r"ISVD_API\s+isvd_status\s+(isvd_\w+)\s*\(", src):
+        assert getattr(L, name).restype is C.c_int, f"{name} should return int"
+    assert L.isvd_get_tuning(None, None) == 1  # null operator: rejected on the host
