@@ -219,6 +219,16 @@ def compose(kind: str, ops, weights=None) -> Operator:
     return op
 
 
+def scale(op: Operator, w: float) -> Operator:
+    """Scalar node w M: a one-child weighted sum (Sec. 4)."""
+    return compose("sum", [op], [w])
+
+
+def power(op: Operator, p: int) -> Operator:
+    """Power node M^p: the product of p copies of a square M (Sec. 4)."""
+    return compose("product", [op] * int(p))
+
+
 def graph_operator(g, **kw) -> Operator:
     return Operator(g.n, g.rowptr, g.colidx, **kw)
 

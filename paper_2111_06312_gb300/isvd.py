@@ -405,6 +405,19 @@ def compose(kind: str, ops, weights=None, use_torch_allocator=True) -> Operator:
     return op
 
 
+def scale(op: Operator, w: float) -> Operator:
+    """Scalar node w M (Sec. 4): a one-child weighted sum."""
+    return compose("sum", [op], [w])
+
+
+def power(op: Operator, p: int) -> Operator:
+    """Power node M^p of a square operator (Sec. 4): the product of p copies
+    (1 <= p <= 16), applied one factor after another."""
+    if not 1 <= int(p) <= 16:
+        raise ValueError("power needs 1 <= p <= 16")
+    return compose("product", [op] * int(p))
+
+
 def info_dict(info: torch.Tensor) -> dict:
     v = info.cpu().tolist()
     return {"status": STATUS_NAMES.get(v[0], v[0]), "chol_shifts": v[1], "cholqr_passes": v[2], "iters_done": v[3]}

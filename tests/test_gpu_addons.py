@@ -436,3 +436,16 @@ def test_splitrelu_finetune_starts_at_the_closed_form_fit(hub_graph):
         hist = finetune(net, labels, train, epochs=15, lr=3e-3)
     assert abs(hist[0] - lin) <= 1e-5 * lin
     assert hist[-1] < hist[0]
+
+
+@pytest.mark.parametrize("p", [1, 3])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_scalar_and_power_nodes(children, p, transpose):
+    gpu, ref = children
+    a = gpu[0]
+    for cg, co in ((isvd.power(a, p), oracle.power(ref[0], p)), (isvd.scale(a, -2.5), oracle.scale(ref[0], -2.5))):
+        G = isvd.gaussian(11, a.shape[1], 13)
+        Y = cg.apply(G, transpose=transpose)
+        Yr = co.apply(npy(G), transpose=transpose)
+        assert np.abs(npy(Y) - Yr).max() <= 1e-5 * np.abs(Yr).max()
+        cg.close()

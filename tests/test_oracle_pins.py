@@ -805,3 +805,20 @@ def test_splitrelu_gradients_are_the_derivative():
                 lm = loss()
                 W[a, b] = old
                 assert abs((lp - lm) / (2 * h) - dW[a, b]) <= 1e-6 * (1 + abs(dW[a, b]))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_scalar_and_power_nodes_on_a_cycle(p):
+    # on C_n: w p(T) has singular values |w p(mu)|, p(T)^p has |p(mu)|^p
+    n = 9
+    g = synth.cycle(n)
+    P = oracle.graph_operator(g, coeffs=C5)
+    mu = np.cos(2 * np.pi * np.arange(n) / n)
+    _, S, _ = oracle.svd_any(oracle.power(P, p).explicit())
+    assert np.allclose(S, np.sort(np.abs(poly(C5, mu)) ** p)[::-1], rtol=1e-12, atol=1e-15)
+    _, S, _ = oracle.svd_any(oracle.scale(P, -2.5).explicit())
+    assert np.allclose(S, np.sort(2.5 * np.abs(poly(C5, mu)))[::-1], rtol=1e-12, atol=1e-15)
+    # T^p as a power node equals the polynomial leaf with c_p = 1
+    T = oracle.graph_operator(g, coeffs=[1.0])
+    Tp = oracle.graph_operator(g, coeffs=[0.0] * (p - 1) + [1.0])
+    assert np.allclose(oracle.power(T, p).explicit(), Tp.explicit(), rtol=0, atol=1e-15)
