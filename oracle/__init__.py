@@ -4,9 +4,13 @@ TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg use this package; the product path never does.
 It shares no code with the CUDA path (``paper_2111_06312_gb300/csrc``).
 
-The arithmetic lives in ``isvd_oracle.c`` (plain FP64 loops, one function per
-definition in the paper); this module compiles it with gcc and marshals numpy
-arrays through ctypes.  The metric helpers at the bottom (principal angles,
+The operator products, Alg. 1 and its steps live in ``isvd_oracle.c`` (plain
+FP64 loops, one function per definition in the paper); this module compiles it
+with gcc and marshals numpy arrays through ctypes.  The consumers of the SVD
+are written here in numpy, FP64, step by step as the paper states them: the
+closed form of Thm. 1, the embeddings and pair scores of Sec. 3.1, the
+Gaussian-kernel edge function of Sec. 5.1 / App. A.4 and the Split-ReLU
+network of Sec. 5.2.  The metric helpers at the bottom (principal angles,
 residuals) use numpy as a library primitive.
 """
 from __future__ import annotations
