@@ -822,3 +822,53 @@ def test_scalar_and_power_nodes_on_a_cycle(p):
     T = oracle.graph_operator(g, coeffs=[1.0])
     Tp = oracle.graph_operator(g, coeffs=[0.0] * (p - 1) + [1.0])
     assert np.allclose(oracle.power(T, p).explicit(), Tp.explicit(), rtol=0, atol=1e-15)
+
+
+def test_gather_pushed_to_the_leaves_selects_composite_rows():
+    # (the reading for Gather on a tree) [A | C][rows] = [A[rows] | C[rows]] and
+    # (A + B)[rows] = A[rows] + B[rows]
+    g = _irregular(70, 300, 85)
+    x = synth.tfidf_features(g.n, 9, 0.2, 86)
+    X = (x.d, x.rowptr, x.colidx, x.values)
+    rows = np.sort(np.random.default_rng(87).choice(g.n, 25, replace=False))
+    a, b, c = (dict(coeffs=C5, ones_coeff=-LAM), dict(norm="sym", coeffs=C2),
+               dict(form="concat", norm="sym", X=X, L=2))
+    full_h = oracle.compose("hcat", [oracle.graph_operator(g, **a), oracle.graph_operator(g, **c)]).explicit()
+    sub_h = oracle.compose("hcat", [oracle.graph_operator(g, gather_rows=rows, **a),
+                                    oracle.graph_operator(g, gather_rows=rows, **c)]).explicit()
+    assert np.array_equal(sub_h, full_h[rows])
+    full_s = oracle.compose("sum", [oracle.graph_operator(g, **a), oracle.graph_operator(g, **b)]).explicit()
+    sub_s = oracle.compose("sum", [oracle.graph_operator(g, gather_rows=rows, **a),
+                                   oracle.graph_operator(g, gather_rows=rows, **b)]).explicit()
+    assert np.array_equal(sub_s, full_s[rows])
+
+
+def test_edge_score_at_the_start_is_the_embedding_score():
+    # w = S at mu = 1, s -> 0: U_i^T diag(w) V_j = <L_i, R_j> with L = U S^1/2, R = V S^1/2
+    rng = np.random.default_rng(88)
+    U = rng.standard_normal((30, 5))
+    V = rng.standard_normal((25, 5))
+    S = np.array([4.0, 2.5, 1.0, 0.3, 0.02])
+    w, _, _ = oracle.edge_kernel_weights(S, 1.0, np.log(1.0 / (2 * 1e-4 ** 2)))
+    src, dst = rng.integers(0, 30, 40), rng.integers(0, 25, 40)
+    Lm, Rm = oracle.embeddings(U, S, V)
+    assert np.allclose(oracle.edge_scores(U, V, w, src, dst), oracle.pair_scores(Lm, Rm, src, dst),
+                       rtol=1e-12, atol=1e-12)
+
+
+def test_splitrelu_head_gradients_at_init_are_the_linear_models():
+    # at the start dWop_l - dWon_l = H_l^T R with H_l = Â^l X, i.e. block l of
+    # M^T R for M = [X | ÂX | ... | Â^L X] (the gradient of the linear model)
+    g = _irregular(60, 250, 89)
+    d, y, L = 4, 3, 2
+    rng = np.random.default_rng(90)
+    X = rng.standard_normal((g.n, d))
+    W_star = rng.standard_normal((d * (L + 1), y))
+    R = rng.standard_normal((g.n, y))
+    Ah = oracle.graph_operator(g, norm="sym", coeffs=[1.0])
+    weights = oracle.splitrelu_init(W_star, d, L)
+    _, cache = oracle.splitrelu_forward(Ah.apply, X, *weights)
+    _, _, dWop, dWon = oracle.splitrelu_backward(lambda G: Ah.apply(G, transpose=True), cache, weights, R)
+    MtR = oracle.graph_operator(g, form="concat", norm="sym", X=X, L=L).apply(R, transpose=True)
+    for l in range(L + 1):
+        assert np.allclose(dWop[l] - dWon[l], MtR[d * l:d * (l + 1)], rtol=1e-11, atol=1e-11)
