@@ -9,6 +9,9 @@
   python -m paper_2111_06312_gb300.kernel_bench equal_error [--workload ne_large] [--k 128 --p 16 --q 6]
   python -m paper_2111_06312_gb300.kernel_bench batched [--count 256]
   python -m paper_2111_06312_gb300.kernel_bench finetune [--epochs 20]
+  python -m paper_2111_06312_gb300.kernel_bench edge [--workload ne_large] [--k 128] [--pairs 1000000]
+  python -m paper_2111_06312_gb300.kernel_bench compose [--epochs 20]
+  python -m paper_2111_06312_gb300.kernel_bench splitrelu [--epochs 20]
 
 Each prints one JSON line per measured configuration (CUDA events on the
 launching stream, L2 written over between repetitions).
@@ -83,7 +86,9 @@ def spmm_case(g, op, width, dtype, reps, flush):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["spmm", "sweep", "orth", "svd", "equal_error", "batched", "finetune"])
+    ap.add_argument("what", choices=["spmm", "sweep", "orth", "svd", "equal_error", "batched", "finetune", "edge",
+                                     "compose", "splitrelu"])
+    ap.add_argument("--pairs", type=int, default=1_000_000)  # edge: edges per loss (10x as many non-edges)
     ap.add_argument("--workload", default="ne_large")
     ap.add_argument("--width", type=int, default=144)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
@@ -173,6 +178,12 @@ def main():
         equal_error(a, flush)
     elif a.what == "batched":
         batched(a, flush)
+    elif a.what == "edge":
+        edge(a, flush)
+    elif a.what == "compose":
+        compose(a, flush)
+    elif a.what == "splitrelu":
+        splitrelu_epochs(a, flush)
     else:
         finetune(a, flush)
 
@@ -355,6 +366,84 @@ def finetune(a, flush):
                           "init_ms": float(np.median(t_init)), "epoch_ms": float(np.median(t_epoch)),
                           "forward_ms": float(np.median(t_fwd)), "backward_ms": float(np.median(t_bwd)),
                           "train_acc_at_init": acc0}), flush=True)
+
+
+def edge(a, flush):
+    """Gaussian-kernel edge function (Sec. 5.1): the Eq. 9 loss and gradient
+    over `pairs` edges and 10x as many random non-edges, from the rank-k SVD of
+    the NE operator.  Algorithmic bytes: two k-rows (FP32) and two indices per
+    pair."""
+    g = synth.cached(a.workload)
+    with isvd.graph_operator(g, coeffs=C5, ones_coeff=-LAM, check_symmetry=False) as op:
+        U, S, V, _ = op.svd(a.k, a.p, a.q, 1)
+    rng = np.random.default_rng(synth.BASE_SEED + 11)
+    e = rng.integers(0, g.nnz, a.pairs)
+    src = np.searchsorted(g.rowptr, e, side="right") - 1  # row of nonzero e
+    pos = (torch.as_tensor(src, dtype=torch.int32).cuda(), torch.as_tensor(g.colidx[e]).cuda())
+    nneg = 10 * a.pairs
+    neg = (torch.as_tensor(rng.integers(0, g.n, nneg), dtype=torch.int32).cuda(),
+           torch.as_tensor(rng.integers(0, g.n, nneg), dtype=torch.int32).cuda())
+    ek = isvd.EdgeKernel(U, S, V, mu=1.1, s=0.2)
+    ek.loss(pos, neg)
+    ts = _time(lambda: ek.loss(pos, neg), a.reps, flush)
+    ms = float(np.median(ts))
+    pairs = a.pairs + nneg
+    bytes_ = pairs * (8 * a.k + 8)
+    print(json.dumps({"what": "edge", "workload": a.workload, "k": a.k, "pairs": pairs, "ms": ms,
+                      "pairs_per_s": pairs / (ms * 1e-3), "algorithmic_GBps": bytes_ / (ms * 1e-3) / 1e9}),
+          flush=True)
+
+
+def compose(a, flush):
+    """Label re-use (Sec. 5.3) on ogbn-arxiv-sized inputs: [X | ÂX | Â^2 X] beside
+    N0 [Y | N0 Y] (N0 = Â - (D+I)^-1), products and a rank-40 SVD, against the
+    plain [X | ÂX | Â^2 X]."""
+    g, x, y, train = synth.workload_finetune()
+    classes = int(y.max()) + 1
+    Y = np.zeros((g.n, classes), np.float32)
+    Y[train, y[train]] = 1.0
+    out = {"what": "compose", "n": g.n, "d": x.shape[1], "classes": classes}
+    with isvd.graph_operator(g, form="concat", norm="sym", X=x, L=2) as nc, \
+            isvd.graph_operator(g, norm="sym_noself", coeffs=[1.0]) as n0, \
+            isvd.graph_operator(g, form="concat", norm="sym_noself", X=Y, L=1) as yb:
+        lr = isvd.compose("hcat", [nc, isvd.compose("product", [n0, yb])])
+        for name, op in (("nc", nc), ("label_reuse", lr)):
+            G = isvd.gaussian(5, op.shape[1], 50)
+            H = isvd.gaussian(6, op.shape[0], 50)
+            out[name + "_apply_ms"] = float(np.median(_time(lambda: op.apply(G), a.reps, flush)))
+            out[name + "_apply_T_ms"] = float(np.median(_time(lambda: op.apply(H, transpose=True), a.reps, flush)))
+            op.svd(40, 10, 4, 1)
+            out[name + "_svd_ms"] = float(np.median(_time(lambda: op.svd(40, 10, 4, 1, check=False), a.reps, flush)))
+        lr.close()
+    print(json.dumps(out), flush=True)
+
+
+def splitrelu_epochs(a, flush):
+    """Split-ReLU network (Sec. 5.2) with L = 2 on ogbn-arxiv-sized inputs,
+    started from the closed-form W* of a rank-40 SVD: ms per fine-tuning epoch."""
+    from .splitrelu import SplitReLUNet
+
+    g, x, y, train = synth.workload_finetune()
+    labels = torch.as_tensor(y).cuda()
+    mask = torch.as_tensor(train).cuda()
+    idx = torch.nonzero(mask).reshape(-1)
+    with isvd.graph_operator(g, form="concat", norm="sym", X=x, L=2) as m, \
+            isvd.graph_operator(g, norm="sym", coeffs=[1.0]) as prop:
+        W0, _ = adjoint.closed_form_init(m, adjoint.one_hot_train(labels, mask, 40), k=40, seed=4)
+        net = SplitReLUNet(prop, torch.as_tensor(x).cuda(), W0, 2)
+        opt = torch.optim.Adam(net.parameters(), lr=1e-3)
+
+        def epoch():
+            opt.zero_grad(set_to_none=True)
+            loss = torch.nn.functional.cross_entropy(net()[idx], labels[idx])
+            loss.backward()
+            opt.step()
+
+        for _ in range(3):
+            epoch()
+        ts = _time(epoch, a.epochs, flush)
+    print(json.dumps({"what": "splitrelu", "n": g.n, "d": x.shape[1], "L": 2, "epoch_ms": float(np.median(ts))}),
+          flush=True)
 
 
 if __name__ == "__main__":
