@@ -872,3 +872,41 @@ def test_splitrelu_head_gradients_at_init_are_the_linear_models():
     MtR = oracle.graph_operator(g, form="concat", norm="sym", X=X, L=L).apply(R, transpose=True)
     for l in range(L + 1):
         assert np.allclose(dWop[l] - dWon[l], MtR[d * l:d * (l + 1)], rtol=1e-11, atol=1e-11)
+
+
+def test_new_pins_reject_planted_mistakes():
+    # plausible slips in the newer oracle functions, each caught by its pin
+    rng = np.random.default_rng(91)
+    # embeddings with S in place of S^1/2: L R^T = U S^2 V^T misses Eckart-Young
+    g = _irregular(50, 220, 92)
+    M = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM).explicit()
+    U, S, Vt = np.linalg.svd(M)
+    k = 5
+    bad = (U[:, :k] * S[:k]) @ (Vt[:k].T * S[:k]).T
+    assert abs(np.linalg.norm(M - bad) ** 2 - np.sum(S[k:] ** 2)) > 1e-6 * np.sum(S ** 2)
+    # softmax of +(x - mu)^2 exp(s_bar) (sign slip) misses the truncated-normal moment
+    from scipy.special import ndtr
+    Sv = np.array([3.0, 0.4])
+    mu, s = 1.2, 0.1
+    sb = np.log(1 / (2 * s * s))
+    x = oracle.edge_kernel_grid()
+    z = (x - mu) ** 2 * np.exp(sb)
+    pi = np.exp(z - z.max())
+    pi /= pi.sum()
+    a = np.log(Sv)
+    al, be = (0.5 - mu) / s, (2.0 - mu) / s
+    want = np.exp(a * mu + a * a * s * s / 2) * (ndtr(be - a * s) - ndtr(al - a * s)) / (ndtr(be) - ndtr(al))
+    assert not np.allclose(pi @ (Sv[None, :] ** x[:, None]), want, rtol=1e-3)
+    # Split-ReLU started with Wn = +I is not the linear model of Thm. 2
+    d, y, L = 3, 2, 2
+    X = rng.standard_normal((g.n, d))
+    W_star = rng.standard_normal((d * (L + 1), y))
+    Ah = oracle.graph_operator(g, norm="sym", coeffs=[1.0])
+    Wp, Wn, Wop, Won = oracle.splitrelu_init(W_star, d, L)
+    out_bad, _ = oracle.splitrelu_forward(Ah.apply, X, Wp, [-w for w in Wn], Wop, Won)
+    Mc = oracle.graph_operator(g, form="concat", norm="sym", X=X, L=L).explicit()
+    assert not np.allclose(out_bad, Mc @ W_star, rtol=1e-6)
+    # side-by-side children in the wrong order fail the block arrangement
+    P = oracle.graph_operator(g, coeffs=C5)
+    Q = oracle.graph_operator(g, norm="sym", coeffs=C2)
+    assert not np.allclose(oracle.compose("hcat", [Q, P]).explicit(), np.hstack([P.explicit(), Q.explicit()]))
