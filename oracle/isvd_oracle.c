@@ -756,7 +756,10 @@ int orc_jacobi_svd(const double *A, int64_t r, int64_t c, double *U, double *S, 
           gamma += gp * gq;
         }
         if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
-        if (alpha <= tiny && beta <= tiny) continue;
+        /* a column below the rounding level of A (norm^2 <= (r eps)^2 ||A||_F^2)
+           is numerically zero: its direction is rounding noise, and rotating
+           against it never converges and changes no singular value */
+        if (alpha <= tiny || beta <= tiny) continue;
         converged = 0;
         const double zeta = (beta - alpha) / (2.0 * gamma);
         const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));

@@ -910,3 +910,29 @@ def test_new_pins_reject_planted_mistakes():
     P = oracle.graph_operator(g, coeffs=C5)
     Q = oracle.graph_operator(g, norm="sym", coeffs=C2)
     assert not np.allclose(oracle.compose("hcat", [Q, P]).explicit(), np.hstack([P.explicit(), Q.explicit()]))
+
+
+@pytest.mark.parametrize("n", [4, 7])
+def test_complete_graph_spectrum_sym(n):
+    # Â on K_n is (A + I)/n = J/n: eigenvalues 1 (on the all-ones vector) and 0
+    g = synth.complete(n)
+    op = oracle.graph_operator(g, norm="sym", coeffs=C5, ones_coeff=-LAM)
+    ev = np.array([poly(C5, 1.0) - LAM * n] + [0.0] * (n - 1))
+    _, S, _ = oracle.jacobi_svd(op.explicit())
+    assert np.allclose(S, np.sort(np.abs(ev))[::-1], rtol=1e-12, atol=1e-13)
+
+
+def test_implicit_matches_explicit_all_graphs_n5():
+    # every undirected graph on 5 nodes (isolated nodes with self-loops), both
+    # normalisations with all correction terms
+    rng = np.random.default_rng(93)
+    count = 0
+    for g in _all_graphs(5):
+        for norm in ("row", "sym"):
+            op = oracle.graph_operator(g, norm=norm, coeffs=C5, ones_coeff=-LAM, adj_coeff=0.3)
+            M = op.explicit()
+            G = rng.standard_normal((5, 2))
+            assert np.abs(op.apply(G) - M @ G).max() <= 1e-12
+            assert np.abs(op.apply(G, transpose=True) - M.T @ G).max() <= 1e-12
+            count += 1
+    assert count == 2 * 1024
