@@ -936,3 +936,54 @@ def test_implicit_matches_explicit_all_graphs_n5():
             assert np.abs(op.apply(G, transpose=True) - M.T @ G).max() <= 1e-12
             count += 1
     assert count == 2 * 1024
+
+
+@pytest.mark.parametrize("r,c,rank", [(20, 10, 3), (12, 12, 1), (40, 8, 5), (9, 9, 0)])
+def test_jacobi_on_rank_deficient_matrices(r, c, rank):
+    # exact zero singular values (the case that once kept the sweep from
+    # converging): LAPACK's spectrum, and orthonormal factors on the range
+    rng = np.random.default_rng(94 + r + c + rank)
+    A = rng.standard_normal((r, rank)) @ rng.standard_normal((rank, c)) if rank else np.zeros((r, c))
+    U, S, V = oracle.jacobi_svd(A)
+    want = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(S, want, rtol=1e-12, atol=1e-13 * max(1.0, want[0] if len(want) else 0.0))
+    assert np.allclose(V.T @ V, np.eye(c), atol=1e-12)
+    if rank:
+        assert np.allclose((U[:, :rank] * S[:rank]) @ V[:, :rank].T, A, atol=1e-12 * np.abs(A).max())
+
+
+def test_jacobi_on_clustered_spectra():
+    # a 6-fold exact cluster among distinct values (degenerate clusters rotate
+    # freely; the values must not)
+    rng = np.random.default_rng(95)
+    Qa, _ = np.linalg.qr(rng.standard_normal((30, 10)))
+    Qb, _ = np.linalg.qr(rng.standard_normal((10, 10)))
+    s = np.array([5.0, 3.0, 2.0, 2.0, 2.0, 2.0, 2.0, 2.0, 0.5, 1e-3])
+    A = (Qa * s) @ Qb.T
+    _, S, _ = oracle.jacobi_svd(A)
+    assert np.allclose(S, s, rtol=1e-12, atol=1e-14)
+
+
+def test_jacobi_after_householder_is_the_same_spectrum():
+    # the tall-matrix route: Householder QR first, Jacobi on the c x c R
+    rng = np.random.default_rng(96)
+    A = rng.standard_normal((300, 12)) * np.geomspace(1, 1e-6, 12)
+    _, S1, _ = oracle.jacobi_svd(A)
+    _, R = oracle.householder_qr(A)
+    _, S2, _ = oracle.jacobi_svd(R)
+    assert np.allclose(S1, S2, rtol=1e-10, atol=0)
+
+
+def test_rayleigh_ritz_routes_agree():
+    # the GPU's route for Alg. 1's svd(B): B^T = Qt R (CholeskyQR2), SVD of R^T
+    # = Ur diag(s) Vr^T gives B = R^T Qt^T = Ur diag(s) (Qt Vr)^T; the oracle
+    # takes the one-sided Jacobi of B^T directly.  Same values, same subspaces.
+    rng = np.random.default_rng(97)
+    Bt = rng.standard_normal((400, 14)) * np.geomspace(1, 1e-3, 14)
+    W, s_direct, UB = oracle.jacobi_svd(Bt)  # B^T = W diag(s) UB^T
+    Qt, R, _ = oracle.cholqr2(Bt)
+    Ur, s_route, Vr = oracle.jacobi_svd(R.T)  # R^T = Ur diag(s) Vr^T
+    assert np.allclose(s_route, s_direct, rtol=1e-10)
+    # left singular vectors of B: UB (direct) and Ur (route); right: W and Qt Vr
+    assert oracle.max_principal_angle(UB[:, :5], Ur[:, :5]) < 1e-10
+    assert oracle.max_principal_angle(W[:, :5], (Qt @ Vr)[:, :5]) < 1e-10
