@@ -987,3 +987,18 @@ def test_rayleigh_ritz_routes_agree():
     # left singular vectors of B: UB (direct) and Ur (route); right: W and Qt Vr
     assert oracle.max_principal_angle(UB[:, :5], Ur[:, :5]) < 1e-10
     assert oracle.max_principal_angle(W[:, :5], (Qt @ Vr)[:, :5]) < 1e-10
+
+
+def test_isvd_block_wider_than_the_rank_breaks_down():
+    # Â on K_n with the all-ones term has rank one: a block of width k + p > 1
+    # leaves CholeskyQR a singular Gram matrix that no shift repairs (the range
+    # has fewer directions than the block), and the oracle reports it; at
+    # k + p <= rank it recovers the spectrum (here T on C_8, rank 6)
+    g = synth.complete(6)
+    op = oracle.graph_operator(g, norm="sym", coeffs=C5, ones_coeff=-LAM)
+    assert np.linalg.matrix_rank(op.explicit()) == 1
+    with pytest.raises(RuntimeError, match="isvd failed"):
+        op.isvd(2, 3, 2, 1)
+    c8 = oracle.graph_operator(synth.cycle(8), coeffs=[1.0])
+    _, S, _, _ = c8.isvd(3, 3, 3, 2)
+    assert np.allclose(S, [1.0, 1.0, np.sqrt(0.5)], rtol=1e-12)
