@@ -1002,3 +1002,20 @@ def test_isvd_block_wider_than_the_rank_breaks_down():
     c8 = oracle.graph_operator(synth.cycle(8), coeffs=[1.0])
     _, S, _, _ = c8.isvd(3, 3, 3, 2)
     assert np.allclose(S, [1.0, 1.0, np.sqrt(0.5)], rtol=1e-12)
+
+
+def test_weighted_sym_and_noself_invariants():
+    # weighted symmetric A, d = A 1: Â (D+I)^1/2 1 = (D+I)^1/2 1 and
+    # (Â - (D+I)^-1) (D+I)^1/2 1 = (D+I)^-1/2 d (both directions: symmetric)
+    g = _irregular()
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    key = np.minimum(rows, g.colidx) * g.n + np.maximum(rows, g.colidx)
+    _, inv = np.unique(key, return_inverse=True)
+    w = np.random.default_rng(98).uniform(0.5, 2.0, inv.max() + 1)[inv]
+    dw = np.bincount(rows, weights=w, minlength=g.n)
+    v = np.sqrt(dw + 1.0)
+    sym = oracle.graph_operator(g, norm="sym", values=w, coeffs=[1.0])
+    n0 = oracle.graph_operator(g, norm="sym_noself", values=w, coeffs=[1.0])
+    for tr in (False, True):
+        assert np.allclose(sym.apply(v, transpose=tr), v, rtol=1e-13)
+        assert np.allclose(n0.apply(v, transpose=tr), dw / v, rtol=1e-13)
