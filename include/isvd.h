@@ -395,7 +395,14 @@ enum {
   ISVD_TUNE_RING_KERNEL = 4,
   ISVD_TUNE_HOT_TAGS = 8,    /* with CACHE_HINTS: keep priority only for hub columns (by degree) */
   ISVD_TUNE_ROWS_OCC3 = 16,  /* row kernel compiled for high occupancy (FP32: 6 CTAs of 256 threads per SM, BF16: 5) */
-  ISVD_TUNE_PREFETCH = 32    /* row kernel: L2 prefetch of the next row's first neighbour rows */
+  ISVD_TUNE_PREFETCH = 32,   /* row kernel: L2 prefetch of the next row's first neighbour rows */
+  ISVD_TUNE_PACKED = 64,     /* polynomial form: the Horner iterates between two sparse products are
+                                stored slab by slab, each column slab a dense [n][width] block, so
+                                that a slab's gathered rows fill whole L2 lines */
+  ISVD_TUNE_SLAB_KERNEL = 128 /* products with A: one launch per column slab over a length-sorted
+                                 list of rows and hub pieces (hub partials summed in piece order by
+                                 the group finishing the last piece); implies PACKED; takes
+                                 precedence over the other kernels */
 };
 
 /* Read / replace the operator's launch shapes.  isvd_set_tuning rebuilds the

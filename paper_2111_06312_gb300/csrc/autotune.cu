@@ -3,8 +3,9 @@
 //
 // The autotuner times isvd_apply on the operator, at the caller's block width
 // and storage type, for a fixed list of launch shapes (row kernel variants:
-// occupancy, L2 budget for hub columns, hub split threshold, wide slabs; the
-// ring and nonzero-chunk kernels) and keeps the fastest.  Results can be kept
+// occupancy, L2 budget for hub columns, hub split threshold, wide slabs,
+// packed temporaries; the ring kernel; the packed-slab kernel at three slab
+// widths) and keeps the fastest.  Results can be kept
 // in a text cache keyed by the operator's shape, its degree histogram, the
 // block width, the storage type and the device name, so that a later process
 // skips the timing.  The paper has no counterpart (it called library kernels).
@@ -150,6 +151,19 @@ isvd_status isvd_autotune(isvd_operator *op, int32_t b, isvd_dtype dtype, const 
   {
     isvd_tuning t = r;
     t.flags = ISVD_TUNE_RING_KERNEL | ISVD_TUNE_CACHE_HINTS | ISVD_TUNE_HOT_TAGS;
+    add(t);
+  }
+  {
+    isvd_tuning t = r;
+    t.flags |= ISVD_TUNE_PACKED;
+    add(t);
+  }
+  // packed slabs of 128, 256 and 512 bytes per row
+  for (int w : {32, 64, 128}) {
+    isvd_tuning t = r;
+    t.flags = ISVD_TUNE_SLAB_KERNEL;
+    t.slab_cols_f32 = w;
+    t.slab_cols_bf16 = 2 * w;
     add(t);
   }
 

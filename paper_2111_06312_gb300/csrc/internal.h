@@ -119,6 +119,27 @@ cudaError_t spmm_launch(const SpmmArgs &a, int dtype, const HeavyPlan &hp, float
 // Column slabs for a block of width b (row-major, 16-byte aligned).
 int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out);
 
+// Packed-slab form: one launch per column slab over a work list of
+// segments sorted by length, longest first: whole rows of at most `chunk`
+// nonzeros (rows without nonzeros included, so that their epilogue runs) and
+// the `chunk`-nonzero pieces of longer (hub) rows.  A hub piece stores its
+// partial sum in its slot; the group that completes a hub's last piece adds
+// the hub's partials in slot order and applies the epilogue, so results do
+// not depend on the order in which pieces finish.
+struct SlabPlan {
+  int32_t n_items = 0;
+  int4 *items = nullptr;        // (row, first nonzero, end, slot): slot -1 = a whole row
+  int32_t n_hubs = 0;
+  int4 *hubs = nullptr;         // (row, first slot, piece count, 0)
+  int32_t *slot_hub = nullptr;  // hub of each slot
+  int32_t n_slots = 0;
+  int32_t *counters = nullptr;  // pieces finished per hub in the running launch (0 between launches)
+  int32_t chunk = 128;
+};
+// partial: p.n_slots x pw FP32 (pw >= the widest slab).
+cudaError_t spmm_slab_launch(const SpmmArgs &a, int dtype, const SlabPlan &p, float *partial, int64_t pw,
+                             cudaStream_t s);
+
 // Nonzero-balanced form: warps take chunks of CH consecutive nonzeros; rows
 // crossing chunk boundaries (split) and rows without nonzeros (empty) are
 // finished by two small passes.  row_of[e] is the row of nonzero e.
@@ -280,8 +301,9 @@ struct isvd_operator {
   int64_t x_nnz = 0;
   isvd::HeavyPlan heavy_A, heavy_X, heavy_XT;
   isvd::ChunkPlan chunk_A, chunk_X, chunk_XT;
+  isvd::SlabPlan slab_A;    // packed-slab work list of A
   isvd::RingTags tags_A;    // degree-bucket tags of A's columns (ring form)
-  int32_t spmm_algo = 0;    // 0: row groups with hub splitting, 1: nonzero chunks, 2: ring
+  int32_t spmm_algo = 3;    // 0: row groups with hub splitting, 1: nonzero chunks, 2: ring, 3: packed slabs
   int32_t chunk_nnz = 512;
   std::vector<void *> owned;  // allocations released at destroy
   // workspace arena (grow only)
@@ -289,11 +311,12 @@ struct isvd_operator {
   size_t arena_bytes = 0;
   cudaStream_t capture_stream = nullptr;
   isvd::SideStream side;        // second stream: split hub rows beside the row-group kernel
-  int32_t slab_cols_f32 = 128, slab_cols_bf16 = 256;
+  int32_t slab_cols_f32 = 64, slab_cols_bf16 = 128;
   int32_t cache_hints = 1;
   int32_t hot_tags = 1;     // row kernel: L2 priority only for gathers of hub columns
   int32_t rows_occupancy = 3;
   int32_t prefetch = 0;
+  int32_t packed_temps = 0; // Horner temporaries stored slab by slab (each slab a dense [n][w] block)
   struct GraphEntry {
     uint64_t key[16];
     cudaGraphExec_t exec;
@@ -314,6 +337,7 @@ namespace isvd {
 void *op_alloc(isvd_operator *op, size_t bytes, cudaStream_t s);
 void free_heavy(isvd_operator *op, HeavyPlan *hp, cudaStream_t s);
 void free_chunks(isvd_operator *op, ChunkPlan *cp, cudaStream_t s);
+void free_slab_plan(isvd_operator *op, SlabPlan *sp, cudaStream_t s);
 void op_free(isvd_operator *op, void *p, cudaStream_t s);
 isvd_status ensure_arena(isvd_operator *op, size_t bytes, cudaStream_t s);
 // Drop the operator's captured graphs (workspace moved or launch shapes changed).

@@ -274,7 +274,80 @@ void free_chunks(isvd_operator *op, ChunkPlan *cp, cudaStream_t s) {
   cp->nchunks = cp->nsplit = cp->nempty = 0;
 }
 
+void free_slab_plan(isvd_operator *op, SlabPlan *sp, cudaStream_t s) {
+  op_free(op, sp->items, s);
+  op_free(op, sp->hubs, s);
+  op_free(op, sp->slot_hub, s);
+  op_free(op, sp->counters, s);
+  sp->items = nullptr;
+  sp->hubs = nullptr;
+  sp->slot_hub = nullptr;
+  sp->counters = nullptr;
+  sp->n_items = sp->n_hubs = sp->n_slots = 0;
+}
+
 namespace {
+
+// Packed-slab work list from a host copy of rowptr: whole rows of at most
+// `threshold` nonzeros and `chunk`-nonzero pieces of the longer rows, sorted by
+// length, longest first (ties in row order), so that the groups of a warp get
+// segments of about the same length.
+isvd_status build_slab_plan(isvd_operator *op, const int32_t *rowptr_dev, int64_t rows, int32_t threshold,
+                            int32_t chunk, SlabPlan *sp, cudaStream_t s) {
+  std::vector<int32_t> rp((size_t)rows + 1);
+  ISVD_CUDA_TRY(cudaMemcpyAsync(rp.data(), rowptr_dev, sizeof(int32_t) * (rows + 1), cudaMemcpyDeviceToHost, s));
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int4> items;
+  std::vector<int4> hubs;
+  std::vector<int32_t> slot_hub;
+  items.reserve((size_t)rows);
+  for (int64_t i = 0; i < rows; ++i) {
+    const int32_t e0 = rp[i], e1 = rp[i + 1];
+    if (e1 - e0 <= threshold) {
+      items.push_back(make_int4((int)i, e0, e1, -1));
+      continue;
+    }
+    const int32_t first = (int32_t)slot_hub.size();
+    for (int32_t e = e0; e < e1; e += chunk) {
+      items.push_back(make_int4((int)i, e, std::min<int32_t>(e1, e + chunk), (int)slot_hub.size()));
+      slot_hub.push_back((int32_t)hubs.size());
+    }
+    hubs.push_back(make_int4((int)i, first, (int32_t)slot_hub.size() - first, 0));
+  }
+  // counting sort by length, longest first, stable
+  const int32_t maxlen = std::max(threshold, chunk);
+  std::vector<int64_t> pos((size_t)maxlen + 2, 0);
+  for (const int4 &t : items) pos[t.z - t.y] += 1;
+  int64_t acc = 0;
+  for (int64_t len = maxlen; len >= 0; --len) {
+    const int64_t c = pos[len];
+    pos[len] = acc;
+    acc += c;
+  }
+  std::vector<int4> sorted(items.size());
+  for (const int4 &t : items) sorted[pos[t.z - t.y]++] = t;
+  free_slab_plan(op, sp, s);
+  sp->chunk = chunk;
+  sp->n_items = (int32_t)sorted.size();
+  sp->n_hubs = (int32_t)hubs.size();
+  sp->n_slots = (int32_t)slot_hub.size();
+  if (sp->n_items == 0) return ISVD_OK;
+  sp->items = (int4 *)op_alloc(op, sizeof(int4) * sorted.size(), s);
+  if (!sp->items) return fail(ISVD_ERR_WORKSPACE, "slab work list allocation failed");
+  ISVD_CUDA_TRY(cudaMemcpyAsync(sp->items, sorted.data(), sizeof(int4) * sorted.size(), cudaMemcpyHostToDevice, s));
+  if (sp->n_hubs > 0) {
+    sp->hubs = (int4 *)op_alloc(op, sizeof(int4) * hubs.size(), s);
+    sp->slot_hub = (int32_t *)op_alloc(op, sizeof(int32_t) * slot_hub.size(), s);
+    sp->counters = (int32_t *)op_alloc(op, sizeof(int32_t) * hubs.size(), s);
+    if (!sp->hubs || !sp->slot_hub || !sp->counters) return fail(ISVD_ERR_WORKSPACE, "slab hub plan allocation failed");
+    ISVD_CUDA_TRY(cudaMemcpyAsync(sp->hubs, hubs.data(), sizeof(int4) * hubs.size(), cudaMemcpyHostToDevice, s));
+    ISVD_CUDA_TRY(
+        cudaMemcpyAsync(sp->slot_hub, slot_hub.data(), sizeof(int32_t) * slot_hub.size(), cudaMemcpyHostToDevice, s));
+    ISVD_CUDA_TRY(cudaMemsetAsync(sp->counters, 0, sizeof(int32_t) * hubs.size(), s));
+  }
+  ISVD_CUDA_TRY(cudaStreamSynchronize(s));
+  return ISVD_OK;
+}
 
 // Build the hub-row split plan from a host copy of rowptr.
 isvd_status build_heavy(isvd_operator *op, const int32_t *rowptr_dev, int64_t rows, HeavyPlan *hp,
@@ -610,6 +683,7 @@ isvd_status create_impl(const isvd_operator_desc *desc, isvd_operator *op, cudaS
   }
   ISVD_TRY(build_heavy(op, d.A.rowptr, n, &op->heavy_A, s));
   ISVD_TRY(build_chunks(op, d.A.rowptr, n, d.A.nnz, &op->chunk_A, s));
+  ISVD_TRY(build_slab_plan(op, d.A.rowptr, n, op->heavy_A.threshold, op->heavy_A.chunk, &op->slab_A, s));
   ISVD_TRY(build_tags(op, s));
 
   if (d.form == ISVD_FORM_CONCAT) {
@@ -654,7 +728,10 @@ struct Chain {
 int slab_cols(const isvd_operator *op, int dtype) {
   if (op->spmm_algo == 1) return chunk_slab_cols(dtype);
   if (op->spmm_algo == 2) return ring_max_cols(dtype);
-  return dtype == DT_F32 ? op->slab_cols_f32 : op->slab_cols_bf16;
+  const int c = dtype == DT_F32 ? op->slab_cols_f32 : op->slab_cols_bf16;
+  // the packed-slab kernel gives each lane one 16-byte chunk: at most 32 lanes' worth
+  const int cap = dtype == DT_F32 ? 128 : 256;
+  return op->spmm_algo == 3 && c > cap ? cap : c;
 }
 
 SpmmArgs base_args_A(const isvd_operator *op) {
@@ -675,8 +752,13 @@ SpmmArgs base_args_A(const isvd_operator *op) {
 int slabs_needed(int dtype, int32_t b, int32_t scols);
 
 // fill slabs for one segment of width b; false when they do not fit kMaxSlabs
+//
+// pack_in / pack_out: `in` / `out` hold the block slab by slab, each slab a
+// dense [rows][w] block (w = its width rounded up to 16 bytes) following the
+// previous one; ldi / ldo are then ignored.
 bool add_slabs(SpmmArgs &a, int dtype, int32_t b, int32_t scols, int32_t col_base, const void *in, int64_t ldi,
-               void *out, int64_t ldo, const void *axpy, int64_t lda) {
+               void *out, int64_t ldo, const void *axpy, int64_t lda, bool pack_in = false,
+               bool pack_out = false) {
   SpmmSlab tmp[256];
   int ns = 0;
   if (scols == ring_max_cols(dtype)) {  // ring form: full-width slabs
@@ -693,12 +775,16 @@ bool add_slabs(SpmmArgs &a, int dtype, int32_t b, int32_t scols, int32_t col_bas
   }
   if (a.nslabs + ns > kMaxSlabs) return false;
   const size_t es = dtype_size(dtype);
+  const int64_t vn = 16 / (int64_t)es;
+  size_t packed_off = 0;  // elements before this slab in a packed block
   for (int i = 0; i < ns; ++i) {
     SpmmSlab sl = tmp[i];
-    sl.in = (const char *)in + (size_t)sl.col0 * es;
-    sl.ldi = ldi;
-    sl.out = (char *)out + (size_t)sl.col0 * es;
-    sl.ldo = ldo;
+    const int64_t pw = round_up(sl.width, vn);
+    sl.in = pack_in ? (const char *)in + packed_off * es : (const char *)in + (size_t)sl.col0 * es;
+    sl.ldi = pack_in ? pw : ldi;
+    sl.out = pack_out ? (char *)out + packed_off * es : (char *)out + (size_t)sl.col0 * es;
+    sl.ldo = pack_out ? pw : ldo;
+    packed_off += (size_t)a.rows * (size_t)pw;
     sl.axpy = axpy ? (const char *)axpy + (size_t)sl.col0 * es : nullptr;
     sl.lda = lda;
     sl.col0 += col_base;
@@ -734,6 +820,8 @@ cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, const ChunkPla
     return cudaSuccess;
   }
   if (c.op->spmm_algo == 1) return spmm_chunk_launch(a, c.dtype, cp, c.sc->heavy_partial, pw, c.s);
+  if (c.op->spmm_algo == 3 && a.colidx == c.op->desc.A.colidx)
+    return spmm_slab_launch(a, c.dtype, c.op->slab_A, c.sc->heavy_partial, pw, c.s);
   if (a.cache_hints && c.op->hot_tags && a.colidx == c.op->desc.A.colidx && c.op->tags_A.tagged) {
     // per slab: the hottest degree buckets whose gathered rows fit the L2 budget keep priority
     const RingTags &t = c.op->tags_A;
@@ -753,7 +841,7 @@ cudaError_t run(const Chain &c, SpmmArgs &a, const HeavyPlan &hp, const ChunkPla
 }
 
 int64_t partial_rows(const isvd_operator *op) {
-  return std::max<int64_t>({op->heavy_A.n_chunks, op->heavy_X.n_chunks, op->heavy_XT.n_chunks,
+  return std::max<int64_t>({op->heavy_A.n_chunks, op->heavy_X.n_chunks, op->heavy_XT.n_chunks, op->slab_A.n_slots,
                             2 * op->chunk_A.nchunks, 2 * op->chunk_X.nchunks, 2 * op->chunk_XT.nchunks, 1});
 }
 
@@ -897,7 +985,10 @@ static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int
       a.ax_rowscale = op->s;
     }
     if (last) set_lowrank(a);
-    ISVD_SLABS(add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, axp, ldg));
+    // packed temporaries: every iterate between two products is written and
+    // gathered slab by slab (the row kernel only)
+    const bool pack = (op->packed_temps && op->spmm_algo == 0) || op->spmm_algo == 3;
+    ISVD_SLABS(add_slabs(a, dtype, b, scols, 0, cur, ldcur, dst, lddst, axp, ldg, pack && !first, pack && !last));
     ISVD_CUDA_TRY(run(ch, a, op->heavy_A, op->chunk_A, bseg));
     cur = dst;
     ldcur = lddst;
@@ -1280,6 +1371,7 @@ void isvd_destroy_operator(isvd_operator *op) {
   free_chunks(op, &op->chunk_A, s);
   free_chunks(op, &op->chunk_X, s);
   free_chunks(op, &op->chunk_XT, s);
+  free_slab_plan(op, &op->slab_A, s);
   if (op->capture_stream) cudaStreamDestroy(op->capture_stream);
   if (op->side.fork) cudaEventDestroy(op->side.fork);
   if (op->side.join) cudaEventDestroy(op->side.join);
@@ -1328,8 +1420,10 @@ isvd_status isvd_get_tuning(const isvd_operator *op, isvd_tuning *out) {
   out->heavy_threshold = op->heavy_A.threshold;
   out->heavy_chunk = op->heavy_A.chunk;
   out->flags = (op->cache_hints ? ISVD_TUNE_CACHE_HINTS : 0) | (op->spmm_algo == 0 ? ISVD_TUNE_ROW_KERNEL : 0) |
+               (op->spmm_algo == 3 ? ISVD_TUNE_SLAB_KERNEL : 0) |
                (op->spmm_algo == 2 ? ISVD_TUNE_RING_KERNEL : 0) | (op->hot_tags ? ISVD_TUNE_HOT_TAGS : 0) |
-               (op->rows_occupancy >= 3 ? ISVD_TUNE_ROWS_OCC3 : 0) | (op->prefetch ? ISVD_TUNE_PREFETCH : 0);
+               (op->rows_occupancy >= 3 ? ISVD_TUNE_ROWS_OCC3 : 0) | (op->prefetch ? ISVD_TUNE_PREFETCH : 0) |
+               (op->packed_temps ? ISVD_TUNE_PACKED : 0);
   out->chunk_nnz = op->chunk_nnz;
   out->l2_budget_mb = (int32_t)(op->tags_A.l2_budget >> 20);
   return ISVD_OK;
@@ -1348,10 +1442,14 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
   op->slab_cols_f32 = t->slab_cols_f32;
   op->slab_cols_bf16 = t->slab_cols_bf16;
   op->cache_hints = (t->flags & ISVD_TUNE_CACHE_HINTS) ? 1 : 0;
-  op->spmm_algo = (t->flags & ISVD_TUNE_RING_KERNEL) ? 2 : (t->flags & ISVD_TUNE_ROW_KERNEL) ? 0 : 1;
+  op->spmm_algo = (t->flags & ISVD_TUNE_SLAB_KERNEL)  ? 3
+                  : (t->flags & ISVD_TUNE_RING_KERNEL) ? 2
+                  : (t->flags & ISVD_TUNE_ROW_KERNEL)  ? 0
+                                                       : 1;
   op->hot_tags = (t->flags & ISVD_TUNE_HOT_TAGS) ? 1 : 0;
   op->rows_occupancy = (t->flags & ISVD_TUNE_ROWS_OCC3) ? 3 : 2;
   op->prefetch = (t->flags & ISVD_TUNE_PREFETCH) ? 1 : 0;
+  op->packed_temps = (t->flags & ISVD_TUNE_PACKED) ? 1 : 0;
   op->chunk_nnz = t->chunk_nnz;
   op->tags_A.l2_budget = (int64_t)t->l2_budget_mb << 20;
   HeavyPlan *plans[3] = {&op->heavy_A, &op->heavy_X, &op->heavy_XT};
@@ -1361,6 +1459,7 @@ isvd_status isvd_set_tuning(isvd_operator *op, const isvd_tuning *t, void *strea
   }
   ISVD_TRY(build_heavy(op, op->desc.A.rowptr, op->n, &op->heavy_A, s));
   ISVD_TRY(build_chunks(op, op->desc.A.rowptr, op->n, op->desc.A.nnz, &op->chunk_A, s));
+  ISVD_TRY(build_slab_plan(op, op->desc.A.rowptr, op->n, op->heavy_A.threshold, op->heavy_A.chunk, &op->slab_A, s));
   if (op->desc.form == ISVD_FORM_CONCAT) {
     ISVD_TRY(build_heavy(op, op->x_rowptr, op->n, &op->heavy_X, s));
     ISVD_TRY(build_heavy(op, op->xt_rowptr, op->desc.d, &op->heavy_XT, s));

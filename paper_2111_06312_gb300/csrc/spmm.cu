@@ -34,6 +34,13 @@
 #ifndef ISVD_WIDE_MINB
 #define ISVD_WIDE_MINB 4
 #endif
+// resident blocks per SM of the packed-slab kernel
+#ifndef ISVD_SLAB_MINB_F32
+#define ISVD_SLAB_MINB_F32 5
+#endif
+#ifndef ISVD_SLAB_MINB_BF16
+#define ISVD_SLAB_MINB_BF16 5
+#endif
 
 namespace isvd {
 namespace {
@@ -586,6 +593,142 @@ __global__ void __launch_bounds__(256) spmm_finish_big_kernel(const __grid_const
   }
 }
 
+// Packed-slab gather: acc += sum over the segment [e0, e0 + len) of
+// a_e w_j in_j for the lane's 16-byte chunk of the slab.  The groups of a
+// warp step together to the warp's longest segment (maxlen); every lane of
+// the warp calls it.  The segment is taken 32 nonzeros at a time (4 G for
+// groups of fewer than eight lanes): the G lanes of a group first load all the
+// block's column indices (one coalesced load per index and lane), then
+// issue its gathers four at a time, so that a row costs one index round trip
+// per block whatever the slab width.
+template <int DT, int G, bool WEIGHTED>
+__device__ __forceinline__ void gather_segment(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int e0,
+                                               int len, int maxlen, float *acc) {
+  using V = Vec<DT>;
+  constexpr int VN = V::N;
+  constexpr int U = G < 4 ? G : 4;
+  constexpr int IPL = G >= 8 ? 32 / G : 4;  // indices per lane and block
+  constexpr int BLK = IPL * G;              // nonzeros per block (32, or 4 G for the narrowest groups)
+  const char *inb = reinterpret_cast<const char *>(sl.in) + (size_t)L.col * V::BYTES;
+  const size_t ldb = (size_t)sl.ldi * V::BYTES;
+  const int lead = L.sub * G;
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  for (int off = 0; off < maxlen; off += BLK) {
+    int j[IPL];
+    float w[WEIGHTED ? IPL : 1];
+#pragma unroll
+    for (int q = 0; q < IPL; ++q) {
+      const int t = off + q * G + L.gl;
+      j[q] = -1;
+      if (WEIGHTED) w[q] = 1.f;
+      if (t < len) {
+        const int e = e0 + t;
+        j[q] = __ldg(a.colidx + e);
+        if (WEIGHTED) {
+          w[q] = a.values ? __ldg(a.values + e) : 1.f;
+          if (a.colw) w[q] *= __ldg(a.colw + j[q]);
+        }
+      }
+    }
+    const int cnt = min(BLK, maxlen - off);  // warp-uniform
+#pragma unroll
+    for (int q = 0; q < IPL; ++q) {
+      if (q * G >= cnt) break;
+#pragma unroll
+      for (int u0 = 0; u0 < G; u0 += U) {
+        int jj[U];
+        float ww[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          jj[u] = __shfl_sync(0xffffffffu, j[q], lead + u0 + u);
+          ww[u] = WEIGHTED ? __shfl_sync(0xffffffffu, w[WEIGHTED ? q : 0], lead + u0 + u) : 1.f;
+        }
+        if (L.active) {
+          uint4 raw[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) raw[u] = jj[u] >= 0 ? ld16<false>(inb + (size_t)jj[u] * ldb, 0) : zero;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            float v[VN];
+            V::unpack(raw[u], v);
+#pragma unroll
+            for (int k = 0; k < VN; ++k) acc[k] = fmaf(ww[u], v[k], acc[k]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// One column slab (a.slab[0]) over the packed-slab work list: `group` lanes
+// per segment, 32 / group segments per warp.  Whole rows end in the epilogue;
+// hub pieces store partials, and the group that finishes a hub's last piece
+// sums the hub's partials in slot order and runs the epilogue.
+template <int DT, int G, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    spmm_slab_kernel(const __grid_constant__ SpmmArgs a, const int4 *__restrict__ items, int32_t n_items,
+                     const int4 *__restrict__ hubs, const int32_t *__restrict__ slot_hub, int32_t *counters,
+                     float *partial, int64_t pw) {
+  constexpr int VN = Vec<DT>::N;
+  const SpmmSlab &sl = a.slab[0];
+  const Lane L = make_lane<DT>(sl);  // sl.group == G
+  const Policies pol{0, 0};
+  constexpr int rpw = 32 / G;
+  const bool weighted = a.values != nullptr || a.colw != nullptr;
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t base = warp * rpw; base < n_items; base += nwarp * rpw) {
+    const int64_t it = base + L.sub;
+    int4 item = make_int4(0, 0, 0, -2);  // slot -2: no segment for this group
+    if (it < n_items) item = __ldg(items + it);
+    const int len = item.z - item.y;
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    float acc[VN];
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = 0.f;
+    if (weighted) gather_segment<DT, G, true>(a, sl, L, item.y, len, maxlen, acc);
+    else gather_segment<DT, G, false>(a, sl, L, item.y, len, maxlen, acc);
+    if (item.w == -2) continue;
+    if (item.w == -1) {
+      epilogue<DT, false, 1>(a, sl, L, item.x, pol, acc);
+      continue;
+    }
+    // a hub piece: publish the partial, then count it
+    if (L.active) {
+      float4 *p = reinterpret_cast<float4 *>(partial + (size_t)item.w * pw + L.col);
+#pragma unroll
+      for (int k = 0; k < VN / 4; ++k) p[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+    }
+    __threadfence();
+    __syncwarp(L.mask);
+    const int h = __ldg(slot_hub + item.w);
+    int done = 0;
+    if (L.gl == 0) done = atomicAdd(counters + h, 1) + 1;
+    done = __shfl_sync(L.mask, done, L.sub * L.G);
+    const int4 hb = __ldg(hubs + h);
+    if (done != hb.z) continue;
+    // last piece of the hub: every other piece's partial is visible (fence before each count)
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < VN; ++k) acc[k] = 0.f;
+    if (L.active) {
+      for (int c = 0; c < hb.z; ++c) {
+        const float4 *q = reinterpret_cast<const float4 *>(partial + (size_t)(hb.y + c) * pw + L.col);
+#pragma unroll
+        for (int k = 0; k < VN / 4; ++k) {
+          const float4 v = __ldcg(q + k);
+          acc[4 * k] += v.x;
+          acc[4 * k + 1] += v.y;
+          acc[4 * k + 2] += v.z;
+          acc[4 * k + 3] += v.w;
+        }
+      }
+    }
+    epilogue<DT, false, 1>(a, sl, L, hb.x, pol, acc);
+    if (L.gl == 0) counters[h] = 0;  // ready for the next launch
+  }
+}
+
 int pow2_ceil(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -686,6 +829,46 @@ int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out) {
     out[n++] = sl;
   }
   return n;
+}
+
+template <int DT, int MINB>
+cudaError_t slab_launch_one(const SpmmArgs &one, const SlabPlan &p, float *partial, int64_t pw, cudaStream_t s) {
+  const int G = one.slab[0].group;
+  int64_t bx = ceil_div(p.n_items, 8 * (32 / G));
+  const int64_t cap = (int64_t)kNumSMs * MINB;
+  if (bx > cap) bx = cap;
+  const dim3 grid((unsigned)bx);
+#define ISVD_SLAB_CASE(g)                                                                                     \
+  case g:                                                                                                     \
+    spmm_slab_kernel<DT, g, MINB><<<grid, 256, 0, s>>>(one, p.items, p.n_items, p.hubs, p.slot_hub, p.counters, \
+                                                       partial, pw);                                          \
+    break;
+  switch (G) {
+    ISVD_SLAB_CASE(1)
+    ISVD_SLAB_CASE(2)
+    ISVD_SLAB_CASE(4)
+    ISVD_SLAB_CASE(8)
+    ISVD_SLAB_CASE(16)
+    ISVD_SLAB_CASE(32)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef ISVD_SLAB_CASE
+  return cudaGetLastError();
+}
+
+cudaError_t spmm_slab_launch(const SpmmArgs &a, int dtype, const SlabPlan &p, float *partial, int64_t pw,
+                             cudaStream_t s) {
+  if (a.rows == 0 || a.nslabs == 0 || p.n_items == 0) return cudaSuccess;
+  for (int i = 0; i < a.nslabs; ++i) {
+    SpmmArgs one = a;
+    one.slab[0] = a.slab[i];
+    one.nslabs = 1;
+    const cudaError_t e = dtype == DT_F32 ? slab_launch_one<DT_F32, ISVD_SLAB_MINB_F32>(one, p, partial, pw, s)
+                                          : slab_launch_one<DT_BF16, ISVD_SLAB_MINB_BF16>(one, p, partial, pw, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t spmm_launch(const SpmmArgs &a, int dtype, const HeavyPlan &hp, float *partial, int64_t pw,

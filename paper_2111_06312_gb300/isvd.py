@@ -311,11 +311,13 @@ class Operator:
         d["hot_tags"] = bool(d["flags"] & 8)
         d["rows_occupancy"] = 3 if d["flags"] & 16 else 2
         d["prefetch"] = bool(d["flags"] & 32)
-        d["kernel"] = "ring" if d["flags"] & 4 else "rows" if d["flags"] & 2 else "chunks"
+        d["packed"] = bool(d["flags"] & 64)
+        d["kernel"] = ("slab" if d["flags"] & 128 else "ring" if d["flags"] & 4 else "rows" if d["flags"] & 2
+                       else "chunks")
         return d
 
     def set_tuning(self, kernel=None, cache_hints=None, hot_tags=None, rows_occupancy=None, prefetch=None,
-                   **fields):
+                   packed=None, **fields):
         """kernel: 'ring' (nonzero chunks, full-width gathers through shared
         memory), 'rows' (row groups with hub splitting) or 'chunks' (nonzero
         chunks over narrow column slabs); other keys as in isvd_tuning."""
@@ -329,10 +331,12 @@ class Operator:
             vals[4] = (vals[4] & ~16) | (16 if rows_occupancy >= 3 else 0)
         if prefetch is not None:
             vals[4] = (vals[4] & ~32) | (32 if prefetch else 0)
+        if packed is not None:
+            vals[4] = (vals[4] & ~64) | (64 if packed else 0)
         if kernel is not None:
-            if kernel not in ("ring", "rows", "chunks"):
+            if kernel not in ("slab", "ring", "rows", "chunks"):
                 raise ValueError(f"unknown kernel {kernel!r}")
-            vals[4] = (vals[4] & ~6) | {"ring": 4, "rows": 2, "chunks": 0}[kernel]
+            vals[4] = (vals[4] & ~134) | {"slab": 128, "ring": 4, "rows": 2, "chunks": 0}[kernel]
         t = (C.c_int32 * 7)(*vals)
         _check(lib().isvd_set_tuning(self._handle, t, _stream()), "isvd_set_tuning")
         return self.tuning()

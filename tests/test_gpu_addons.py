@@ -13,7 +13,7 @@ from svd_checks import check_svd
 pytestmark = pytest.mark.gpu
 LAM = 0.05
 C5 = oracle.ne_coefficients(5)
-KERNELS = ["ring", "chunks", "rows"]
+KERNELS = ["ring", "chunks", "rows", "slab"]
 
 
 @pytest.fixture(scope="module", autouse=True)

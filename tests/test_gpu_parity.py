@@ -105,16 +105,26 @@ def make_ops(g, norm, K, ones, adj, weighted, lowrank, seed=5):
     return gpu, oracle.graph_operator(g, **kw)
 
 
-KERNELS = ["ring", "chunks", "rows", "rows_wide"]
+KERNELS = ["ring", "chunks", "rows", "rows_wide", "rows_packed", "slab", "slab_narrow", "slab_pieces"]
 
 
 def tune(op, kernel, **kw):
     """rows_wide: the row kernel with slabs wider than 32 lanes x 16 bytes
-    (two 16-byte chunks per lane)."""
+    (two 16-byte chunks per lane); rows_packed: the row kernel with packed
+    Horner temporaries; slab: the packed-slab kernel at its default widths;
+    slab_narrow: packed slabs of 16 columns (several rows per warp);
+    slab_pieces: packed slabs with rows above 32 nonzeros cut into 32-nonzero
+    pieces (many hub partials finished by the last piece)."""
     if kernel == "rows_wide":
-        op.set_tuning(kernel="rows", slab_cols_f32=256, slab_cols_bf16=512, **kw)
+        op.set_tuning(kernel="rows", slab_cols_f32=256, slab_cols_bf16=512, packed=False, **kw)
+    elif kernel == "rows_packed":
+        op.set_tuning(kernel="rows", slab_cols_f32=128, slab_cols_bf16=256, packed=True, **kw)
+    elif kernel == "slab_narrow":
+        op.set_tuning(kernel="slab", slab_cols_f32=16, slab_cols_bf16=16, **kw)
+    elif kernel == "slab_pieces":
+        op.set_tuning(kernel="slab", heavy_threshold=32, heavy_chunk=32, **kw)
     else:
-        op.set_tuning(kernel=kernel, **kw)
+        op.set_tuning(kernel=kernel, packed=False, **kw)
 
 
 @pytest.mark.parametrize("case", CASES)

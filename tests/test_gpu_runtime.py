@@ -40,7 +40,7 @@ def test_autotune_keeps_results_and_caches(graph, dtype, tmp_path):
     oop = oracle.graph_operator(graph, coeffs=C5, ones_coeff=-0.05)
     try:
         t1 = gop.autotune(42, dtype=dtype, cache_path=cache)
-        assert t1["kernel"] in ("rows", "ring")
+        assert t1["kernel"] in ("rows", "ring", "slab")
         _check_apply(gop, oop, 42, dtype, 1e-5 if dtype == torch.float32 else 2e-2)
         lines = open(cache).read().strip().splitlines()
         assert len(lines) == 1 and "b=42" in lines[0]
