@@ -8,6 +8,7 @@ import torch
 
 import oracle
 from paper_2111_06312_gb300 import build, isvd, synth
+from svd_checks import assert_svd, measure_svd, npy
 
 pytestmark = pytest.mark.gpu
 LAM = 0.05
@@ -59,15 +60,31 @@ def test_batched_equals_single_calls(problems, precision):
         assert torch.equal(S2[i], S[i]) and torch.equal(U2[i], U[i]) and torch.equal(V2[i], V[i])
 
 
-def test_batched_matches_oracle(problems):
+# stated error of the mixed-precision path against the FP64 oracle on these
+# problems (BF16 blocks in the power iterations, FP32 refinement and
+# Rayleigh-Ritz): measured on a GB300 at most 2.8e-4 (sigma, relative) and
+# 9.9e-2 rad (principal angle on the gapped prefix), asserted at about twice that
+MIXED_TOL_S, MIXED_TOL_ANGLE, MIXED_TOL_ORTH = 6e-4, 2e-1, 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_batched_matches_oracle(problems, precision):
+    """Every problem of the batch against the oracle's Alg. 1 with its own
+    seed: FP32 within the single-call tolerances (sigma within relative 1e-5
+    per value, principal angles below 1e-3 rad on the gapped prefix,
+    orthonormality 1e-5, residuals no worse than the oracle's); the mixed path
+    within its stated error."""
     graphs, ops, ranks = problems
-    batch = isvd.Batch(ops, ranks, oversample=10, iters=4, seed=SEED)
+    batch = isvd.Batch(ops, ranks, oversample=10, iters=4, seed=SEED, precision=precision)
     U, S, V = batch.run()
-    for i in (1, 2):
-        oop = oracle.graph_operator(graphs[i], coeffs=C5, ones_coeff=-LAM)
-        Uo, So, Vo, _ = oop.isvd(ranks[i], 10, 4, SEED + i)
-        s = S[i].double().cpu().numpy()
-        assert np.abs(s - So).max() <= 1e-5 * So[0]
+    for i, g in enumerate(graphs):
+        oop = oracle.graph_operator(g, coeffs=C5, ones_coeff=-LAM)
+        out = measure_svd(npy(U[i]), npy(S[i]), npy(V[i]), oop, ranks[i], 10, 4, SEED + i)
+        print(i, precision, out)
+        if precision == "fp32":
+            assert_svd(out)
+        else:
+            assert_svd(out, MIXED_TOL_S, MIXED_TOL_ANGLE, MIXED_TOL_ORTH)
 
 
 def test_batched_rejects_repeated_operator(problems):
