@@ -27,6 +27,9 @@
  *     the legacy default stream).  isvd_create_operator synchronises once to
  *     validate its input.  Calls on one operator must be ordered (one stream,
  *     or explicit events): the operator owns a reusable workspace.
+ *   - One device per process: kernel attributes (shared-memory sizes,
+ *     cluster shapes) are set once per process, on the device current at the
+ *     first call into the library.
  *   - Errors are returned as isvd_status; no exception or abort crosses the
  *     ABI.  isvd_last_error() returns a thread-local detail string.  Errors
  *     that only the GPU can see (CholeskyQR breakdown) are written to a
@@ -243,9 +246,15 @@ ISVD_API isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t ro
  * library holds until the process exits.
  *   - Same arguments and results as isvd_orthonormalize (no operator), but
  *     l <= ISVD_NOALLOC_MAX_BLOCK (64); larger l returns ISVD_ERR_UNSUPPORTED.
- *   - The first call on a device sets up that device (looks up the array's
- *     device address and kernel attributes): make it before any stream
- *     capture on that device.
+ *   - The first call on a device sets up that device: it looks up the
+ *     array's device address, and loading the library's code for that device
+ *     (the array itself and the kernels, on their first use) makes the CUDA
+ *     driver allocate device memory.  Make that first call outside the
+ *     no-allocation context, as a warm-up, and before any stream capture on
+ *     that device; later calls allocate nothing.
+ *   - Kernel attributes (shared-memory sizes, cluster shapes) are set once
+ *     per process, on the device current at the first call into the
+ *     library: use the library from one device per process.
  *   - Every call shares the one array: calls that overlap on the GPU (other
  *     streams, other host threads) race and corrupt each other's results.
  *     Order them on one stream.  dev_info NULL uses a slot in the array that

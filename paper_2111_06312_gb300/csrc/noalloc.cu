@@ -34,8 +34,10 @@ std::mutex g_setup_mutex;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the array
-// (in host code its name is only a host-side stand-in) and the kernel
-// attributes the orthonormalisation kernels need.
+// (in host code its name is only a host-side stand-in).  The kernel
+// attributes the orthonormalisation kernels need are set here too, but once
+// per process (the library's init functions), so the library serves one
+// device per process.
 isvd_status setup_device(unsigned char **out) {
   int dev = 0;
   ISVD_CUDA_TRY(cudaGetDevice(&dev));
