@@ -307,6 +307,100 @@ def relative_residuals(op, U, S, V):
     return (r / S).double().cpu().numpy()
 
 
+def batched_section(args, flush, stream):
+    """Many uneven problems (256 seeded graphs, n ~ U[500, 50,000], mean degree
+    8, rank drawn from {16, 32, 64}, oversample 10, 4 power iterations): one
+    isvd_svd_batched call against one isvd_svd call per problem, FP32 and
+    mixed; equal error as for the single SVD, with the error the largest over
+    all problems."""
+    import torch
+
+    from paper_2111_06312_gb300 import isvd, synth
+
+    graphs, ranks = synth.workload_batched()
+    seed, p, q = 20211106315, 10, 4
+    ops = [isvd.graph_operator(gr, coeffs=coeffs5(), ones_coeff=-LAM) for gr in graphs]
+    try:
+        def batch_ms(prec, iters):
+            b = isvd.Batch(ops, ranks, oversample=p, iters=iters, seed=seed, precision=prec)
+            b.run()
+            ms = float(np.mean(timed_steps(lambda: b.run(check=False), args.steps, flush, stream)))
+            b.run()
+            torch.cuda.synchronize()
+            err = max(float(relative_residuals(op, b.U[i], b.S[i], b.V[i]).max()) for i, op in enumerate(ops))
+            return ms, err
+
+        ms32, err32 = batch_ms("fp32", q)
+        msm, errm = batch_ms("mixed", q)
+        eq = None
+        for qm in range(q, q + 5):
+            t, e = (msm, errm) if qm == q else batch_ms("mixed", qm)
+            if e <= err32:
+                eq = {"iters": qm, "ms": t, "max_rel_residual": e, "speedup_mixed_over_fp32": ms32 / t}
+                break
+        outs = [(isvd.new_block(op.shape[0], k), isvd.new_block(op.shape[1], k), torch.empty(k, device="cuda"))
+                for op, k in zip(ops, ranks)]
+        info = torch.zeros(4, dtype=torch.int32, device="cuda")
+
+        def singles():
+            for i, (op, k) in enumerate(zip(ops, ranks)):
+                U, V, S = outs[i]
+                op.svd(k, p, q, seed=seed + i, U=U, S=S, V=V, info=info, check=False)
+
+        singles()
+        single_ms = float(np.mean(timed_steps(singles, max(1, args.steps // 2), flush, stream)))
+        return {"count": len(ops), "sum_n": int(sum(gr.n for gr in graphs)),
+                "sum_nnz": int(sum(gr.nnz for gr in graphs)), "oversample": p, "iters": q,
+                "batched_fp32_ms": ms32, "single_calls_fp32_ms": single_ms, "speedup_batched_over_single": single_ms / ms32,
+                "batched_mixed_ms": msm, "fp32_max_rel_residual": err32, "mixed_max_rel_residual": errm,
+                "mixed_at_equal_error": eq,
+                "error": "largest over all problems of max_i r_i / s_i (library FP32 products)"}
+    finally:
+        for op in ops:
+            op.close()
+
+
+def finetune_section(args, flush, stream):
+    """Fine-tuning step of the linear model Y = M W, M = [X | ÂX | Â^2 X]
+    (ogbn-arxiv-sized: n = 169,343, 1.17M directed edges, dense X n x 128,
+    40 outputs, W 384 x 40 from the closed form of a rank-40 iSVD): forward
+    M W, backward M^T dY, and one whole epoch (forward, cross-entropy on the
+    training rows, backward, Adam step)."""
+    import torch
+
+    from paper_2111_06312_gb300 import adjoint, isvd, synth
+
+    g, x, y, train = synth.workload_finetune()
+    with isvd.Operator(g.n, g.rowptr, g.colidx, form="concat", norm="sym", X=x, L=2) as op:
+        labels = torch.as_tensor(y).cuda()
+        mask = torch.as_tensor(train).cuda()
+        idx = torch.nonzero(mask).reshape(-1)
+        Ylab = adjoint.one_hot_train(labels, mask, 40)
+        W0, _ = adjoint.closed_form_init(op, Ylab, k=40, oversample=10, iters=4, seed=4)
+        init_ms = float(np.mean(timed_steps(
+            lambda: adjoint.closed_form_init(op, Ylab, k=40, oversample=10, iters=4, seed=4), 3, flush, stream)))
+        model = adjoint.ImplicitLinear(op, W0)
+        opt = torch.optim.Adam(model.parameters(), lr=1e-3)
+
+        def epoch():
+            opt.zero_grad()
+            loss = torch.nn.functional.cross_entropy(model()[idx], labels[idx])
+            loss.backward()
+            opt.step()
+
+        for _ in range(3):
+            epoch()
+        epoch_ms = float(np.mean(timed_steps(epoch, args.steps, flush, stream)))
+        r, c = op.shape
+        dY = torch.randn((r, 40), device="cuda")
+        Yb = isvd.new_block(r, 40)
+        dWb = isvd.new_block(c, 40)
+        fwd = float(np.mean(timed_steps(lambda: op.apply(W0, out=Yb), args.steps, flush, stream)))
+        bwd = float(np.mean(timed_steps(lambda: op.apply(dY, out=dWb, transpose=True), args.steps, flush, stream)))
+        return {"n": g.n, "nnz": g.nnz, "d": int(x.shape[1]), "outputs": 40, "forward_ms": fwd, "backward_ms": bwd,
+                "forward_plus_backward_ms": fwd + bwd, "epoch_ms": epoch_ms, "closed_form_init_ms": init_ms}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -472,6 +566,11 @@ def run_ours(args):
                "includes": "H2D of the CSR, operator construction (validation, symmetry check, work lists), "
                            "FP32 SVD, D2H of U, S, V"}
 
+    extras = {}
+    if not args.no_extras:
+        extras["batched"] = batched_section(args, flush, stream)
+        extras["finetune"] = finetune_section(args, flush, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -498,7 +597,7 @@ def run_ours(args):
             "step_ms": step_ms, "construct_ms": construct_ms,
             "mixed": {"iters": q, "ms": mixed_ms, "dtype": "bf16+f32", "speedup_at_same_iters": ms / mixed_ms},
             "equal_error": eq,
-            "spmm": spmm, "roofline": roofline,
+            "spmm": spmm, "roofline": roofline, **extras,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(kernels_per_step * args.steps) if kernels_per_step > 0 else None,
             "device_status": st,
@@ -506,6 +605,30 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_case_orth(args):
+    """CholeskyQR2 (isvd_orthonormalize) of a seeded N(0,1) block of
+    `--rows` x `--width` FP32, one JSON line per repetition set: a fixed case
+    for profiling the orthonormalisation kernels (Gram, FP64 Cholesky, Q R^-1)."""
+    import torch
+
+    from paper_2111_06312_gb300 import build as libbuild
+    from paper_2111_06312_gb300 import isvd, synth
+
+    libbuild.build()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with isvd.graph_operator(synth.cycle(64), coeffs=[1.0]) as op:
+        Q0 = isvd.gaussian(3, args.rows, args.width)
+        Q = Q0.clone()
+        _, _, info = isvd.orthonormalize(op, Q, want_r=False)
+        Qd = Q.double()
+        orth = float((Qd.T @ Qd - torch.eye(args.width, dtype=torch.float64, device=Q.device)).abs().max())
+        passes = isvd.info_dict(info)["cholqr_passes"]
+        stream = torch.cuda.current_stream()
+        ms = timed_steps(lambda: (Q.copy_(Q0), isvd.orthonormalize(op, Q, want_r=False)), args.steps, flush, stream)
+    print(json.dumps({"case": "orth", "rows": args.rows, "width": args.width, "ms_incl_copy": float(np.median(ms)),
+                      "orthogonality": orth, "passes": passes}), flush=True)
 
 
 def main():
@@ -517,8 +640,15 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ne_large")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and fine-tuning sections")
+    ap.add_argument("--case", choices=["svd", "orth"], default="svd",
+                    help="orth: only the CholeskyQR2 of a --rows x --width block (a profiling case)")
+    ap.add_argument("--rows", type=int, default=1_000_000)
+    ap.add_argument("--width", type=int, default=144)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case == "orth":
+        run_case_orth(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
