@@ -311,6 +311,18 @@ ISVD_API isvd_status isvd_compose_operators(isvd_compose kind, isvd_operator *co
                                             const double *weights, const isvd_allocator *alloc, void *stream,
                                             isvd_operator **out);
 
+/* Lazy product cache of a composite (App. A.3: intermediate products cached
+ * by the chain of operators applied to the input).  At composition the tree
+ * is walked in evaluation order and every product that one evaluation forms
+ * more than once (the same child applied to the same input: N G inside
+ * N^2 + N, N^T H inside [N | N^2]^T H, M G inside [M ; M]) gets a slot of
+ * the apply workspace (rows x round8(b) elements each); a call then forms it
+ * once and reads it from its slot afterwards.  The results are bit for bit
+ * those of the uncached evaluation.  enable = 0 turns the cache off for this
+ * composite (evaluated as the root of a call), 1 (the default) on; drops
+ * captured graphs.  Errors: INVALID_ARGUMENT (null, or a leaf operator). */
+ISVD_API isvd_status isvd_composite_cache(isvd_operator *op, int32_t enable);
+
 /* Network-embedding outputs of a rank-k SVD (Sec. 3.1): the rows and columns
  * of M are embedded as L = U diag(S)^1/2 and R = V diag(S)^1/2, so that
  * L R^T = U diag(S) V^T.  One call scales one factor: out = X diag(S)^1/2.

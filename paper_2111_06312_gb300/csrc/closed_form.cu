@@ -154,21 +154,34 @@ int32_t closed_form_parts(int64_t rows, int32_t k, int32_t m) {
   const int64_t cap = (2 * kNumSMs + tiles - 1) / tiles;
   if (parts > cap) parts = cap;
   if (parts < 1) parts = 1;
-  return (int32_t)parts;
+  // room for the tensor-core form's partial count too
+  return std::max<int32_t>((int32_t)parts, gram_ab_parts(rows));
 }
 
+// U^T Y on the tensor cores (k <= 128, m <= 160) or the CUDA cores, then
+// Z = diag(S)^+ (U^T Y), then W = V Z on the tensor cores where the layout
+// suits them.  nparts: the capacity of `partial` (closed_form_parts).
 cudaError_t closed_form_launch(const float *U, int64_t ldu, const float *S, const float *V, int64_t ldv, int64_t r,
                                int64_t c, int32_t k, const float *Y, int64_t ldy, int32_t m, double rcond,
                                float *W, int64_t ldw, double *partial, int32_t nparts, float *Z, cudaStream_t s) {
-  const int tiles = ((k + kTnTile - 1) / kTnTile) * ((m + kTnTile - 1) / kTnTile);
-  const int64_t rpp = round_up(ceil_div(r, nparts), kTnRows);
-  tn_partial_kernel<<<dim3((unsigned)nparts, (unsigned)tiles), 256, 0, s>>>(U, ldu, Y, ldy, r, k, m, rpp, partial);
-  cudaError_t e = cudaGetLastError();
+  bool tc = false;
+  int32_t used = std::min(nparts, gram_ab_parts(r));
+  cudaError_t e = gram_ab_launch(U, ldu, k, Y, ldy, m, r, partial, used, nullptr, &tc, s);
   if (e != cudaSuccess) return e;
-  closed_form_reduce_kernel<<<(unsigned)ceil_div((int64_t)k * m, 256), 256, 0, s>>>(partial, nparts, k, m, S, rcond,
-                                                                                   Z);
+  if (!tc) {
+    const int tiles = ((k + kTnTile - 1) / kTnTile) * ((m + kTnTile - 1) / kTnTile);
+    used = nparts;
+    const int64_t rpp = round_up(ceil_div(r, used), kTnRows);
+    tn_partial_kernel<<<dim3((unsigned)used, (unsigned)tiles), 256, 0, s>>>(U, ldu, Y, ldy, r, k, m, rpp, partial);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  closed_form_reduce_kernel<<<(unsigned)ceil_div((int64_t)k * m, 256), 256, 0, s>>>(partial, used, k, m, S, rcond, Z);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  bool launched = false;
+  e = gemm_tc_launch(V, ldv, c, k, Z, m, m, W, ldw, &launched, s);
+  if (e != cudaSuccess || launched) return e;
   return gemm_small_launch(V, ldv, DT_F32, c, k, Z, m, m, false, W, ldw, DT_F32, PassGate{}, s);
 }
 

@@ -227,6 +227,16 @@ cudaError_t pair_scores_launch(const float *L, int64_t ldl, int64_t rows, const 
                                int32_t k, const int32_t *src, const int32_t *dst, int64_t n_pairs, float *out,
                                isvd_info *info, cudaStream_t s);
 
+// C (p x q, FP64 partials per row part: [parts][p][q]) = A^T B over `rows`
+// rows on the tensor cores (gram_ab_tc.cu), p <= 128, q <= 160, A and B FP32
+// with 16-byte aligned bases and rows; *launched = false (nothing enqueued)
+// otherwise.  err (nullable, device int32): set to 1 when a bounded wait
+// gave up.  gram_ab_parts: the partial count it uses for `rows` rows.
+int32_t gram_ab_parts(int64_t rows);
+cudaError_t gram_ab_launch(const float *A, int64_t lda, int32_t p, const float *B, int64_t ldb, int32_t q,
+                           int64_t rows, double *partial, int32_t parts, int32_t *err, bool *launched,
+                           cudaStream_t s);
+
 // C (p x q, FP64 partials per row part) = A^T B over `rows` rows (closed_form.cu).
 int32_t tn_tiles(int32_t p, int32_t q);
 cudaError_t tn_partial_launch(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t rows, int32_t p,
@@ -331,6 +341,12 @@ struct isvd_operator {
   int32_t compose = -1;
   std::vector<isvd_operator *> child;
   std::vector<double> weight;
+  // lazy product cache (App. A.3): the products (a child applied to a given
+  // input) that one evaluation of this tree forms more than once, per
+  // direction [transpose], each with a slot of the apply scratch; planned at
+  // composition from the tree's structure
+  std::vector<uint64_t> cache_keys[2];
+  int32_t cache_on = 1;
 };
 
 namespace isvd {
@@ -356,6 +372,9 @@ struct ApplyScratch {
   // composite nodes: two block temporaries and the children's scratch
   void *ct1 = nullptr, *ct2 = nullptr;
   char *child_base = nullptr;
+  // root composite: the lazy product cache's slots
+  char *cache_base = nullptr;
+  size_t cache_slot_bytes = 0;
 };
 // Generation of an operator and everything below it (composite graphs go
 // stale when a child's workspace or launch shapes change).

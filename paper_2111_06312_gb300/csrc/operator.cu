@@ -855,15 +855,37 @@ static int64_t composite_span(const isvd_operator *op) {
   return m;
 }
 
+// Largest row count of any product in the tree (a cache slot's rows).
+static int64_t tree_span(const isvd_operator *op) {
+  int64_t m = std::max(op->rows, op->cols);
+  for (const isvd_operator *c : op->child) m = std::max(m, tree_span(c));
+  return m;
+}
+
+static size_t cache_slot_bytes(const isvd_operator *op, int32_t b, int dtype) {
+  return (size_t)round_up((int64_t)(dtype_size(dtype) * tree_span(op) * round_up(b, 8)), 256);
+}
+
+// Scratch of a composite evaluated as a child (no cache region of its own).
+static size_t composite_core_bytes(const isvd_operator *op, int32_t b, int dtype, bool transpose) {
+  const size_t es = dtype_size(dtype);
+  const int64_t bseg = round_up(b, 8);
+  // two temporaries, then one region the children use in turn
+  const size_t t = (size_t)round_up((int64_t)(es * composite_span(op) * bseg), 256);
+  size_t cmax = 0;
+  for (const isvd_operator *c : op->child)
+    cmax = std::max(cmax, c->compose >= 0 ? composite_core_bytes(c, b, dtype, transpose)
+                                          : apply_scratch_bytes(c, b, dtype, transpose));
+  return 2 * t + cmax;
+}
+
 size_t apply_scratch_bytes(const isvd_operator *op, int32_t b, int dtype, bool transpose) {
   const size_t es = dtype_size(dtype);
   const int64_t bseg = round_up(b, 8);
   if (op->compose >= 0) {
-    // two temporaries, then one region the children use in turn
-    const size_t t = (size_t)round_up((int64_t)(es * composite_span(op) * bseg), 256);
-    size_t cmax = 0;
-    for (const isvd_operator *c : op->child) cmax = std::max(cmax, apply_scratch_bytes(c, b, dtype, transpose));
-    return 2 * t + cmax;
+    // as the root of an evaluation: the slots of its lazy product cache follow
+    const size_t slots = op->cache_on ? op->cache_keys[transpose ? 1 : 0].size() : 0;
+    return composite_core_bytes(op, b, dtype, transpose) + slots * cache_slot_bytes(op, b, dtype);
   }
   size_t total = 0;
   auto add = [&](size_t x) { total += (size_t)round_up((int64_t)x, 256); };
@@ -895,6 +917,8 @@ void apply_scratch_carve(const isvd_operator *op, int32_t b, int dtype, bool tra
     sc->ct1 = base;
     sc->ct2 = base + t;
     sc->child_base = base + 2 * t;
+    sc->cache_base = base + composite_core_bytes(op, b, dtype, transpose);
+    sc->cache_slot_bytes = cache_slot_bytes(op, b, dtype);
     return;
   }
   size_t off = 0;
@@ -1154,6 +1178,82 @@ static cudaError_t axpy_launch(const void *x, int64_t ldx, void *y, int64_t ldy,
   return cudaGetLastError();
 }
 
+// Identity of a product during one evaluation of a composite tree (the lazy
+// cache of App. A.3): the root's input is token 1; a child applied to the
+// input with token t gives the product with token key(child, t, transpose);
+// the rows of an input from row `off` on (the block of a concatenation's
+// child) have token slice(t, off).  Equal tokens are the same matrix.
+static uint64_t mix64(uint64_t x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+static uint64_t product_key(const isvd_operator *c, uint64_t tok, bool transpose) {
+  return mix64(mix64(tok ^ 0x9e3779b97f4a7c15ull) + c->serial * 2 + (transpose ? 1 : 0));
+}
+static uint64_t slice_token(uint64_t tok, int64_t off) {
+  return mix64(mix64(tok + 0x632be59bd9b4e019ull) ^ (uint64_t)off);
+}
+
+// Walk the tree in evaluation order (as apply_composite does) and count each
+// product; a composite child whose product was seen before is not walked
+// again (its evaluation will come from the cache).
+static void plan_walk(const isvd_operator *op, uint64_t tok, bool transpose, std::vector<std::pair<uint64_t, int>> &cnt) {
+  auto visit = [&](const isvd_operator *c, uint64_t in) {
+    const uint64_t k = product_key(c, in, transpose);
+    for (auto &e : cnt)
+      if (e.first == k) {
+        ++e.second;
+        return k;
+      }
+    cnt.emplace_back(k, 1);
+    if (c->compose >= 0) plan_walk(c, in, transpose, cnt);
+    return k;
+  };
+  const int m = (int)op->child.size();
+  const bool summing = op->compose == ISVD_COMPOSE_SUM || (op->compose == ISVD_COMPOSE_HCAT && !transpose) ||
+                       (op->compose == ISVD_COMPOSE_VCAT && transpose);
+  if (op->compose == ISVD_COMPOSE_PRODUCT) {
+    uint64_t cur = tok;
+    for (int step = 0; step < m; ++step) cur = visit(op->child[transpose ? step : m - 1 - step], cur);
+    return;
+  }
+  int64_t off = 0;
+  for (int i = 0; i < m; ++i) {
+    const isvd_operator *c = op->child[i];
+    const uint64_t in = summing && op->compose != ISVD_COMPOSE_SUM ? slice_token(tok, off) : tok;
+    visit(c, in);
+    off += op->compose == ISVD_COMPOSE_HCAT ? c->cols : c->rows;
+  }
+}
+
+void plan_product_cache(isvd_operator *op) {
+  for (int t = 0; t < 2; ++t) {
+    std::vector<std::pair<uint64_t, int>> cnt;
+    plan_walk(op, 1, t == 1, cnt);
+    op->cache_keys[t].clear();
+    for (const auto &e : cnt)
+      if (e.second > 1) op->cache_keys[t].push_back(e.first);
+  }
+}
+
+// The cache of one evaluation: slot i holds the product with token keys[i]
+// once done[i].
+struct ProductCache {
+  const std::vector<uint64_t> *keys = nullptr;
+  char *base = nullptr;
+  size_t slot_bytes = 0;
+  bool done[ISVD_MAX_CHILDREN * 8] = {};
+  int find(uint64_t k) const {
+    if (!keys) return -1;
+    for (size_t i = 0; i < keys->size() && i < sizeof done; ++i)
+      if ((*keys)[i] == k) return (int)i;
+    return -1;
+  }
+};
+
 // Products of a composite node from its children's (Sec. 4, App. A.3):
 //   (sum_i w_i M_i) G = sum_i w_i (M_i G), and likewise for the transpose;
 //   [M_1 | ...] G = sum_i M_i G_i (G_i: the rows of G meeting M_i's columns),
@@ -1161,34 +1261,70 @@ static cudaError_t axpy_launch(const void *x, int64_t ldx, void *y, int64_t ldy,
 //   [M_1 ; ...]^T H = sum_i M_i^T H_i;  (M_1 ... M_m) G = M_1 (... (M_m G)),
 //   (M_1 ... M_m)^T H = M_m^T (... (M_1^T H)).
 // Children run one after another on the stream and share one scratch region;
-// sums accumulate into `out` through one block pass per extra child.
+// sums accumulate into `out` through one block pass per extra child.  A
+// product that the tree forms more than once (the same child on the same
+// input, e.g. N G inside N^2 + N, or N^T H in [N | N^2]^T H) is formed once
+// into a cache slot and read from there afterwards (the lazy cache of App.
+// A.3, keyed by the chain of operators applied to the input).
 static isvd_status apply_composite(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo,
-                                   int dtype, bool transpose, const ApplyScratch &sc, cudaStream_t s) {
+                                   int dtype, bool transpose, const ApplyScratch &sc, cudaStream_t s,
+                                   ProductCache *pc, uint64_t tok) {
   const size_t es = dtype_size(dtype);
   const int64_t ldz = round_up(b, 8);
   const int m = (int)op->child.size();
-  auto child_apply = [&](isvd_operator *c, const void *in, int64_t ldi, void *o, int64_t ldoo) {
-    ApplyScratch cs;
-    apply_scratch_carve(c, b, dtype, transpose, sc.child_base, &cs);
-    return apply_impl(c, in, ldi, b, o, ldoo, dtype, transpose, cs, s);
+  ProductCache own;
+  if (!pc) {  // the root of this evaluation
+    own.keys = op->cache_on ? &op->cache_keys[transpose ? 1 : 0] : nullptr;
+    own.base = sc.cache_base;
+    own.slot_bytes = sc.cache_slot_bytes;
+    pc = &own;
+  }
+  // child c on `in` (token in_tok): the product lands in `o` (ld ldoo), or in
+  // its cache slot, whose address is returned in *res (ld ldz) -- then the
+  // caller reads it from there
+  auto child_apply = [&](isvd_operator *c, const void *in, int64_t ldi, uint64_t in_tok, void *o, int64_t ldoo,
+                         const void **res, int64_t *ldres) -> isvd_status {
+    const uint64_t key = product_key(c, in_tok, transpose);
+    const int slot = pc->find(key);
+    void *dst = o;
+    int64_t ldd = ldoo;
+    if (slot >= 0) {
+      dst = pc->base + (size_t)slot * pc->slot_bytes;
+      ldd = ldz;
+    }
+    if (slot < 0 || !pc->done[slot]) {
+      ApplyScratch cs;
+      apply_scratch_carve(c, b, dtype, transpose, sc.child_base, &cs);
+      if (c->compose >= 0) ISVD_TRY(apply_composite(c, in, ldi, b, dst, ldd, dtype, transpose, cs, s, pc, in_tok));
+      else ISVD_TRY(apply_impl(c, in, ldi, b, dst, ldd, dtype, transpose, cs, s));
+      if (slot >= 0) pc->done[slot] = true;
+    }
+    *res = dst;
+    *ldres = ldd;
+    return ISVD_OK;
+  };
+  // out-of-place result into o (o = w x + [o])
+  auto deliver = [&](const void *res, int64_t ldr, void *o, int64_t ldoo, int64_t rows, double w, bool first) {
+    if (res == o && first && w == 1.0) return cudaSuccess;
+    if (res == o && first) return axpy_launch(o, ldoo, o, ldoo, rows, b, w, true, dtype, s);
+    return axpy_launch(res, ldr, o, ldoo, rows, b, w, first, dtype, s);
   };
   auto rows_at = [&](const void *p, int64_t ld, int64_t r0) { return (char *)p + (size_t)r0 * ld * es; };
   const int64_t rows_out = transpose ? op->cols : op->rows;
   const bool summing = op->compose == ISVD_COMPOSE_SUM || (op->compose == ISVD_COMPOSE_HCAT && !transpose) ||
                        (op->compose == ISVD_COMPOSE_VCAT && transpose);
+  const void *res = nullptr;
+  int64_t ldr = 0;
   if (summing) {
     int64_t off = 0;  // first row of G_i (concatenations)
     for (int i = 0; i < m; ++i) {
       isvd_operator *c = op->child[i];
-      const void *in = op->compose == ISVD_COMPOSE_SUM ? G : (const void *)rows_at(G, ldg, off);
+      const bool whole = op->compose == ISVD_COMPOSE_SUM;
+      const void *in = whole ? G : (const void *)rows_at(G, ldg, off);
+      const uint64_t in_tok = whole ? tok : slice_token(tok, off);
       const double w = op->weight[i];
-      if (i == 0) {
-        ISVD_TRY(child_apply(c, in, ldg, out, ldo));
-        if (w != 1.0) ISVD_CUDA_TRY(axpy_launch(out, ldo, out, ldo, rows_out, b, w, true, dtype, s));
-      } else {
-        ISVD_TRY(child_apply(c, in, ldg, sc.ct1, ldz));
-        ISVD_CUDA_TRY(axpy_launch(sc.ct1, ldz, out, ldo, rows_out, b, w, false, dtype, s));
-      }
+      ISVD_TRY(child_apply(c, in, ldg, in_tok, i == 0 ? out : sc.ct1, i == 0 ? ldo : ldz, &res, &ldr));
+      ISVD_CUDA_TRY(deliver(res, ldr, out, ldo, rows_out, w, i == 0));
       off += op->compose == ISVD_COMPOSE_HCAT ? c->cols : c->rows;
     }
     return ISVD_OK;
@@ -1197,22 +1333,32 @@ static isvd_status apply_composite(isvd_operator *op, const void *G, int64_t ldg
     int64_t off = 0;  // first row of child i's block of out
     for (int i = 0; i < m; ++i) {
       isvd_operator *c = op->child[i];
-      ISVD_TRY(child_apply(c, G, ldg, rows_at(out, ldo, off), ldo));
-      off += op->compose == ISVD_COMPOSE_HCAT ? c->cols : c->rows;
+      const int64_t crows = op->compose == ISVD_COMPOSE_HCAT ? c->cols : c->rows;
+      void *o = rows_at(out, ldo, off);
+      ISVD_TRY(child_apply(c, G, ldg, tok, o, ldo, &res, &ldr));
+      ISVD_CUDA_TRY(deliver(res, ldr, o, ldo, crows, 1.0, true));
+      off += crows;
     }
     return ISVD_OK;
   }
   // product: right to left (transpose: left to right), two temporaries in turn
   const void *cur = G;
   int64_t ldc = ldg;
+  uint64_t cur_tok = tok;
   void *tmp[2] = {sc.ct1, sc.ct2};
+  int which = 0;
   for (int step = 0; step < m; ++step) {
     isvd_operator *c = op->child[transpose ? step : m - 1 - step];
     const bool last = step == m - 1;
-    void *dst = last ? out : tmp[step & 1];
-    ISVD_TRY(child_apply(c, cur, ldc, dst, last ? ldo : ldz));
-    cur = dst;
-    ldc = ldz;
+    // the temporary that does not hold the current input
+    if (tmp[which] == cur) which ^= 1;
+    void *dst = last ? out : tmp[which];
+    ISVD_TRY(child_apply(c, cur, ldc, cur_tok, dst, last ? ldo : ldz, &res, &ldr));
+    if (last) ISVD_CUDA_TRY(deliver(res, ldr, out, ldo, rows_out, 1.0, true));
+    cur = res;
+    ldc = ldr;
+    cur_tok = product_key(c, cur_tok, transpose);
+    which ^= 1;
   }
   return ISVD_OK;
 }
@@ -1226,7 +1372,7 @@ uint64_t tree_generation(const isvd_operator *op) {
 // With a row gather S: (S M) G = S (M G) and (S M)^T H = M^T (S^T H).
 isvd_status apply_impl(isvd_operator *op, const void *G, int64_t ldg, int32_t b, void *out, int64_t ldo, int dtype,
                        bool transpose, const ApplyScratch &sc, cudaStream_t s) {
-  if (op->compose >= 0) return apply_composite(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
+  if (op->compose >= 0) return apply_composite(op, G, ldg, b, out, ldo, dtype, transpose, sc, s, nullptr, 1);
   const isvd_operator_desc &d = op->desc;
   if (!d.gather_rows) return apply_form(op, G, ldg, b, out, ldo, dtype, transpose, sc, s);
   const int64_t ldz = round_up(b, 8);
@@ -1342,6 +1488,7 @@ isvd_status isvd_compose_operators(isvd_compose kind, isvd_operator *const *ops,
   op->weight = weights ? std::vector<double>(weights, weights + count) : std::vector<double>(count, 1.0);
   op->rows = rows;
   op->cols = cols;
+  plan_product_cache(op);
   if (alloc) {
     op->alloc = *alloc;
     op->has_alloc = true;
@@ -1354,6 +1501,14 @@ isvd_status isvd_compose_operators(isvd_compose kind, isvd_operator *const *ops,
     return fail(ISVD_ERR_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
   }
   *out = op;
+  return ISVD_OK;
+}
+
+isvd_status isvd_composite_cache(isvd_operator *op, int32_t enable) {
+  if (!op) return fail(ISVD_ERR_INVALID_ARGUMENT, "null operator");
+  if (op->compose < 0) return fail(ISVD_ERR_INVALID_ARGUMENT, "the product cache belongs to composite operators");
+  op->cache_on = enable ? 1 : 0;
+  invalidate_graphs(op);
   return ISVD_OK;
 }
 

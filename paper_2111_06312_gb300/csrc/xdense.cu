@@ -4,10 +4,13 @@
 //   forward   P = X [G_0 | ... | G_L]       (n x d times d x (L+1) b, one pass over X)
 //   transpose out_l = X^T P_l, stacked       (d x n times n x (L+1) b, split over rows)
 // The forward product restacks the (L+1) d x b input blocks side by side
-// (FP32) and runs the small-matrix product of the Rayleigh-Ritz step; the
-// transposed product reuses the row-split X^T P partial sums of the
-// closed-form weights (FP64 across row parts, fixed order) and writes each
-// d x b segment to its place in the (L+1) d x b output.
+// (FP32) and runs X B on the tensor cores (the Q.B kernel that closes Alg. 1;
+// the CUDA-core small-matrix product for BF16 output or unsuitable layouts);
+// the transposed product takes X^T P on the tensor cores (A^T B with FP64
+// partials per row range, added in a fixed order) and writes each d x b
+// segment to its place in the (L+1) d x b output.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace isvd {
@@ -70,7 +73,7 @@ int grid_for(int64_t n) {
 
 size_t xdense_scratch_bytes(int32_t d, int32_t segs, int32_t bseg, int64_t n) {
   const int32_t q = segs * bseg;
-  const int32_t parts = xdense_parts(n, d, q);
+  const int32_t parts = std::max(xdense_parts(n, d, q), gram_ab_parts(n));
   return (size_t)round_up((int64_t)sizeof(float) * d * q, 256) + (size_t)round_up((int64_t)sizeof(double) * parts * d * q, 256);
 }
 
@@ -93,8 +96,14 @@ cudaError_t xdense_forward(const float *X, int64_t n, int32_t d, const void *G, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // all (L+1) segments, padding columns included (zero), in one pass over X;
-  // a single segment is the caller's block: its b columns only
+  // a single segment is the caller's block: its b columns only.  FP32 on the
+  // tensor cores (3xTF32) where the layout suits them
   const int32_t w = segs == 1 ? b : segs * bseg;
+  if (dtype == DT_F32) {
+    bool launched = false;
+    e = gemm_tc_launch(X, d, n, d, B, (int64_t)segs * bseg, w, reinterpret_cast<float *>(P), ldp, &launched, s);
+    if (e != cudaSuccess || launched) return e;
+  }
   return gemm_small_launch(X, d, DT_F32, n, d, B, (int64_t)segs * bseg, w, false, P, ldp, dtype, PassGate{}, s);
 }
 
@@ -102,15 +111,22 @@ cudaError_t xdense_transpose(const float *X, int64_t n, int32_t d, const float *
                              int32_t bseg, int32_t segs, float *P, int64_t ldp, float *out, int64_t ldo, void *scratch,
                              cudaStream_t s) {
   const int32_t q = segs * bseg;
-  const int32_t parts = xdense_parts(n, d, q);
   double *partial = reinterpret_cast<double *>(reinterpret_cast<char *>(scratch) +
                                                round_up((int64_t)sizeof(float) * d * q, 256));
   // segment 0 of P holds H itself
   copy_cols_kernel<<<grid_for(n * b), 256, 0, s>>>(H, ldh, P, ldp, n, b);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = tn_partial_launch(X, d, P, ldp, n, d, q, partial, parts, s);
+  // X^T P on the tensor cores where the shapes suit them (d <= 128, q <= 160)
+  bool tc = false;
+  int32_t parts = gram_ab_parts(n);
+  e = gram_ab_launch(X, d, d, P, ldp, q, n, partial, parts, nullptr, &tc, s);
   if (e != cudaSuccess) return e;
+  if (!tc) {
+    parts = xdense_parts(n, d, q);
+    e = tn_partial_launch(X, d, P, ldp, n, d, q, partial, parts, s);
+    if (e != cudaSuccess) return e;
+  }
   tn_reduce_stacked_kernel<<<(unsigned)ceil_div((int64_t)d * q, 256), 256, 0, s>>>(partial, parts, d, q, b, bseg, out,
                                                                                   ldo);
   return cudaGetLastError();

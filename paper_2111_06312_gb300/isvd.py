@@ -120,6 +120,7 @@ def lib():
             L.isvd_get_tuning.argtypes = [P, P]
             L.isvd_set_tuning.argtypes = [P, P, P]
             L.isvd_orthonormalize_noalloc.argtypes = [P, I64, I32, I64, P, P, P]
+            L.isvd_composite_cache.argtypes = [P, I32]
             L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
             L.isvd_autotune.argtypes = [P, I32, C.c_int, C.c_char_p, P, P]
             L.isvd_selftest_wait.argtypes = [I32, P, P]
@@ -136,6 +137,7 @@ def lib():
                          "isvd_closed_form", "isvd_compose_operators", "isvd_embed", "isvd_pair_scores",
                          "isvd_edge_kernel_weights", "isvd_edge_kernel_scores", "isvd_edge_kernel_loss",
                          "isvd_get_tuning", "isvd_set_tuning", "isvd_orthonormalize_noalloc", "isvd_svd_batched", "isvd_autotune",
+                         "isvd_composite_cache",
                          "isvd_selftest_wait"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -407,6 +409,11 @@ def compose(kind: str, ops, weights=None, use_torch_allocator=True) -> Operator:
     op.device = ops[0].device
     op.n = ops[0].n
     return op
+
+
+def set_product_cache(op: Operator, enable: bool) -> None:
+    """Turn a composite's lazy product cache (App. A.3) on or off."""
+    _check(lib().isvd_composite_cache(op._handle, 1 if enable else 0), "isvd_composite_cache")
 
 
 def scale(op: Operator, w: float) -> Operator:

@@ -449,3 +449,54 @@ def test_scalar_and_power_nodes(children, p, transpose):
         Yr = co.apply(npy(G), transpose=transpose)
         assert np.abs(npy(Y) - Yr).max() <= 1e-5 * np.abs(Yr).max()
         cg.close()
+
+
+def _spmm_launches(fn):
+    """Sparse-product kernel launches made by fn() (CUDA profiler trace)."""
+    from torch.profiler import ProfilerActivity, profile
+
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    return sum(e.count for e in prof.key_averages() if "spmm_" in e.key)
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_lazy_product_cache(hub_graph, transpose):
+    """The lazy cache of App. A.3 on composite trees with repeated products:
+    S = c_1 N + c_2 N^2 + c_3 N^3 (N = Â) written as a sum of powers forms
+    N G, N^2 G once each (3 products of N instead of 6), and H = [N | N^2]
+    forms N^T G once in the transposed product (2 instead of 3; the forward
+    product has nothing to share).  Cached and uncached results are bit for
+    bit equal, and both match the oracle's composite."""
+    g = hub_graph
+    with isvd.graph_operator(g, norm="sym", coeffs=[1.0], check_symmetry=False) as T:
+        ref_T = oracle.graph_operator(g, norm="sym", coeffs=[1.0])
+        c = [0.5, -0.3, 0.2]
+        p2, p3 = isvd.power(T, 2), isvd.power(T, 3)
+        S = isvd.compose("sum", [T, p2, p3], c)
+        H = isvd.compose("hcat", [T, p2])
+        refs = {"S": oracle.compose("sum", [ref_T, oracle.power(ref_T, 2), oracle.power(ref_T, 3)], c),
+                "H": oracle.compose("hcat", [ref_T, oracle.power(ref_T, 2)])}
+        expect = {"S": (3, 6), "H": (2, 3) if transpose else (3, 3)}
+        G1 = isvd.gaussian(1, g.n, 24)
+        T.apply(G1)
+        _spmm_launches(lambda: T.apply(G1))  # the first trace of a process may miss launches
+        one = _spmm_launches(lambda: T.apply(G1))  # sparse-product launches of one product with N
+        assert one >= 1
+        for name, op in (("S", S), ("H", H)):
+            rows_in = op.shape[0] if transpose else op.shape[1]
+            G = isvd.gaussian(12, rows_in, 24)
+            out = {}
+            counts = {}
+            for on in (True, False):
+                isvd.set_product_cache(op, on)
+                op.apply(G, transpose=transpose)  # warm the workspace
+                counts[on] = _spmm_launches(lambda: out.__setitem__(on, op.apply(G, transpose=transpose)))
+            assert torch.equal(out[True], out[False]), name
+            assert (counts[True], counts[False]) == (expect[name][0] * one, expect[name][1] * one), (name, counts, one)
+            Yr = refs[name].apply(npy(G), transpose=transpose)
+            assert np.abs(npy(out[True]) - Yr).max() <= 1e-5 * np.abs(Yr).max()
+        for op in (S, H, p3, p2):
+            op.close()

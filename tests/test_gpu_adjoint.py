@@ -128,5 +128,30 @@ def test_finetune_from_closed_form_lowers_the_loss(sub):
         loss = torch.nn.functional.cross_entropy(model()[idx], labels[idx])
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert losses[-1] < losses[0]
+
+
+def test_dense_contractions_run_on_tensor_cores(full):
+    """The dense contractions of the fine-tuning step (Sec. 3.3, Eq. 6 with
+    dense X): the forward X [W_0 | W_1 | W_2] and the weight gradient
+    X^T [dY | N dY | N^2 dY] run on the tcgen05 kernels (the Q.B product and
+    the A^T B contraction), and so do the closed form's U^T Y and V Z (Thm.
+    1): the CUDA-core fallbacks are not launched."""
+    from torch.profiler import ProfilerActivity, profile
+
+    g, x, y, train, gop, oop = full
+    W = torch.randn((384, 40), device="cuda")
+    dY = torch.randn((g.n, 40), device="cuda")
+    U, S, V, _ = gop.svd(40, 10, 2, 5)
+    Yl = torch.randn((g.n, 40), device="cuda")
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        gop.apply(W)
+        gop.apply(dY, transpose=True)
+        isvd.closed_form(gop, U, S, V, Yl)
+        torch.cuda.synchronize()
+    names = [e.key for e in prof.key_averages()]
+    assert any("gemm_tc_kernel" in k for k in names), names
+    assert any("gram_ab_tc_kernel" in k for k in names), names
+    assert not any("tn_partial_kernel" in k or "gemm_small_kernel" in k for k in names), names
