@@ -382,6 +382,30 @@ ISVD_API isvd_status isvd_edge_kernel_loss(const float *U, int64_t ldu, int64_t 
                                            double k_neg, double *out, double *work, int64_t work_doubles,
                                            isvd_info *dev_info, void *stream);
 
+/* Split-ReLU layer of the fine-tuning network (Sec. 5.2):
+ *     Z = [X Wp]_+ - [X Wn]_+        ([t]_+ = max(t, 0))
+ * X (n x d, ld ldx), Wp and Wn (d x e, row-major, ld e), all DEVICE FP32;
+ * 1 <= d, e <= ISVD_MAX_BLOCK.  The forward writes Z (n x e, ld ldz) and the
+ * pre-activations Ap = X Wp, An = X Wn (n x e each, ld lda), which the
+ * backward takes: with Gp = dZ * 1[Ap > 0] and Gn = -dZ * 1[An > 0],
+ *     dWp = X^T Gp, dWn = X^T Gn (d x e, ld e, written),
+ *     dX = Gp Wp^T + Gn Wn^T (n x d, ld lddx; dX NULL: not formed).
+ * The dense products run on the tensor cores (3xTF32) where the blocks'
+ * bases and row pitches are 16-byte aligned, on the CUDA cores otherwise;
+ * X^T G is summed in FP64 across row ranges in a fixed order.  `work`: DEVICE
+ * scratch of isvd_split_relu_work_bytes(n, d, e) bytes, 256-byte aligned,
+ * owned by the caller.  Asynchronous on `stream`.  Errors: INVALID_ARGUMENT
+ * (null pointer, leading dimension), SHAPE (d or e out of range), WORKSPACE
+ * (work too small or misaligned), CUDA. */
+ISVD_API size_t isvd_split_relu_work_bytes(int64_t n, int32_t d, int32_t e);
+ISVD_API isvd_status isvd_split_relu_forward(const float *X, int64_t ldx, int64_t n, int32_t d, const float *Wp,
+                                             const float *Wn, int32_t e, float *Z, int64_t ldz, float *Ap, float *An,
+                                             int64_t lda, void *stream);
+ISVD_API isvd_status isvd_split_relu_backward(const float *X, int64_t ldx, int64_t n, int32_t d, const float *Wp,
+                                              const float *Wn, int32_t e, const float *Ap, const float *An,
+                                              int64_t lda, const float *dZ, int64_t ldz, float *dX, int64_t lddx,
+                                              float *dWp, float *dWn, void *work, size_t work_bytes, void *stream);
+
 /* SVD of a small square upper-triangular-or-dense FP64 matrix by one-sided
  * Jacobi on its transpose (the Rayleigh-Ritz step of Alg. 1, done as
  * SVD(R^T) after a QR of B^T).  A (l x l, row-major, DEVICE) = Uo diag(S) Vo^T

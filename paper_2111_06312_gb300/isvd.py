@@ -121,6 +121,11 @@ def lib():
             L.isvd_set_tuning.argtypes = [P, P, P]
             L.isvd_orthonormalize_noalloc.argtypes = [P, I64, I32, I64, P, P, P]
             L.isvd_composite_cache.argtypes = [P, I32]
+            L.isvd_split_relu_work_bytes.argtypes = [I64, I32, I32]
+            L.isvd_split_relu_work_bytes.restype = C.c_size_t
+            L.isvd_split_relu_forward.argtypes = [P, I64, I64, I32, P, P, I32, P, I64, P, P, I64, P]
+            L.isvd_split_relu_backward.argtypes = [P, I64, I64, I32, P, P, I32, P, P, I64, P, I64, P, I64, P, P, P,
+                                                   C.c_size_t, P]
             L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
             L.isvd_autotune.argtypes = [P, I32, C.c_int, C.c_char_p, P, P]
             L.isvd_selftest_wait.argtypes = [I32, P, P]
@@ -137,7 +142,7 @@ def lib():
                          "isvd_closed_form", "isvd_compose_operators", "isvd_embed", "isvd_pair_scores",
                          "isvd_edge_kernel_weights", "isvd_edge_kernel_scores", "isvd_edge_kernel_loss",
                          "isvd_get_tuning", "isvd_set_tuning", "isvd_orthonormalize_noalloc", "isvd_svd_batched", "isvd_autotune",
-                         "isvd_composite_cache",
+                         "isvd_composite_cache", "isvd_split_relu_forward", "isvd_split_relu_backward",
                          "isvd_selftest_wait"):
                 getattr(L, name).restype = C.c_int
             _lib = L

@@ -9,8 +9,11 @@ the network equals the linear model [X | ÂX | ... | Â^L X] W* of Eq. 6 (Thm. 2
 and fine-tuning by cross-entropy starts from the closed-form fit.
 
 The propagation Â H and its adjoint Â^T dH are the library's sparse products
-(isvd_apply / isvd_apply_T on the operator N = Â); the d x d and d x y weight
-products and the ReLUs are PyTorch's (dense library GEMMs and elementwise ops).
+(isvd_apply / isvd_apply_T on the operator N = Â); every split-ReLU layer,
+forward and backward, is the library's too (isvd_split_relu_forward /
+_backward: the d x d and d x y weight products on the tensor cores, the ReLUs
+and their masks in the same calls).  PyTorch holds the parameters, runs Adam
+and the cross-entropy.
 """
 from __future__ import annotations
 
@@ -20,9 +23,50 @@ from . import isvd
 from .adjoint import implicit_matmul
 
 
+class _SplitReLU(torch.autograd.Function):
+    """Z = [X Wp]_+ - [X Wn]_+ through the library (forward keeps the two
+    pre-activations for the backward)."""
+
+    @staticmethod
+    def forward(ctx, X, Wp, Wn):
+        L = isvd.lib()
+        X = isvd._as_block(X.detach().float())
+        Wp_c = Wp.detach().float().contiguous()
+        Wn_c = Wn.detach().float().contiguous()
+        n, d = X.shape
+        e = Wp_c.shape[1]
+        Z = isvd.new_block(n, e, device=X.device)
+        Ap = isvd.new_block(n, e, device=X.device)
+        An = isvd.new_block(n, e, device=X.device)
+        isvd._check(L.isvd_split_relu_forward(isvd._ptr(X), X.stride(0), n, d, isvd._ptr(Wp_c), isvd._ptr(Wn_c), e,
+                                              isvd._ptr(Z), Z.stride(0), isvd._ptr(Ap), isvd._ptr(An), Ap.stride(0),
+                                              isvd._stream()), "isvd_split_relu_forward")
+        ctx.save_for_backward(X, Wp_c, Wn_c, Ap, An)
+        return Z
+
+    @staticmethod
+    def backward(ctx, dZ):
+        L = isvd.lib()
+        X, Wp, Wn, Ap, An = ctx.saved_tensors
+        n, d = X.shape
+        e = Wp.shape[1]
+        dZ = isvd._as_block(dZ.float())
+        dX = isvd.new_block(n, d, device=X.device) if ctx.needs_input_grad[0] else None
+        dWp = torch.empty((d, e), dtype=torch.float32, device=X.device)
+        dWn = torch.empty((d, e), dtype=torch.float32, device=X.device)
+        nbytes = int(L.isvd_split_relu_work_bytes(n, d, e))
+        work = torch.empty(nbytes, dtype=torch.uint8, device=X.device)
+        isvd._check(L.isvd_split_relu_backward(isvd._ptr(X), X.stride(0), n, d, isvd._ptr(Wp), isvd._ptr(Wn), e,
+                                               isvd._ptr(Ap), isvd._ptr(An), Ap.stride(0), isvd._ptr(dZ), dZ.stride(0),
+                                               isvd._ptr(dX), dX.stride(0) if dX is not None else 0, isvd._ptr(dWp),
+                                               isvd._ptr(dWn), isvd._ptr(work), nbytes, isvd._stream()),
+                    "isvd_split_relu_backward")
+        return dX, dWp, dWn
+
+
 def split_relu(X: torch.Tensor, Wp: torch.Tensor, Wn: torch.Tensor) -> torch.Tensor:
     """[X Wp]_+ - [X Wn]_+ (Sec. 5.2): linear in X when Wp = -Wn."""
-    return torch.relu(X @ Wp) - torch.relu(X @ Wn)
+    return _SplitReLU.apply(X, Wp, Wn)
 
 
 class SplitReLUNet(torch.nn.Module):

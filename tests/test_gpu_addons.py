@@ -500,3 +500,31 @@ def test_lazy_product_cache(hub_graph, transpose):
             assert np.abs(npy(out[True]) - Yr).max() <= 1e-5 * np.abs(Yr).max()
         for op in (S, H, p3, p2):
             op.close()
+
+
+def test_splitrelu_layers_run_in_the_library(hub_graph):
+    """Every dense product and ReLU of the Split-ReLU network (Sec. 5.2),
+    forward and backward, runs in the library's kernels: the split-ReLU
+    entry points (tensor-core Q.B and A^T B products, elementwise ReLU and
+    mask passes); no library GEMM (cuBLAS / CUTLASS) is launched."""
+    from torch.profiler import ProfilerActivity, profile
+
+    from paper_2111_06312_gb300.splitrelu import SplitReLUNet
+    g = hub_graph
+    d, y, L = 16, 5, 2
+    X, W_star = _splitrelu_setup(g, d, y, L)
+    with isvd.graph_operator(g, norm="sym", coeffs=[1.0]) as prop:
+        net = SplitReLUNet(prop, torch.from_numpy(X).cuda(), torch.from_numpy(W_star).cuda(), L)
+        R = torch.randn((g.n, y), device="cuda")
+        (net() * R).sum().backward()  # warm
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            (net() * R).sum().backward()
+            torch.cuda.synchronize()
+    names = [e.key for e in prof.key_averages()]
+    assert any("split_relu_fwd_kernel" in k for k in names), names
+    assert any("split_relu_mask_kernel" in k for k in names), names
+    assert any("gemm_tc_kernel" in k for k in names), names
+    assert any("gram_ab_tc_kernel" in k for k in names), names
+    foreign = [k for k in names if any(t in k.lower() for t in ("xmma", "nvjet", "cutlass", "sgemm", "cublas"))]
+    assert not foreign, foreign
