@@ -109,7 +109,8 @@ enum {
 
 #define ISVD_MAX_DEGREE 16
 #define ISVD_MAX_LOWRANK 8
-#define ISVD_MAX_BLOCK 160   /* largest block width l = k + p of isvd_svd */
+#define ISVD_MAX_BLOCK 160   /* largest block width l = k + p of isvd_svd (any precision) */
+#define ISVD_MAX_BLOCK_WIDE 512  /* largest FP32 block width of isvd_svd, isvd_orthonormalize */
 
 typedef struct {
   isvd_form form;
@@ -181,8 +182,14 @@ ISVD_API isvd_status isvd_apply_T(isvd_operator *op, const void *G, int64_t ldg,
  * uses l = 2k), `iters` power iterations (Alg. 1's `iterations`), start block
  * N(0,1) from Philox4x32-10 keyed by `seed`.  Outputs: U (rows x k, ldu),
  * S (k, descending), V (cols x k, ldv), all FP32.  dev_info may be NULL.
- * Requires 1 <= k, l <= min(rows, cols), l <= ISVD_MAX_BLOCK.  The sequence
- * is captured once per argument set into a CUDA graph and replayed. */
+ * Requires 1 <= k, l <= min(rows, cols) and l <= ISVD_MAX_BLOCK, or, in
+ * ISVD_PREC_FP32, l <= ISVD_MAX_BLOCK_WIDE (the paper's l = 2k at ranks up
+ * to 256): blocks wider than ISVD_MAX_BLOCK are orthonormalised in panels of
+ * 128 columns (block Gram-Schmidt with two projections, then CholeskyQR2 per
+ * panel), which gives the same thin QR up to rounding.  The sequence is
+ * captured once per argument set into a CUDA graph and replayed.  Errors:
+ * UNSUPPORTED (l > ISVD_MAX_BLOCK_WIDE, or l > ISVD_MAX_BLOCK in
+ * ISVD_PREC_MIXED). */
 ISVD_API isvd_status isvd_svd(isvd_operator *op, int32_t k, int32_t oversample, int32_t iters, uint64_t seed,
                      isvd_precision precision, float *U, int64_t ldu, float *S, float *V, int64_t ldv,
                      isvd_info *dev_info, void *stream);
@@ -232,7 +239,8 @@ ISVD_API isvd_status isvd_philox_words(uint64_t seed, int64_t rows, uint32_t *ou
  * follow (up to 4 passes).  R_out (DEVICE, l x l FP64, row-major, upper)
  * receives R with Q_in = Q_out R, or NULL.  dev_info as in
  * isvd_svd.  Uses the operator's workspace (any operator; pass the one whose
- * calls this is ordered with).  l <= ISVD_MAX_BLOCK; ldq >= l and a
+ * calls this is ordered with).  l <= ISVD_MAX_BLOCK_WIDE (above
+ * ISVD_MAX_BLOCK in 128-column panels, as in isvd_svd); ldq >= l and a
  * multiple of 8, Q 16-byte aligned (else ISVD_ERR_INVALID_ARGUMENT). */
 ISVD_API isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t rows, int32_t l, int64_t ldq,
                                 double *R_out, isvd_info *dev_info, void *stream);
@@ -409,7 +417,8 @@ ISVD_API isvd_status isvd_split_relu_backward(const float *X, int64_t ldx, int64
 /* SVD of a small square upper-triangular-or-dense FP64 matrix by one-sided
  * Jacobi on its transpose (the Rayleigh-Ritz step of Alg. 1, done as
  * SVD(R^T) after a QR of B^T).  A (l x l, row-major, DEVICE) = Uo diag(S) Vo^T
- * with Uo, Vo (l x l, FP64, row-major) and S (l, FP64, descending). */
+ * with Uo, Vo (l x l, FP64, row-major) and S (l, FP64, descending).
+ * 1 <= l <= ISVD_MAX_BLOCK_WIDE. */
 ISVD_API isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double *Uo, double *S,
                            double *Vo, isvd_info *dev_info, void *stream);
 

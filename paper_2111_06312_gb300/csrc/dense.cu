@@ -257,14 +257,28 @@ size_t gemm_smem(int32_t l, int32_t w) {
   return sizeof(float) * ((size_t)l * wp + (size_t)kGemmRows * l);
 }
 
+// the kernel's shared-memory limit: a 160 x 160 B, or 64 columns of a 512-row B
+size_t gemm_smem_cap() {
+  const size_t a = gemm_smem(ISVD_MAX_BLOCK, ISVD_MAX_BLOCK), b = gemm_smem(ISVD_MAX_BLOCK_WIDE, 64);
+  return a > b ? a : b;
+}
+
+// Column slices of at most 160 (five accumulators a lane) whose B fits the
+// shared memory; an in-place (upper) product must fit in one.
 template <typename TI, typename TO>
 cudaError_t gemm_small_t(const void *Q, int64_t ldq, int64_t rows, int32_t l, const float *B, int64_t ldb,
                          int32_t w, bool upper, void *out, int64_t ldo, PassGate g, cudaStream_t s) {
   int64_t bx = ceil_div(rows, kGemmRows);
   if (bx > kNumSMs * 2) bx = kNumSMs * 2;
   if (bx < 1) bx = 1;
-  gemm_small_kernel<TI, TO><<<(unsigned)bx, 256, gemm_smem(l, w), s>>>(
-      (const TI *)Q, ldq, rows, l, B, ldb, w, upper ? 1 : 0, (TO *)out, ldo, g);
+  int32_t ws = w < ISVD_MAX_BLOCK ? w : ISVD_MAX_BLOCK;
+  while (ws > 32 && gemm_smem(l, ws) > gemm_smem_cap()) ws = (ws - 1) / 32 * 32;
+  if (gemm_smem(l, ws) > gemm_smem_cap() || (upper && ws < w)) return cudaErrorInvalidValue;
+  for (int32_t c0 = 0; c0 < w; c0 += ws) {
+    const int32_t wc = w - c0 < ws ? w - c0 : ws;
+    gemm_small_kernel<TI, TO><<<(unsigned)bx, 256, gemm_smem(l, wc), s>>>(
+        (const TI *)Q, ldq, rows, l, B + c0, ldb, wc, upper ? 1 : 0, (TO *)out + c0, ldo, g);
+  }
   return cudaGetLastError();
 }
 
@@ -274,7 +288,7 @@ cudaError_t dense_kernels_init() {
   static cudaError_t err = cudaSuccess;
   static std::once_flag once;
   std::call_once(once, [] {
-    const int big = (int)gemm_smem(ISVD_MAX_BLOCK, ISVD_MAX_BLOCK);
+    const int big = (int)gemm_smem_cap();
     cudaError_t e = cudaSuccess;
     e = cudaFuncSetAttribute(gemm_small_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)

@@ -289,6 +289,12 @@ struct OrthBufs {
 };
 isvd_status orth_enqueue(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, double *Racc, const OrthBufs &o,
                          isvd_info *info, cudaStream_t s);
+// FP32 blocks of ISVD_MAX_BLOCK < l <= ISVD_MAX_BLOCK_WIDE columns (orth_wide.cu):
+// 128-column panels by block Gram-Schmidt (two projections) and CholeskyQR2.
+// o: buffers for 128 columns; wbuf: wide_orth_bytes(rows, l), 256-byte aligned.
+size_t wide_orth_bytes(int64_t rows, int32_t l);
+isvd_status wide_orth_enqueue(float *Q, int64_t ldq, int64_t rows, int32_t l, double *Racc, const OrthBufs &o,
+                              char *wbuf, isvd_info *info, cudaStream_t s);
 
 }  // namespace isvd
 

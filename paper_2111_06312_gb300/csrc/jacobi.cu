@@ -14,6 +14,13 @@
 // Rotation: Rutishauser's formula, column norms carried along (recomputed each
 // sweep); converged when every pair satisfies |g_p.g_q| <= tol ||g_p|| ||g_q||,
 // tol = max(1e-15, sqrt(l) eps).
+//
+// Blocks too large for the cluster's shared memory (l above ~300; the wide
+// blocks of up to 512 columns) stay in global memory (L2-resident: 2 MB at
+// l = 512) at their final position: a tournament step then moves no data,
+// only the ids of the two blocks each CTA works on, and every read of a
+// column goes to L2 (ld.global.cg) so that no CTA reads a stale L1 copy of a
+// block another CTA has rotated since.
 #include <cooperative_groups.h>
 
 #include <mutex>
@@ -33,20 +40,23 @@ constexpr int kJacMaxSmem = 200 * 1024;
 // caller) if they are not yet orthogonal.  Only g_p . g_q is summed; the norms
 // follow the rotation in closed form (||g_p'||^2 = ||g_p||^2 - t g_p.g_q,
 // ||g_q'||^2 = ||g_q||^2 + t g_p.g_q) and are recomputed exactly every sweep.
+// a column element: from shared memory, or (global mode) from L2
+__device__ __forceinline__ double ldc(const double *p, bool gmode) { return gmode ? __ldcg(p) : *p; }
+
 __device__ __forceinline__ int rotate_pair(double *gp, double *gq, double *np, double *nq, int l, int lane,
-                                           double tol, double tiny) {
+                                           double tol, double tiny, bool gmode) {
   double ga = 0.0;
-  for (int i = lane; i < l; i += 32) ga += gp[i] * gq[i];
+  for (int i = lane; i < l; i += 32) ga += ldc(gp + i, gmode) * ldc(gq + i, gmode);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
-  const double al = *np, be = *nq;
+  const double al = ldc(np, gmode), be = ldc(nq, gmode);
   if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) return 0;
   if (al <= tiny && be <= tiny) return 0;
   const double zeta = (be - al) / (2.0 * ga);
   const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
   const double cs = rsqrt(1.0 + t * t), sn = cs * t;
   for (int i = lane; i < l; i += 32) {
-    const double x = gp[i], y = gq[i];
+    const double x = ldc(gp + i, gmode), y = ldc(gq + i, gmode);
     gp[i] = cs * x - sn * y;
     gq[i] = sn * x + cs * y;
   }
@@ -74,7 +84,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
     const double *__restrict__ A, int32_t l, int32_t bs, double *__restrict__ Wg, double *__restrict__ nrm_g,
     int32_t *__restrict__ perm_g, double *__restrict__ Uo, double *__restrict__ S, double *__restrict__ Vo,
     float *__restrict__ Uk, float *__restrict__ Vk, float *__restrict__ Sk, int32_t k, isvd_info *info,
-    int32_t iters) {
+    int32_t iters, int32_t gmode, double *__restrict__ gnrm) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int c = (int)cluster.block_rank();
@@ -86,9 +96,16 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
   __shared__ int any_flags[kJacMaxCluster];
   __shared__ int stop;
   __shared__ double red[kJacThreads / 32];
-  auto colp = [&](int buf, int slot, int j) { return sm + ((size_t)(buf * 2 + slot) * bs + j) * l; };
+  // shared-memory mode: [2 buffers][2 slots][bs][l] then the norms; global
+  // mode: block b's columns at Wg[b bs ..] and norms at gnrm[b bs ..]
+  const bool gm = gmode != 0;
+  auto colp = [&](int buf, int slot, int j) {
+    return gm ? Wg + ((size_t)ids[buf][slot] * bs + j) * l : sm + ((size_t)(buf * 2 + slot) * bs + j) * l;
+  };
   double *nrm = sm + (size_t)4 * bs * l;
-  auto nrmp = [&](int buf, int slot, int j) { return nrm + (buf * 2 + slot) * bs + j; };
+  auto nrmp = [&](int buf, int slot, int j) {
+    return gm ? gnrm + (size_t)ids[buf][slot] * bs + j : nrm + (buf * 2 + slot) * bs + j;
+  };
 
   if (tid == 0) {
     ids[0][0] = c;
@@ -122,7 +139,10 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
     for (int q = warp; q < 2 * bs; q += nwarp) {
       const double *g = colp(cur, q / bs, q % bs);
       double s2 = 0.0;
-      for (int i = lane; i < l; i += 32) s2 += g[i] * g[i];
+      for (int i = lane; i < l; i += 32) {
+        const double x = ldc(g + i, gm);
+        s2 += x * x;
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
       if (lane == 0) *nrmp(cur, q / bs, q % bs) = s2;
@@ -136,7 +156,7 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
         tourney(r, kk, bsp, p, q);
         if (p < bs && q < bs)
           rotated |= rotate_pair(colp(cur, slot, p), colp(cur, slot, q), nrmp(cur, slot, p), nrmp(cur, slot, q), l,
-                                 lane, tol, tiny);
+                                 lane, tol, tiny, gm);
       }
       __syncthreads();
     }
@@ -145,10 +165,11 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
       for (int r = 0; r < bs; ++r) {
         for (int i = warp; i < bs; i += nwarp)
           rotated |= rotate_pair(colp(cur, 0, i), colp(cur, 1, (i + r) % bs), nrmp(cur, 0, i),
-                                 nrmp(cur, 1, (i + r) % bs), l, lane, tol, tiny);
+                                 nrmp(cur, 1, (i + r) % bs), l, lane, tol, tiny, gm);
         __syncthreads();
       }
       if (CL == 1) continue;  // two blocks only: they never move
+      if (gm) __threadfence();  // the rotated columns, before other CTAs take the blocks
       cluster.sync();
       // circle [t1 .. t_{CL-1}, b_{CL-1} .. b0] rotates by one; t0 stays
       const int nxt = cur ^ 1;
@@ -166,11 +187,13 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
         src_rank[1] = c + 1; src_slot[1] = 1;
       }
       for (int slot = 0; slot < 2; ++slot) {
-        double *src = cluster.map_shared_rank(colp(cur, src_slot[slot], 0), src_rank[slot]);
-        double *dst = colp(nxt, slot, 0);
-        for (int idx = tid; idx < bs * l; idx += blockDim.x) dst[idx] = src[idx];
-        const double *nsrc = cluster.map_shared_rank(nrmp(cur, src_slot[slot], 0), src_rank[slot]);
-        for (int j = tid; j < bs; j += blockDim.x) *nrmp(nxt, slot, j) = nsrc[j];
+        if (!gm) {  // global mode: the blocks stay where they are, only their ids move
+          double *src = cluster.map_shared_rank(colp(cur, src_slot[slot], 0), src_rank[slot]);
+          double *dst = colp(nxt, slot, 0);
+          for (int idx = tid; idx < bs * l; idx += blockDim.x) dst[idx] = src[idx];
+          const double *nsrc = cluster.map_shared_rank(nrmp(cur, src_slot[slot], 0), src_rank[slot]);
+          for (int j = tid; j < bs; j += blockDim.x) *nrmp(nxt, slot, j) = nsrc[j];
+        }
         if (tid == 0) {
           int *rid = cluster.map_shared_rank(&ids[cur][src_slot[slot]], src_rank[slot]);
           ids[nxt][slot] = *rid;
@@ -199,9 +222,9 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
       const double *g = colp(cur, slot, j);
       double s2 = 0.0;
       for (int i = lane; i < l; i += 32) {
-        const double x = g[i];
+        const double x = ldc(g + i, gm);
         s2 += x * x;
-        Wg[(size_t)p * l + i] = x;
+        if (!gm) Wg[(size_t)p * l + i] = x;
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
@@ -213,9 +236,9 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
     // descending order of the first l columns (the rest are zero padding),
     // stable: rank of column p = #columns with a larger norm, or an equal norm
     // and a smaller index (a NaN norm ranks below every number)
-    __shared__ double snrm[ISVD_MAX_BLOCK];
+    __shared__ double snrm[ISVD_MAX_BLOCK_WIDE];
     for (int p = tid; p < l; p += blockDim.x) {
-      const double x = nrm_g[p];
+      const double x = __ldcg(nrm_g + p);
       snrm[p] = x == x ? x : -1.0;
     }
     __syncthreads();
@@ -230,21 +253,33 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(
   (void)l3;
   __threadfence();
   cluster.sync();
-  // outputs: column kk of Vo = w_p / sigma, of Uo = A w_p / sigma^2
+  // outputs: column kk of Vo = w_p / sigma, of Uo = A w_p / sigma^2; w_p is
+  // staged in shared memory (no CTA reads another's columns any more), one
+  // warp per row of A (coalesced)
+  double *wsm = sm;
   for (int kk = c; kk < l; kk += CL) {
-    const int p = perm_g[kk];
-    const double sg = nrm_g[p];
-    const double *w = Wg + (size_t)p * l;
-    for (int i = tid; i < l; i += blockDim.x) {
+    const int p = __ldcg(perm_g + kk);
+    const double sg = __ldcg(nrm_g + p);
+    __syncthreads();  // the previous column's readers are done
+    for (int i = tid; i < l; i += blockDim.x) wsm[i] = __ldcg(Wg + (size_t)p * l + i);
+    __syncthreads();
+    const bool need_u = Uo || (Uk && kk < k);
+    for (int i = warp; i < l; i += nwarp) {
       double u = 0.0;
-      for (int t = 0; t < l; ++t) u += A[(size_t)i * l + t] * w[t];
-      const double v = sg > 0.0 ? w[i] / sg : 0.0;
-      u = sg > 0.0 ? u / (sg * sg) : 0.0;
-      if (Vo) Vo[(size_t)i * l + kk] = v;
-      if (Uo) Uo[(size_t)i * l + kk] = u;
-      if (kk < k) {
-        if (Vk) Vk[(size_t)i * k + kk] = (float)v;
-        if (Uk) Uk[(size_t)i * k + kk] = (float)u;
+      if (need_u) {
+        for (int t = lane; t < l; t += 32) u += A[(size_t)i * l + t] * wsm[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+      }
+      if (lane == 0) {
+        const double v = sg > 0.0 ? wsm[i] / sg : 0.0;
+        u = sg > 0.0 ? u / (sg * sg) : 0.0;
+        if (Vo) Vo[(size_t)i * l + kk] = v;
+        if (Uo) Uo[(size_t)i * l + kk] = u;
+        if (kk < k) {
+          if (Vk) Vk[(size_t)i * k + kk] = (float)v;
+          if (Uk) Uk[(size_t)i * k + kk] = (float)u;
+        }
       }
     }
     if (tid == 0) {
@@ -259,6 +294,8 @@ std::once_flag g_once;
 cudaError_t g_err = cudaSuccess;
 
 size_t jac_smem(int32_t l, int32_t bs) { return sizeof(double) * 4 * (size_t)bs * (l + 1); }
+// global mode: shared memory only stages one column of the outputs
+size_t jac_smem_global(int32_t l) { return sizeof(double) * (size_t)l; }
 
 int block_size_for(int32_t l, int cl) { return (int)((l + 2 * cl - 1) / (2 * cl)); }
 
@@ -306,14 +343,16 @@ cudaError_t small_svd_launch(const double *A, int32_t l, double *Uo, double *S, 
   while (cl > 1 && block_size_for(l, cl) < 4) cl >>= 1;
   const int bs = block_size_for(l, cl);
   const int l3 = 2 * cl * bs;
-  if (jac_smem(l, bs) > (size_t)kJacMaxSmem) return cudaErrorInvalidConfiguration;
+  if (l > ISVD_MAX_BLOCK_WIDE) return cudaErrorInvalidValue;
+  // blocks that do not fit the cluster's shared memory stay in global memory
+  const int32_t gmode = jac_smem(l, bs) > (size_t)kJacMaxSmem ? 1 : 0;
   double *Wg = work;                                   // l3 x l
-  double *nrm = work + (size_t)l3 * l;                 // l3
+  double *nrm = work + (size_t)l3 * l;                 // l3 (squared norms during the sweeps in global mode)
   int32_t *perm = reinterpret_cast<int32_t *>(nrm + l3);  // l
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(cl);
   cfg.blockDim = dim3(kJacThreads);
-  cfg.dynamicSmemBytes = jac_smem(l, bs);
+  cfg.dynamicSmemBytes = gmode ? jac_smem_global(l) : jac_smem(l, bs);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -323,7 +362,7 @@ cudaError_t small_svd_launch(const double *A, int32_t l, double *Uo, double *S, 
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, A, l, bs, Wg, nrm, perm, Uo, S, Vo, Uk, Vk, Sk, k, info,
-                            iters);
+                            iters, gmode, nrm);
 }
 
 size_t small_svd_work_doubles(int32_t l) {

@@ -45,13 +45,30 @@ struct Carver {
   }
 };
 
-void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o) {
+// OrthBufs for blocks of width l; above ISVD_MAX_BLOCK the CholeskyQR2
+// buffers serve the 128-column panels of the wide path, which adds its own
+// (`wide`, may be null when l <= ISVD_MAX_BLOCK).
+void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o, char **wide = nullptr) {
+  if (l > ISVD_MAX_BLOCK) {
+    char *w = c.take<char>(wide_orth_bytes(rows, l));
+    if (wide) *wide = w;
+    l = ISVD_MAX_BLOCK;
+  }
   o->n_part = gram_partials(rows);
   o->gram_partial = c.take<double>((size_t)o->n_part * l * l);
   o->W = c.take<double>((size_t)l * l);
   o->tmp = c.take<double>((size_t)l * l);
   o->Rinv = c.take<float>((size_t)l * l);
   o->state = c.take<int32_t>(kOrthStateInts);
+}
+
+// Q (rows x l) <- its orthonormal factor: one CholeskyQR2 up to
+// ISVD_MAX_BLOCK columns, 128-column panels (FP32) above
+isvd_status orth_any(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, double *Racc, const OrthBufs &o,
+                     char *wide, isvd_info *info, cudaStream_t s) {
+  if (l <= ISVD_MAX_BLOCK) return orth_enqueue(Q, ldq, dt, rows, l, Racc, o, info, s);
+  if (dt != DT_F32 || !wide) return fail(ISVD_ERR_UNSUPPORTED, "blocks wider than %d are FP32 only", ISVD_MAX_BLOCK);
+  return wide_orth_enqueue((float *)Q, ldq, rows, l, Racc, o, wide, info, s);
 }
 
 struct SvdPlan {
@@ -68,6 +85,7 @@ struct SvdBufs {
   float *qr32, *qc32;   // FP32 blocks (alias qr/qc in FP32 mode)
   char *apply_base;
   OrthBufs orth;
+  char *wide = nullptr;  // panel buffers of blocks wider than ISVD_MAX_BLOCK
   double *Racc, *Uo, *So, *Vo, *jwork;
   float *Lk, *Rk;
   isvd_info *info;
@@ -89,7 +107,7 @@ size_t carve_svd(const isvd_operator *op, const SvdPlan &P, char *base, SvdBufs 
   }
   const size_t ab = std::max(apply_scratch_bytes(op, P.l, DT_F32, false), apply_scratch_bytes(op, P.l, DT_F32, true));
   b->apply_base = c.take<char>(ab);
-  carve_orth(c, std::max(rows, cols), P.l, &b->orth);
+  carve_orth(c, std::max(rows, cols), P.l, &b->orth, &b->wide);
   b->Racc = c.take<double>((size_t)P.l * P.l);
   b->Uo = c.take<double>((size_t)P.l * P.l);
   b->Vo = c.take<double>((size_t)P.l * P.l);
@@ -118,9 +136,9 @@ isvd_status svd_enqueue(isvd_operator *op, const SvdPlan &P, const SvdBufs &b, c
   ISVD_CUDA_TRY(gaussian_launch(P.seed, cols, P.l, b.qc, P.ld, dt, s));
   for (int it = 0; it < P.iters; ++it) {
     ISVD_TRY(apply_step(op, b.qc, b.qr, P.l, P.ld, dt, false, b, s));  // M Q
-    ISVD_TRY(orth_enqueue(b.qr, P.ld, dt, rows, P.l, nullptr, b.orth, info, s));
+    ISVD_TRY(orth_any(b.qr, P.ld, dt, rows, P.l, nullptr, b.orth, b.wide, info, s));
     ISVD_TRY(apply_step(op, b.qr, b.qc, P.l, P.ld, dt, true, b, s));   // M^T Q
-    ISVD_TRY(orth_enqueue(b.qc, P.ld, dt, cols, P.l, nullptr, b.orth, info, s));
+    ISVD_TRY(orth_any(b.qc, P.ld, dt, cols, P.l, nullptr, b.orth, b.wide, info, s));
   }
   if (mixed) {
     // the refinement step and the Rayleigh-Ritz step run in FP32
@@ -131,10 +149,10 @@ isvd_status svd_enqueue(isvd_operator *op, const SvdPlan &P, const SvdBufs &b, c
     ISVD_CUDA_TRY(cudaGetLastError());
   }
   ISVD_TRY(apply_step(op, b.qc32, b.qr32, P.l, P.ld, DT_F32, false, b, s));
-  ISVD_TRY(orth_enqueue(b.qr32, P.ld, DT_F32, rows, P.l, nullptr, b.orth, info, s));
+  ISVD_TRY(orth_any(b.qr32, P.ld, DT_F32, rows, P.l, nullptr, b.orth, b.wide, info, s));
   // B^T = M^T Q = Qt R  (CholeskyQR of B^T, R accumulated over the passes)
   ISVD_TRY(apply_step(op, b.qr32, b.qc32, P.l, P.ld, DT_F32, true, b, s));
-  ISVD_TRY(orth_enqueue(b.qc32, P.ld, DT_F32, cols, P.l, b.Racc, b.orth, info, s));
+  ISVD_TRY(orth_any(b.qc32, P.ld, DT_F32, cols, P.l, b.Racc, b.orth, b.wide, info, s));
   // B = R^T Qt^T;  R = Uo S Vo^T  =>  B = Vo S (Qt Uo)^T:  U = Q Vo, V = Qt Uo
   ISVD_CUDA_TRY(small_svd_launch(b.Racc, P.l, b.Uo, b.So, b.Vo, b.jwork, /*Uk=*/b.Rk, /*Vk=*/b.Lk, /*Sk=*/P.S, P.k,
                                  info, P.iters, s));
@@ -265,7 +283,10 @@ isvd_status isvd_svd(isvd_operator *op, int32_t k, int32_t oversample, int32_t i
   if (precision != ISVD_PREC_FP32 && precision != ISVD_PREC_MIXED)
     return fail(ISVD_ERR_INVALID_ARGUMENT, "unknown precision");
   const int64_t l = (int64_t)k + oversample;
-  if (l > ISVD_MAX_BLOCK) return fail(ISVD_ERR_UNSUPPORTED, "block width k + oversample = %lld > %d", (long long)l, ISVD_MAX_BLOCK);
+  if (l > ISVD_MAX_BLOCK_WIDE)
+    return fail(ISVD_ERR_UNSUPPORTED, "block width k + oversample = %lld > %d", (long long)l, ISVD_MAX_BLOCK_WIDE);
+  if (l > ISVD_MAX_BLOCK && precision != ISVD_PREC_FP32)
+    return fail(ISVD_ERR_UNSUPPORTED, "block widths above %d run in FP32 only", ISVD_MAX_BLOCK);
   if (l > std::min(op->rows, op->cols))
     return fail(ISVD_ERR_SHAPE, "block width k + oversample = %lld exceeds min(rows, cols)", (long long)l);
   if (ldu < k || ldv < k) return fail(ISVD_ERR_INVALID_ARGUMENT, "ldu and ldv must be >= k");
@@ -458,21 +479,23 @@ isvd_status isvd_philox_words(uint64_t seed, int64_t rows, uint32_t *out, void *
 isvd_status isvd_orthonormalize(isvd_operator *op, float *Q, int64_t rows, int32_t l, int64_t ldq, double *R_out,
                                 isvd_info *dev_info, void *stream) {
   if (!op || !Q) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
-  if (l < 1 || l > ISVD_MAX_BLOCK || rows < l) return fail(ISVD_ERR_SHAPE, "need 1 <= l <= min(rows, %d)", ISVD_MAX_BLOCK);
+  if (l < 1 || l > ISVD_MAX_BLOCK_WIDE || rows < l)
+    return fail(ISVD_ERR_SHAPE, "need 1 <= l <= min(rows, %d)", ISVD_MAX_BLOCK_WIDE);
   if (ldq < l || ldq % 8 || (uintptr_t)Q % 16)
     return fail(ISVD_ERR_INVALID_ARGUMENT, "ldq must be >= l and a multiple of 8, Q 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   Carver c{nullptr};
   OrthBufs o;
-  carve_orth(c, rows, l, &o);
+  char *wide = nullptr;
+  carve_orth(c, rows, l, &o, &wide);
   c.take<isvd_info>(1);
   ISVD_TRY(ensure_arena(op, c.off, s));
   Carver c2{(char *)op->arena};
-  carve_orth(c2, rows, l, &o);
+  carve_orth(c2, rows, l, &o, &wide);
   isvd_info *own = c2.take<isvd_info>(1);
   isvd_info *info = dev_info ? dev_info : own;
   if (!dev_info) ISVD_CUDA_TRY(cudaMemsetAsync(own, 0, sizeof(isvd_info), s));
-  return orth_enqueue(Q, ldq, DT_F32, rows, l, R_out, o, info, s);
+  return orth_any(Q, ldq, DT_F32, rows, l, R_out, o, wide, info, s);
 }
 
 isvd_status isvd_closed_form(isvd_operator *op, const float *U, int64_t ldu, const float *S, const float *V,
@@ -525,7 +548,7 @@ isvd_status isvd_pair_scores(const float *L, int64_t ldl, int64_t rows, const fl
 isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double *Uo, double *S, double *Vo,
                            isvd_info *dev_info, void *stream) {
   if (!op || !A || !Uo || !S || !Vo) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument");
-  if (l < 1 || l > ISVD_MAX_BLOCK) return fail(ISVD_ERR_SHAPE, "need 1 <= l <= %d", ISVD_MAX_BLOCK);
+  if (l < 1 || l > ISVD_MAX_BLOCK_WIDE) return fail(ISVD_ERR_SHAPE, "need 1 <= l <= %d", ISVD_MAX_BLOCK_WIDE);
   cudaStream_t s = (cudaStream_t)stream;
   Carver c{nullptr};
   c.take<double>(small_svd_work_doubles(l));

@@ -28,6 +28,7 @@ NORM = {"row": 0, "sym": 1, "sym_noself": 2}
 FORM = {"poly": 0, "concat": 1}
 FLAG_SKIP_SYMMETRY_CHECK = 1
 MAX_BLOCK = 160
+MAX_BLOCK_WIDE = 512  # FP32 block widths of svd and orthonormalize
 
 
 class IsvdError(RuntimeError):

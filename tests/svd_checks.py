@@ -61,3 +61,12 @@ def check_svd(gpu_op, ref_op, k, p, q, seed, tol_s=1e-5, tol_angle=1e-3, precisi
     assert out["info"]["status"] == "OK", out
     assert_svd(out, tol_s, tol_angle)
     return out
+
+
+def cond_block(r, c, cond, seed):
+    """r x c FP64 block with singular values geomspace(1, 1/cond) and random
+    singular vectors (seeded)."""
+    rng = np.random.default_rng(seed)
+    Ua, _ = np.linalg.qr(rng.standard_normal((r, c)))
+    Va, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    return (Ua * np.geomspace(1, 1 / cond, c)) @ Va.T

@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from paper_2111_06312_gb300 import build, isvd, synth
-from svd_checks import check_svd, gapped_prefix  # noqa: F401
+from svd_checks import check_svd, cond_block, gapped_prefix  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 LAM = 0.05
@@ -230,13 +230,6 @@ def test_concat_dense_x_wide_and_bf16(hub_graph, b, dtype, transpose):
 
 
 # ---- orthonormalisation (Alg. 2) and the small SVD --------------------------------
-
-def cond_block(r, c, cond, seed):
-    rng = np.random.default_rng(seed)
-    Ua, _ = np.linalg.qr(rng.standard_normal((r, c)))
-    Va, _ = np.linalg.qr(rng.standard_normal((c, c)))
-    return (Ua * np.geomspace(1, 1 / cond, c)) @ Va.T
-
 
 @pytest.mark.parametrize("rows,l,cond", [(5000, 42, 1e2), (20011, 144, 1e3), (3001, 19, 1e5), (70000, 74, 1e6),
                                          (9000, 160, 1e5), (4000, 33, 1e4), (2500, 31, 1e2)])
