@@ -401,6 +401,48 @@ def finetune_section(args, flush, stream):
                 "forward_plus_backward_ms": fwd + bwd, "epoch_ms": epoch_ms, "closed_form_init_ms": init_ms}
 
 
+def wide_section(args, op, g, q, flush, stream):
+    """The paper's own block width l = 2k at rank 256 (l = 512, FP32) on the
+    same operator and iterations as the main line: the whole SVD, its error
+    (max_i r_i / s_i over the top 256), and two of its steps alone: the
+    orthonormalisation of an n x 512 block (128-column panels) and the small
+    SVD of a 512 x 512 upper-triangular factor (global-memory Jacobi)."""
+    import torch
+
+    from paper_2111_06312_gb300 import isvd
+
+    k, p = 256, 256
+    l = k + p
+    U = isvd.new_block(g.n, k)
+    V = isvd.new_block(g.n, k)
+    S = torch.empty(k, device="cuda")
+    info = torch.zeros(4, dtype=torch.int32, device="cuda")
+    fn = lambda: op.svd(k, p, q, seed=SEED, U=U, S=S, V=V, info=info, check=False)  # noqa: E731
+    fn()
+    torch.cuda.synchronize()
+    st = isvd.info_dict(info)
+    if st["status"] != "OK":
+        raise RuntimeError(f"device status {st}")
+    steps = max(2, args.steps // 3)
+    ms = float(np.mean(timed_steps(fn, steps, flush, stream)))
+    err = relative_residuals(op, U, S, V)
+    del U, V
+    Q0 = isvd.gaussian(5, g.n, l)
+    Q = Q0.clone()
+    isvd.orthonormalize(op, Q, want_r=False)
+    orth_ms = float(np.mean(timed_steps(lambda: (Q.copy_(Q0), isvd.orthonormalize(op, Q, want_r=False)),
+                                        steps, flush, stream)))
+    copy_ms = float(np.mean(timed_steps(lambda: Q.copy_(Q0), steps, flush, stream)))
+    del Q, Q0
+    R = torch.linalg.qr(torch.randn((l, l), dtype=torch.float64, device="cuda"))[1]
+    isvd.small_svd(op, R)
+    jac_ms = float(np.mean(timed_steps(lambda: isvd.small_svd(op, R), steps, flush, stream)))
+    return {"k": k, "oversample": p, "iters": q, "width": l, "ms": ms, "cholqr_passes": st["cholqr_passes"],
+            "max_rel_residual": float(err.max()), "median_rel_residual": float(np.median(err)),
+            "orthonormalize_ms": orth_ms - copy_ms, "orthonormalize_rows": g.n,
+            "small_svd_ms": jac_ms}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -568,6 +610,7 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras:
+        extras["wide"] = wide_section(args, op, g, q, flush, stream)
         extras["batched"] = batched_section(args, flush, stream)
         extras["finetune"] = finetune_section(args, flush, stream)
 

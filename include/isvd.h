@@ -418,7 +418,8 @@ ISVD_API isvd_status isvd_split_relu_backward(const float *X, int64_t ldx, int64
  * Jacobi on its transpose (the Rayleigh-Ritz step of Alg. 1, done as
  * SVD(R^T) after a QR of B^T).  A (l x l, row-major, DEVICE) = Uo diag(S) Vo^T
  * with Uo, Vo (l x l, FP64, row-major) and S (l, FP64, descending).
- * 1 <= l <= ISVD_MAX_BLOCK_WIDE. */
+ * 1 <= l <= ISVD_MAX_BLOCK_WIDE.  dev_info (nullable): status, and the
+ * number of Jacobi sweeps run in iters_done (60 at most). */
 ISVD_API isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double *Uo, double *S,
                            double *Vo, isvd_info *dev_info, void *stream);
 

@@ -553,7 +553,8 @@ isvd_status isvd_small_svd(isvd_operator *op, const double *A, int32_t l, double
   Carver c{nullptr};
   c.take<double>(small_svd_work_doubles(l));
   ISVD_TRY(ensure_arena(op, c.off, s));
-  ISVD_CUDA_TRY(small_svd_launch(A, l, Uo, S, Vo, (double *)op->arena, nullptr, nullptr, nullptr, 0, dev_info, 0, s));
+  // iters = -1: dev_info->iters_done receives the Jacobi sweep count
+  ISVD_CUDA_TRY(small_svd_launch(A, l, Uo, S, Vo, (double *)op->arena, nullptr, nullptr, nullptr, 0, dev_info, -1, s));
   return ISVD_OK;
 }
 

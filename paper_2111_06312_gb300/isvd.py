@@ -468,14 +468,16 @@ def orthonormalize(op: Operator, Q: torch.Tensor, want_r: bool = True):
     return Q, R, info
 
 
-def small_svd(op: Operator, A: torch.Tensor):
-    """SVD of a small square FP64 matrix (one-sided Jacobi): A = U diag(S) V^T."""
+def small_svd(op: Operator, A: torch.Tensor, info: torch.Tensor | None = None):
+    """SVD of a small square FP64 matrix (one-sided Jacobi): A = U diag(S) V^T.
+    `info` (int32[4] on the device, optional) receives the status and, in
+    iters_done, the number of sweeps."""
     A = A.to(torch.float64).contiguous()
     l = A.shape[0]
     U = torch.zeros((l, l), dtype=torch.float64, device=A.device)
     V = torch.zeros((l, l), dtype=torch.float64, device=A.device)
     S = torch.zeros(l, dtype=torch.float64, device=A.device)
-    _check(lib().isvd_small_svd(op._handle, _ptr(A), l, _ptr(U), _ptr(S), _ptr(V), None, _stream()),
+    _check(lib().isvd_small_svd(op._handle, _ptr(A), l, _ptr(U), _ptr(S), _ptr(V), _ptr(info), _stream()),
            "isvd_small_svd")
     return U, S, V
 

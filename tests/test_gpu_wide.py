@@ -5,8 +5,9 @@ Wide blocks are orthonormalised in 128-column panels (block Gram-Schmidt with
 two projections, then CholeskyQR2 per panel); the thin QR they give is the
 one CholeskyQR2 of the whole block gives (Q with R's diagonal positive is
 unique), so the oracle's full-width CholeskyQR2 is the reference.  The
-Rayleigh-Ritz SVD of an l x l R beyond the cluster's shared memory runs with
-the column blocks in global memory; LAPACK's singular values pin it.
+Rayleigh-Ritz SVD of an l x l R above 160 columns runs over the whole grid
+(column blocks in global memory, grid barriers); LAPACK's singular values pin
+it.
 
 Singular-value tolerance of Alg. 1 here: the FP32 products perturb M by
 about u ||M|| (u = 2^-24) per product, and by Weyl's inequality every
@@ -78,15 +79,19 @@ def test_wide_orthonormalize_matches_narrow_at_160(ne_small):
 
 # ---- the small SVD ---------------------------------------------------------------
 
-# 256 and 384: blocks in the cluster's shared memory; 460, 480, 512: in global memory
-@pytest.mark.parametrize("l,cond,upper", [(256, 1e6, True), (384, 1e3, False), (460, 1e4, True), (480, 1e2, False),
-                                          (512, 1e8, True)])
+# above 160 columns the grid form (blocks of two columns in global memory, one
+# CTA per block pair); 161: one column in the last block
+@pytest.mark.parametrize("l,cond,upper", [(161, 1e3, False), (256, 1e6, True), (384, 1e3, False), (460, 1e4, True),
+                                          (480, 1e2, False), (512, 1e8, True)])
 def test_wide_small_svd(ne_small, l, cond, upper):
     A = cond_block(l, l, cond, 31 + l)
     if upper:
         A = np.linalg.qr(A)[1]
+    info = torch.zeros(4, dtype=torch.int32, device="cuda")
     with isvd.graph_operator(ne_small, coeffs=C5) as op:
-        U, S, V = isvd.small_svd(op, torch.tensor(A, device="cuda"))
+        U, S, V = isvd.small_svd(op, torch.tensor(A, device="cuda"), info=info)
+    inf = isvd.info_dict(info)
+    assert inf["status"] == "OK" and 1 <= inf["iters_done"] < 60, inf  # converged within the sweep limit
     U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
     Sr = np.linalg.svd(A, compute_uv=False)
     assert np.allclose(S, Sr, rtol=1e-11, atol=1e-14 * Sr[0])
