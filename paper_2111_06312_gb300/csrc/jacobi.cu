@@ -44,6 +44,33 @@ constexpr int kJacMaxSmem = 200 * 1024;
 // caller) if they are not yet orthogonal.  Only g_p . g_q is summed; the norms
 // follow the rotation in closed form (||g_p'||^2 = ||g_p||^2 - t g_p.g_q,
 // ||g_q'||^2 = ||g_q||^2 + t g_p.g_q) and are recomputed exactly every sweep.
+// The rotation of a pair with g_p.g_q = ga and squared norms al, be, or
+// false when the pair counts as orthogonal: ga^2 <= tol^2 al be (no square
+// root: an FP64 square root costs ~10 times an FMA on this part, and an FP64
+// instruction ~64 clocks of a warp).  The tangent t (Rutishauser) is taken in
+// FP32 from zeta = (be - al) / (2 ga) scaled by a power of two: it only sets
+// how far the pair turns, so an FP32-accurate t leaves g_p.g_q at ~1e-7 of its
+// size (cleared in the next sweep) but cannot cost accuracy; cs = (1 + t^2)^-1/2
+// and sn = t cs in FP64 keep the rotation orthogonal to FP64 rounding.
+__device__ __forceinline__ bool jacobi_angle(double ga, double al, double be, double tol, double tiny, double &t,
+                                             double &cs, double &sn) {
+  if (ga == 0.0 || ga * ga <= (tol * tol) * (al * be)) return false;
+  if (al <= tiny && be <= tiny) return false;
+  const double num = be - al, den = 2.0 * ga;
+  const int e = ((__double2hiint(den) >> 20) & 0x7FF) - 1023;  // den = 2^e (1 + f)
+  const double sc = __hiloint2double((1023 - e) << 20, 0);    // 2^-e
+  const float zf = __double2float_rn(num * sc) / __double2float_rn(den * sc);
+  float tf;
+  if (fabsf(zf) < 1e18f)
+    tf = copysignf(1.f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.f)));
+  else
+    tf = 0.5f / zf;  // t ~ 1 / (2 zeta); 0 when zeta overflowed
+  t = (double)tf;
+  cs = rsqrt(fma(t, t, 1.0));
+  sn = cs * t;
+  return true;
+}
+
 // a column element: from shared memory, or (global mode) from L2
 __device__ __forceinline__ double ldc(const double *p, bool gmode) { return gmode ? __ldcg(p) : *p; }
 
@@ -54,11 +81,8 @@ __device__ __forceinline__ int rotate_pair(double *gp, double *gq, double *np, d
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
   const double al = ldc(np, gmode), be = ldc(nq, gmode);
-  if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) return 0;
-  if (al <= tiny && be <= tiny) return 0;
-  const double zeta = (be - al) / (2.0 * ga);
-  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cs = rsqrt(1.0 + t * t), sn = cs * t;
+  double t, cs, sn;
+  if (!jacobi_angle(ga, al, be, tol, tiny, t, cs, sn)) return 0;
   for (int i = lane; i < l; i += 32) {
     const double x = ldc(gp + i, gmode), y = ldc(gq + i, gmode);
     gp[i] = cs * x - sn * y;
@@ -402,12 +426,9 @@ __device__ int rotate_group(double *x, double *y, double *nx, double *ny, int l,
   group_sync(id);
   ga = (gred[0] + gred[1]) + (gred[2] + gred[3]);
   const double al = *nx, be = *ny;
-  int rot = 1;
-  if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be) || (al <= tiny && be <= tiny)) rot = 0;
+  double t, cs, sn;
+  const int rot = jacobi_angle(ga, al, be, tol, tiny, t, cs, sn) ? 1 : 0;
   if (rot) {
-    const double zeta = (be - al) / (2.0 * ga);
-    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double cs = rsqrt(1.0 + t * t), sn = cs * t;
     for (int i = gt; i < l; i += 128) {
       const double a = x[i], b = y[i];
       x[i] = cs * a - sn * b;
