@@ -457,7 +457,9 @@ enum {
   ISVD_TUNE_SLAB_KERNEL = 128 /* products with A: one launch per column slab over a length-sorted
                                  list of rows and hub pieces (hub partials summed in piece order by
                                  the group finishing the last piece); implies PACKED; takes
-                                 precedence over the other kernels */
+                                 precedence over the other kernels.  It always sets L2 policies
+                                 (gathered slab rows evict_last, the CSR stream, the axpy operand
+                                 and the output evict_first); CACHE_HINTS concerns the others */
 };
 
 /* Read / replace the operator's launch shapes.  isvd_set_tuning rebuilds the

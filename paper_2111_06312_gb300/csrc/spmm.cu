@@ -41,6 +41,14 @@
 #ifndef ISVD_SLAB_MINB_BF16
 #define ISVD_SLAB_MINB_BF16 5
 #endif
+// L2 policies of the packed-slab kernel: gathered rows of the slab
+// evict_last (ISVD_SLAB_GATHER_KEEP 1) or unmarked (0); the CSR stream, the
+// axpy operand and the output evict_first.  Measured on the 10^6-node
+// graph at width 144: 7.94 -> 7.80 ms per FP32 apply, 5.30 -> 5.22 ms BF16
+// (unmarked gathers: 7.81 and 5.36), results bit for bit the same.
+#ifndef ISVD_SLAB_GATHER_KEEP
+#define ISVD_SLAB_GATHER_KEEP 1
+#endif
 
 namespace isvd {
 namespace {
@@ -68,6 +76,20 @@ __device__ __forceinline__ uint4 ld16(const void *p, uint64_t pol) {
                  : "l"(p), "l"(pol));
   else
     v = __ldg(reinterpret_cast<const uint4 *>(p));
+  return v;
+}
+
+// coherent (not .nc) 16-byte load with an L2 policy: for blocks that the
+// same kernel may also write (an in-place Horner accumulate)
+template <bool HINT>
+__device__ __forceinline__ uint4 ld16c(const void *p, uint64_t pol) {
+  uint4 v;
+  if (HINT)
+    asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+  else
+    v = *reinterpret_cast<const uint4 *>(p);
   return v;
 }
 
@@ -346,9 +368,9 @@ __device__ __forceinline__ void epilogue(const SpmmArgs &a, const SpmmSlab &sl, 
     for (int k = 0; k < VN; ++k) acc[k] *= sc;
     if (sl.axpy) {
       float v[VN];
-      // plain load: the axpy block may be the output block (in-place accumulate)
-      V::unpack(*reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(sl.axpy) +
-                                                 ((size_t)r * sl.lda + col) * V::BYTES),
+      // coherent load: the axpy block may be the output block (in-place accumulate)
+      V::unpack(ld16c<HINT>(reinterpret_cast<const char *>(sl.axpy) + ((size_t)r * sl.lda + col) * V::BYTES,
+                            pol.stream),
                 v);
 #pragma unroll
       for (int k = 0; k < VN; ++k) acc[k] = fmaf(as, v[k], acc[k]);
@@ -601,9 +623,9 @@ __global__ void __launch_bounds__(256) spmm_finish_big_kernel(const __grid_const
 // block's column indices (one coalesced load per index and lane), then
 // issue its gathers four at a time, so that a row costs one index round trip
 // per block whatever the slab width.
-template <int DT, int G, bool WEIGHTED>
+template <int DT, int G, bool WEIGHTED, bool HINT>
 __device__ __forceinline__ void gather_segment(const SpmmArgs &a, const SpmmSlab &sl, const Lane &L, int e0,
-                                               int len, int maxlen, float *acc) {
+                                               int len, int maxlen, const Policies &pol, float *acc) {
   using V = Vec<DT>;
   constexpr int VN = V::N;
   constexpr int U = G < 4 ? G : 4;
@@ -623,7 +645,7 @@ __device__ __forceinline__ void gather_segment(const SpmmArgs &a, const SpmmSlab
       if (WEIGHTED) w[q] = 1.f;
       if (t < len) {
         const int e = e0 + t;
-        j[q] = __ldg(a.colidx + e);
+        j[q] = ld_idx<HINT>(a.colidx + e, pol.stream);
         if (WEIGHTED) {
           w[q] = a.values ? __ldg(a.values + e) : 1.f;
           if (a.colw) w[q] *= __ldg(a.colw + j[q]);
@@ -646,7 +668,8 @@ __device__ __forceinline__ void gather_segment(const SpmmArgs &a, const SpmmSlab
         if (L.active) {
           uint4 raw[U];
 #pragma unroll
-          for (int u = 0; u < U; ++u) raw[u] = jj[u] >= 0 ? ld16<false>(inb + (size_t)jj[u] * ldb, 0) : zero;
+          for (int u = 0; u < U; ++u)
+            raw[u] = jj[u] >= 0 ? ld16<HINT && ISVD_SLAB_GATHER_KEEP>(inb + (size_t)jj[u] * ldb, pol.keep) : zero;
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             float v[VN];
@@ -664,7 +687,7 @@ __device__ __forceinline__ void gather_segment(const SpmmArgs &a, const SpmmSlab
 // per segment, 32 / group segments per warp.  Whole rows end in the epilogue;
 // hub pieces store partials, and the group that finishes a hub's last piece
 // sums the hub's partials in slot order and runs the epilogue.
-template <int DT, int G, int MINB>
+template <int DT, int G, int MINB, bool HINT>
 __global__ void __launch_bounds__(256, MINB)
     spmm_slab_kernel(const __grid_constant__ SpmmArgs a, const int4 *__restrict__ items, int32_t n_items,
                      const int4 *__restrict__ hubs, const int32_t *__restrict__ slot_hub, int32_t *counters,
@@ -672,7 +695,8 @@ __global__ void __launch_bounds__(256, MINB)
   constexpr int VN = Vec<DT>::N;
   const SpmmSlab &sl = a.slab[0];
   const Lane L = make_lane<DT>(sl);  // sl.group == G
-  const Policies pol{0, 0};
+  Policies pol{0, 0};
+  if (HINT) pol = Policies{policy_keep(), policy_stream()};
   constexpr int rpw = 32 / G;
   const bool weighted = a.values != nullptr || a.colw != nullptr;
   const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -686,11 +710,11 @@ __global__ void __launch_bounds__(256, MINB)
     float acc[VN];
 #pragma unroll
     for (int k = 0; k < VN; ++k) acc[k] = 0.f;
-    if (weighted) gather_segment<DT, G, true>(a, sl, L, item.y, len, maxlen, acc);
-    else gather_segment<DT, G, false>(a, sl, L, item.y, len, maxlen, acc);
+    if (weighted) gather_segment<DT, G, true, HINT>(a, sl, L, item.y, len, maxlen, pol, acc);
+    else gather_segment<DT, G, false, HINT>(a, sl, L, item.y, len, maxlen, pol, acc);
     if (item.w == -2) continue;
     if (item.w == -1) {
-      epilogue<DT, false, 1>(a, sl, L, item.x, pol, acc);
+      epilogue<DT, HINT, 1>(a, sl, L, item.x, pol, acc);
       continue;
     }
     // a hub piece: publish the partial, then count it
@@ -724,7 +748,7 @@ __global__ void __launch_bounds__(256, MINB)
         }
       }
     }
-    epilogue<DT, false, 1>(a, sl, L, hb.x, pol, acc);
+    epilogue<DT, HINT, 1>(a, sl, L, hb.x, pol, acc);
     if (L.gl == 0) counters[h] = 0;  // ready for the next launch
   }
 }
@@ -831,6 +855,8 @@ int make_slabs(int dtype, int32_t b, int32_t slab_cols, SpmmSlab *out) {
   return n;
 }
 
+constexpr bool kSlabHints = true;
+
 template <int DT, int MINB>
 cudaError_t slab_launch_one(const SpmmArgs &one, const SlabPlan &p, float *partial, int64_t pw, cudaStream_t s) {
   const int G = one.slab[0].group;
@@ -838,10 +864,10 @@ cudaError_t slab_launch_one(const SpmmArgs &one, const SlabPlan &p, float *parti
   const int64_t cap = (int64_t)kNumSMs * MINB;
   if (bx > cap) bx = cap;
   const dim3 grid((unsigned)bx);
-#define ISVD_SLAB_CASE(g)                                                                                     \
-  case g:                                                                                                     \
-    spmm_slab_kernel<DT, g, MINB><<<grid, 256, 0, s>>>(one, p.items, p.n_items, p.hubs, p.slot_hub, p.counters, \
-                                                       partial, pw);                                          \
+#define ISVD_SLAB_CASE(g)                                                                                      \
+  case g:                                                                                                      \
+    spmm_slab_kernel<DT, g, MINB, kSlabHints><<<grid, 256, 0, s>>>(one, p.items, p.n_items, p.hubs, p.slot_hub,  \
+                                                                   p.counters, partial, pw);                   \
     break;
   switch (G) {
     ISVD_SLAB_CASE(1)

@@ -425,7 +425,10 @@ def test_invalid_graphs_rejected():
 def test_bad_svd_arguments(ne_small):
     with isvd.graph_operator(ne_small, coeffs=C5) as op:
         with pytest.raises(isvd.IsvdError) as e:
-            op.svd(150, 20, 1, 0)
+            op.svd(500, 20, 1, 0)  # block width above 512
+        assert e.value.name == "UNSUPPORTED"
+        with pytest.raises(isvd.IsvdError) as e:
+            op.svd(150, 20, 1, 0, precision="mixed")  # above 160: FP32 only
         assert e.value.name == "UNSUPPORTED"
         with pytest.raises(isvd.IsvdError) as e:
             op.svd(0, 2, 1, 0)
