@@ -310,9 +310,10 @@ def relative_residuals(op, U, S, V):
 def batched_section(args, flush, stream):
     """Many uneven problems (256 seeded graphs, n ~ U[500, 50,000], mean degree
     8, rank drawn from {16, 32, 64}, oversample 10, 4 power iterations): one
-    isvd_svd_batched call against one isvd_svd call per problem, FP32 and
-    mixed; equal error as for the single SVD, with the error the largest over
-    all problems."""
+    isvd_svd_batched call (graph of parallel branches) and one
+    isvd_svd_batched_persistent call (one persistent kernel) against one
+    isvd_svd call per problem, FP32 and mixed; equal error as for the single
+    SVD, with the error the largest over all problems."""
     import torch
 
     from paper_2111_06312_gb300 import isvd, synth
@@ -332,6 +333,13 @@ def batched_section(args, flush, stream):
 
         ms32, err32 = batch_ms("fp32", q)
         msm, errm = batch_ms("mixed", q)
+        # the same batch in one persistent kernel (FP32)
+        bp = isvd.Batch(ops, ranks, oversample=p, iters=q, seed=seed, persistent=True)
+        bp.run()
+        ms_p = float(np.mean(timed_steps(lambda: bp.run(check=False), args.steps, flush, stream)))
+        bp.run()
+        torch.cuda.synchronize()
+        err_p = max(float(relative_residuals(op, bp.U[i], bp.S[i], bp.V[i]).max()) for i, op in enumerate(ops))
         eq = None
         for qm in range(q, q + 5):
             t, e = (msm, errm) if qm == q else batch_ms("mixed", qm)
@@ -352,6 +360,9 @@ def batched_section(args, flush, stream):
         return {"count": len(ops), "sum_n": int(sum(gr.n for gr in graphs)),
                 "sum_nnz": int(sum(gr.nnz for gr in graphs)), "oversample": p, "iters": q,
                 "batched_fp32_ms": ms32, "single_calls_fp32_ms": single_ms, "speedup_batched_over_single": single_ms / ms32,
+                "persistent_fp32_ms": ms_p, "persistent_max_rel_residual": err_p,
+                "speedup_persistent_over_graph": ms32 / ms_p, "persistent_teams": int(sum(
+                    min(8, max(1, -(-gr.n // 16384))) for gr in graphs)),
                 "batched_mixed_ms": msm, "fp32_max_rel_residual": err32, "mixed_max_rel_residual": errm,
                 "mixed_at_equal_error": eq,
                 "error": "largest over all problems of max_i r_i / s_i (library FP32 products)"}

@@ -218,6 +218,33 @@ ISVD_API isvd_status isvd_svd_batched(isvd_operator *const *ops, const int32_t *
  * isvd_svd_batched call (-1 if none).  Introspection for benchmarks. */
 ISVD_API int64_t isvd_batched_kernel_nodes(void);
 
+/* The same batch in ONE persistent kernel (FP32): each problem is taken by
+ * a team of 1..8 CTAs (one per 16,384 rows, at most max_team) that runs the
+ * whole of Alg. 1 for it, its members meeting at a per-problem stage counter
+ * in device memory wherever a step reads rows another member wrote (the
+ * sparse products, the summed Gram matrices and column sums).  Every wait is
+ * bounded: one that runs out abandons that problem (status
+ * ISVD_ERR_TIMEOUT in its isvd_info) and the kernel goes on with the others.
+ * Arguments as isvd_svd_batched (precision FP32); results equal isvd_svd's up
+ * to rounding.  Takes polynomial operators of an unweighted graph (Eq. 3 with
+ * N = T or A-hat, at most the all-ones term; no values, beta A, low-rank
+ * terms, row gather or composite nodes), k + oversample <=
+ * ISVD_PERSISTENT_MAX_BLOCK, else ISVD_ERR_UNSUPPORTED.  opt may be NULL.
+ * Workspace from each problem's operator (operator 0 also holds the queue).
+ * Asynchronous on `stream`: one cooperative kernel launch after a few copies. */
+#define ISVD_PERSISTENT_MAX_BLOCK 96
+typedef struct {
+  int32_t max_team;     /* CTAs per problem at most (0: 8) */
+  int32_t spin_limit;   /* polls of a team wait before it gives up (0: ~4 million, seconds) */
+  int32_t test_phantom; /* test only: every team waits for one member more than it has,
+                           so that every wait runs out (the failure path, without a fault) */
+} isvd_persistent_options;
+ISVD_API isvd_status isvd_svd_batched_persistent(isvd_operator *const *ops, const int32_t *k, int32_t count,
+                                                 int32_t oversample, int32_t iters, uint64_t seed,
+                                                 float *const *U, float *const *S, float *const *V,
+                                                 isvd_info *dev_info, const isvd_persistent_options *opt,
+                                                 void *stream);
+
 /* --- individual steps, exported for verification and reuse --------------- */
 
 /* out[i][j] (rows x cols) = standard normal from Philox4x32-10 (Salmon et al.

@@ -128,6 +128,7 @@ def lib():
             L.isvd_split_relu_backward.argtypes = [P, I64, I64, I32, P, P, I32, P, P, I64, P, I64, P, I64, P, P, P,
                                                    C.c_size_t, P]
             L.isvd_svd_batched.argtypes = [P, P, I32, I32, I32, U64, C.c_int, P, P, P, P, P]
+            L.isvd_svd_batched_persistent.argtypes = [P, P, I32, I32, I32, U64, P, P, P, P, P, P]
             L.isvd_autotune.argtypes = [P, I32, C.c_int, C.c_char_p, P, P]
             L.isvd_selftest_wait.argtypes = [I32, P, P]
             L.isvd_batched_kernel_nodes.argtypes = []
@@ -143,6 +144,7 @@ def lib():
                          "isvd_closed_form", "isvd_compose_operators", "isvd_embed", "isvd_pair_scores",
                          "isvd_edge_kernel_weights", "isvd_edge_kernel_scores", "isvd_edge_kernel_loss",
                          "isvd_get_tuning", "isvd_set_tuning", "isvd_orthonormalize_noalloc", "isvd_svd_batched", "isvd_autotune",
+                         "isvd_svd_batched_persistent",
                          "isvd_composite_cache", "isvd_split_relu_forward", "isvd_split_relu_backward",
                          "isvd_selftest_wait"):
                 getattr(L, name).restype = C.c_int
@@ -606,12 +608,21 @@ class EdgeKernel:
         return hist
 
 
-class Batch:
-    """Many independent rank-k SVDs in one call (isvd_svd_batched).  Output
-    buffers are allocated once and reused, so that repeated calls replay one
-    captured graph."""
+class _PersistentOptions(C.Structure):
+    _fields_ = [("max_team", C.c_int32), ("spin_limit", C.c_int32), ("test_phantom", C.c_int32)]
 
-    def __init__(self, ops, ks, oversample: int = 10, iters: int = 4, seed: int = 0, precision: str = "fp32"):
+
+class Batch:
+    """Many independent rank-k SVDs in one call: isvd_svd_batched (one
+    captured graph of parallel branches), or with ``persistent=True``
+    isvd_svd_batched_persistent (one persistent kernel; FP32; ``max_team``,
+    ``spin_limit`` and ``test_phantom`` as its options).  Output buffers are
+    allocated once and reused."""
+
+    def __init__(self, ops, ks, oversample: int = 10, iters: int = 4, seed: int = 0, precision: str = "fp32",
+                 persistent: bool = False, max_team: int = 0, spin_limit: int = 0, test_phantom: bool = False):
+        self.persistent = bool(persistent)
+        self._opt = _PersistentOptions(int(max_team), int(spin_limit), 1 if test_phantom else 0)
         if len(ops) != len(ks) or not ops:
             raise ValueError("need one rank per operator")
         self.ops = list(ops)
@@ -630,9 +641,17 @@ class Batch:
         self._h_V = (C.c_void_p * n)(*[t.data_ptr() for t in self.V])
 
     def run(self, check: bool = True):
-        _check(lib().isvd_svd_batched(self._h_ops, self._h_k, len(self.ops), self.oversample, self.iters,
-                                      C.c_uint64(self.seed), PREC[self.precision], self._h_U, self._h_S, self._h_V,
-                                      _ptr(self.info), _stream()), "isvd_svd_batched")
+        if self.persistent:
+            if self.precision != "fp32":
+                raise ValueError("the persistent batch runs in FP32")
+            _check(lib().isvd_svd_batched_persistent(self._h_ops, self._h_k, len(self.ops), self.oversample,
+                                                     self.iters, C.c_uint64(self.seed), self._h_U, self._h_S,
+                                                     self._h_V, _ptr(self.info), C.byref(self._opt), _stream()),
+                   "isvd_svd_batched_persistent")
+        else:
+            _check(lib().isvd_svd_batched(self._h_ops, self._h_k, len(self.ops), self.oversample, self.iters,
+                                          C.c_uint64(self.seed), PREC[self.precision], self._h_U, self._h_S,
+                                          self._h_V, _ptr(self.info), _stream()), "isvd_svd_batched")
         if check:
             torch.cuda.current_stream().synchronize()
             bad = torch.nonzero(self.info[:, 0]).reshape(-1).tolist()
