@@ -362,7 +362,7 @@ def batched_section(args, flush, stream):
                 "batched_fp32_ms": ms32, "single_calls_fp32_ms": single_ms, "speedup_batched_over_single": single_ms / ms32,
                 "persistent_fp32_ms": ms_p, "persistent_max_rel_residual": err_p,
                 "speedup_persistent_over_graph": ms32 / ms_p, "persistent_teams": int(sum(
-                    min(8, max(1, -(-gr.n // 16384))) for gr in graphs)),
+                    min(32, max(1, -(-gr.n // 16384))) for gr in graphs)),
                 "batched_mixed_ms": msm, "fp32_max_rel_residual": err32, "mixed_max_rel_residual": errm,
                 "mixed_at_equal_error": eq,
                 "error": "largest over all problems of max_i r_i / s_i (library FP32 products)"}

@@ -219,8 +219,8 @@ ISVD_API isvd_status isvd_svd_batched(isvd_operator *const *ops, const int32_t *
 ISVD_API int64_t isvd_batched_kernel_nodes(void);
 
 /* The same batch in ONE persistent kernel (FP32): each problem is taken by
- * a team of 1..8 CTAs (one per 16,384 rows, at most max_team) that runs the
- * whole of Alg. 1 for it, its members meeting at a per-problem stage counter
+ * a team of 1..32 CTAs (one per rows_per_member rows, at most max_team) that
+ * runs the whole of Alg. 1 for it, its members meeting at a per-problem stage counter
  * in device memory wherever a step reads rows another member wrote (the
  * sparse products, the summed Gram matrices and column sums).  Every wait is
  * bounded: one that runs out abandons that problem (status
@@ -234,7 +234,8 @@ ISVD_API int64_t isvd_batched_kernel_nodes(void);
  * Asynchronous on `stream`: one cooperative kernel launch after a few copies. */
 #define ISVD_PERSISTENT_MAX_BLOCK 96
 typedef struct {
-  int32_t max_team;     /* CTAs per problem at most (0: 8) */
+  int32_t max_team;     /* CTAs per problem at most (0: 32) */
+  int32_t rows_per_member; /* rows per team member (0: 16384) */
   int32_t spin_limit;   /* polls of a team wait before it gives up (0: ~4 million, seconds) */
   int32_t test_phantom; /* test only: every team waits for one member more than it has,
                            so that every wait runs out (the failure path, without a fault) */

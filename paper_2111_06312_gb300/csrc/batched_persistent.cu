@@ -1,7 +1,7 @@
 // Many independent rank-k SVDs (Alg. 1 on each problem) in ONE persistent
 // kernel: the batched form with per-problem stage counters and bounded waits.
 //
-// A problem is taken by a team of T CTAs (T from its size, 1..8), member m
+// A problem is taken by a team of T CTAs (one per 16,384 rows, 1..32), member m
 // owning rows [n m / T, n (m + 1) / T) of every block.  The CTAs of the grid
 // (all resident: cooperative launch, one per SM) pull (problem, member) items
 // from one queue in which a team's members are consecutive and the largest
@@ -37,7 +37,8 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxL = ISVD_PERSISTENT_MAX_BLOCK;
-constexpr int kMaxTeam = 8;
+constexpr int kMaxTeam = 32;
+constexpr int kDefaultTeamRows = 16384;  // rows per team member (measured best of 1,024..16,384)
 constexpr int kStageRows = 128;         // rows of a block staged in shared memory
 constexpr int kPromoteChunks = 4;       // Gram: FP32 sums promoted to FP64 every 512 rows
 constexpr uint32_t kDefaultSpin = 1u << 22;
@@ -192,6 +193,39 @@ __device__ bool column_sums(Ctx &c, const float *G) {
 
 // ---- one sparse product of the Horner chain, rows of this member ----
 // out_i = mult (op src)_i + axc G_i [+ ones_b], op = T (norm row), T^T, or A-hat.
+// A group of Gl lanes (one 16-byte column chunk each) takes two rows at a
+// time, A and B, so that their index and gather round trips overlap: the
+// group loads Gl column indices of each row at once (one per lane), then
+// every lane gathers its chunk of four rows of A and four of B at a time.
+__device__ __forceinline__ float4 fma4(float w, float4 v, float4 a) {
+  return make_float4(fmaf(w, v.x, a.x), fmaf(w, v.y, a.y), fmaf(w, v.z, a.z), fmaf(w, v.w, a.w));
+}
+
+__device__ void sparse_epilogue(Ctx &c, const float *src, float *out, float mult, const float *G, float axc,
+                                bool transpose, bool add_ones, int64_t i, int gl, float4 acc, float4 g) {
+  const Problem &P = c.P;
+  float sc;
+  if (P.norm == ISVD_NORM_ROW) {
+    sc = transpose ? 1.f : __ldg(P.inv_d + i);
+  } else {
+    const float si = __ldg(P.s + i);
+    if (P.norm == ISVD_NORM_SYM_SELFLOOP)
+      acc = fma4(si, __ldcg(reinterpret_cast<const float4 *>(src + i * P.ld) + gl), acc);
+    sc = si;
+  }
+  sc *= mult;
+  float4 r = make_float4(sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+  if (G) r = fma4(axc, g, r);
+  if (add_ones) {
+    const int b = 4 * gl;
+    if (b + 0 < P.l) r.x += c.sm.ones[b + 0];
+    if (b + 1 < P.l) r.y += c.sm.ones[b + 1];
+    if (b + 2 < P.l) r.z += c.sm.ones[b + 2];
+    if (b + 3 < P.l) r.w += c.sm.ones[b + 3];
+  }
+  reinterpret_cast<float4 *>(out + i * P.ld)[gl] = r;
+}
+
 __device__ void sparse_step(Ctx &c, const float *src, float *out, float mult, const float *G, float axc,
                             bool transpose, bool add_ones) {
   const Problem &P = c.P;
@@ -201,74 +235,70 @@ __device__ void sparse_step(Ctx &c, const float *src, float *out, float mult, co
   const int rpw = 32 / Gl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sub = lane / Gl, gl = lane - sub * Gl;
+  const int lead = sub * Gl;
   const bool active = gl < nq;
   const bool row = P.norm == ISVD_NORM_ROW;
-  const bool selfloop = P.norm == ISVD_NORM_SYM_SELFLOOP;
-  for (int64_t base = c.r0 + (int64_t)warp * rpw; base < c.r1; base += (int64_t)kWarps * rpw) {
-    const int64_t i = base + sub;
-    const bool have = i < c.r1;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int e0 = 0, e1 = 0;
-    if (have) {
-      e0 = __ldg(P.rowptr + i);
-      e1 = __ldg(P.rowptr + i + 1);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto weight = [&](int j) { return row ? (transpose ? __ldg(P.inv_d + j) : 1.f) : __ldg(P.s + j); };
+  for (int64_t base = c.r0 + (int64_t)warp * 2 * rpw; base < c.r1; base += (int64_t)kWarps * 2 * rpw) {
+    const int64_t iA = base + sub, iB = base + rpw + sub;
+    const bool hA = iA < c.r1, hB = iB < c.r1;
+    int eA = 0, lenA = 0, eB = 0, lenB = 0;
+    if (hA) {
+      eA = __ldg(P.rowptr + iA);
+      lenA = __ldg(P.rowptr + iA + 1) - eA;
     }
-    for (int e = e0; e < e1; e += 4) {
-      int j[4];
-      float w[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        j[u] = e + u < e1 ? __ldg(P.colidx + e + u) : -1;
-        w[u] = 0.f;
-        if (j[u] >= 0) w[u] = row ? (transpose ? __ldg(P.inv_d + j[u]) : 1.f) : __ldg(P.s + j[u]);
-      }
-      if (active) {
-        float4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          v[u] = j[u] >= 0 ? __ldcg(reinterpret_cast<const float4 *>(src + (int64_t)j[u] * P.ld) + gl)
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (hB) {
+      eB = __ldg(P.rowptr + iB);
+      lenB = __ldg(P.rowptr + iB + 1) - eB;
+    }
+    float4 gA = zero, gB = zero;  // the axpy operand, loaded ahead of the gathers
+    if (G && active) {
+      if (hA) gA = __ldcg(reinterpret_cast<const float4 *>(G + iA * P.ld) + gl);
+      if (hB) gB = __ldcg(reinterpret_cast<const float4 *>(G + iB * P.ld) + gl);
+    }
+    float4 accA = zero, accB = zero;
+    const int len = max(lenA, lenB);
+    for (int off = 0; __any_sync(0xffffffffu, off < len); off += Gl) {
+      int jA = -1, jB = -1;
+      float wA = 0.f, wB = 0.f;
+      if (off + gl < lenA) jA = __ldg(P.colidx + eA + off + gl);
+      if (off + gl < lenB) jB = __ldg(P.colidx + eB + off + gl);
+      if (jA >= 0) wA = weight(jA);
+      if (jB >= 0) wB = weight(jB);
+      const int cA = max(0, min(Gl, lenA - off)), cB = max(0, min(Gl, lenB - off));
+      const int wcnt = __reduce_max_sync(0xffffffffu, max(cA, cB));  // the warp steps to its longest row
+      for (int u0 = 0; u0 < wcnt; u0 += 4) {
+        int ja[4], jb[4];
+        float wa[4], wb[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          acc.x = fmaf(w[u], v[u].x, acc.x);
-          acc.y = fmaf(w[u], v[u].y, acc.y);
-          acc.z = fmaf(w[u], v[u].z, acc.z);
-          acc.w = fmaf(w[u], v[u].w, acc.w);
+          const int sl = lead + ((u0 + u) & (Gl - 1));
+          ja[u] = __shfl_sync(0xffffffffu, jA, sl);
+          wa[u] = __shfl_sync(0xffffffffu, wA, sl);
+          jb[u] = __shfl_sync(0xffffffffu, jB, sl);
+          wb[u] = __shfl_sync(0xffffffffu, wB, sl);
+          if (u0 + u >= cA) ja[u] = -1;
+          if (u0 + u >= cB) jb[u] = -1;
+        }
+        if (active) {
+          float4 va[4], vb[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            va[u] = ja[u] >= 0 ? __ldcg(reinterpret_cast<const float4 *>(src + (int64_t)ja[u] * P.ld) + gl) : zero;
+            vb[u] = jb[u] >= 0 ? __ldcg(reinterpret_cast<const float4 *>(src + (int64_t)jb[u] * P.ld) + gl) : zero;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            accA = fma4(wa[u], va[u], accA);
+            accB = fma4(wb[u], vb[u], accB);
+          }
         }
       }
     }
-    if (!have || !active) continue;
-    float sc;
-    if (row) {
-      sc = transpose ? 1.f : __ldg(P.inv_d + i);
-    } else {
-      const float si = __ldg(P.s + i);
-      if (selfloop) {
-        const float4 x = __ldcg(reinterpret_cast<const float4 *>(src + i * P.ld) + gl);
-        acc.x = fmaf(si, x.x, acc.x);
-        acc.y = fmaf(si, x.y, acc.y);
-        acc.z = fmaf(si, x.z, acc.z);
-        acc.w = fmaf(si, x.w, acc.w);
-      }
-      sc = si;
-    }
-    sc *= mult;
-    float4 r = make_float4(sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
-    if (G) {
-      const float4 g = __ldcg(reinterpret_cast<const float4 *>(G + i * P.ld) + gl);
-      r.x = fmaf(axc, g.x, r.x);
-      r.y = fmaf(axc, g.y, r.y);
-      r.z = fmaf(axc, g.z, r.z);
-      r.w = fmaf(axc, g.w, r.w);
-    }
-    if (add_ones) {
-      const int b = 4 * gl;
-      if (b + 0 < P.l) r.x += c.sm.ones[b + 0];
-      if (b + 1 < P.l) r.y += c.sm.ones[b + 1];
-      if (b + 2 < P.l) r.z += c.sm.ones[b + 2];
-      if (b + 3 < P.l) r.w += c.sm.ones[b + 3];
-    }
-    reinterpret_cast<float4 *>(out + i * P.ld)[gl] = r;
+    if (!active) continue;
+    if (hA) sparse_epilogue(c, src, out, mult, G, axc, transpose, add_ones, iA, gl, accA, gA);
+    if (hB) sparse_epilogue(c, src, out, mult, G, axc, transpose, add_ones, iB, gl, accB, gB);
   }
 }
 
@@ -700,9 +730,15 @@ __device__ void run_member(const Problem &P, int member, uint32_t spin, int phan
   if (!orthonormalize(c, P.Qr, false, ps)) return;
   if (!apply(c, P.Qr, P.Qc, true)) return;  // B^T = M^T Q
   if (!orthonormalize(c, P.Qc, true, ps)) return;
-  if (member == 0) rayleigh_ritz(c, P.Racc[ps.racc_cur]);
-  if (!team_meet(c)) return;  // Lk, Rk are written
-  // U = Q Vo_k, V = Qt Uo_k on this member's rows
+  // every row of both blocks is final; member 0 alone finishes (the others
+  // take the next item instead of waiting through the FP64 Jacobi)
+  if (!team_meet(c)) return;
+  if (member != 0) return;
+  rayleigh_ritz(c, P.Racc[ps.racc_cur]);
+  __syncthreads();
+  // U = Q Vo_k, V = Qt Uo_k over all rows
+  c.r0 = 0;
+  c.r1 = P.n;
   const int k = P.k;
   for (int idx = threadIdx.x; idx < P.l * P.ld; idx += kThreads) {
     const int i = idx / P.ld, col = idx - i * P.ld;
@@ -770,6 +806,7 @@ isvd_status isvd_svd_batched_persistent(isvd_operator *const *ops, const int32_t
   if (!ops || !k || !U || !S || !V || count < 1) return fail(ISVD_ERR_INVALID_ARGUMENT, "null argument or count < 1");
   if (oversample < 0 || iters < 0) return fail(ISVD_ERR_INVALID_ARGUMENT, "need oversample >= 0, iters >= 0");
   const int32_t max_team = opt && opt->max_team > 0 ? std::min(opt->max_team, kMaxTeam) : kMaxTeam;
+  const int64_t team_rows = opt && opt->rows_per_member > 0 ? opt->rows_per_member : kDefaultTeamRows;
   const uint32_t spin = opt && opt->spin_limit > 0 ? (uint32_t)opt->spin_limit : kDefaultSpin;
   const int32_t phantom = opt && opt->test_phantom ? 1 : 0;
   cudaStream_t s = (cudaStream_t)stream;
@@ -801,7 +838,7 @@ isvd_status isvd_svd_batched_persistent(isvd_operator *const *ops, const int32_t
     P.l = (int32_t)l;
     P.ld = (int32_t)round_up(l, 4);
     P.k = k[i];
-    P.team = (int32_t)std::min<int64_t>(std::max<int64_t>(1, ceil_div(op->n, 16384)), max_team);
+    P.team = (int32_t)std::min<int64_t>(std::max<int64_t>(1, ceil_div(op->n, team_rows)), max_team);
     P.team = std::min(P.team, std::max(1, sms));
     P.norm = d.norm;
     P.degree = d.degree;

@@ -609,20 +609,23 @@ class EdgeKernel:
 
 
 class _PersistentOptions(C.Structure):
-    _fields_ = [("max_team", C.c_int32), ("spin_limit", C.c_int32), ("test_phantom", C.c_int32)]
+    _fields_ = [("max_team", C.c_int32), ("rows_per_member", C.c_int32), ("spin_limit", C.c_int32),
+                ("test_phantom", C.c_int32)]
 
 
 class Batch:
     """Many independent rank-k SVDs in one call: isvd_svd_batched (one
     captured graph of parallel branches), or with ``persistent=True``
     isvd_svd_batched_persistent (one persistent kernel; FP32; ``max_team``,
-    ``spin_limit`` and ``test_phantom`` as its options).  Output buffers are
-    allocated once and reused."""
+    ``rows_per_member``, ``spin_limit`` and ``test_phantom`` as its options).
+    Output buffers are allocated once and reused."""
 
     def __init__(self, ops, ks, oversample: int = 10, iters: int = 4, seed: int = 0, precision: str = "fp32",
-                 persistent: bool = False, max_team: int = 0, spin_limit: int = 0, test_phantom: bool = False):
+                 persistent: bool = False, max_team: int = 0, rows_per_member: int = 0, spin_limit: int = 0,
+                 test_phantom: bool = False):
         self.persistent = bool(persistent)
-        self._opt = _PersistentOptions(int(max_team), int(spin_limit), 1 if test_phantom else 0)
+        self._opt = _PersistentOptions(int(max_team), int(rows_per_member), int(spin_limit),
+                                       1 if test_phantom else 0)
         if len(ops) != len(ks) or not ops:
             raise ValueError("need one rank per operator")
         self.ops = list(ops)

@@ -28,7 +28,8 @@ def built():
 
 
 # sizes span one-member teams and teams of 2 and 3 (one member per 16,384
-# rows); norms: T = D^-1 A and A-hat (with and without its identity term)
+# rows by default); norms: T = D^-1 A and A-hat (with and without its
+# identity term)
 SIZES = [700, 1500, 3100, 900, 2500, 4000, 520, 20000, 33000]
 RANKS = [16, 32, 64, 16, 32, 8, 16, 32, 64]
 NORMS = ["row", "row", "sym", "row", "sym_noself", "row", "row", "sym", "row"]
@@ -82,8 +83,11 @@ def test_persistent_team_size_changes_rounding_only(problems):
     _, ops = problems
     _, S1, _, _ = _run(ops, max_team=1)
     _, S3, _, info = _run(ops, max_team=3)
-    assert int(info[:, 0].abs().sum()) == 0
+    _, S9, _, info9 = _run(ops, rows_per_member=4096)  # teams of up to 9
+    assert int(info[:, 0].abs().sum()) == 0 and int(info9[:, 0].abs().sum()) == 0
     for i in range(len(ops)):
+        rel = ((S9[i].double() - S3[i].double()).abs() / S3[i].double()).max().item()
+        assert rel < 1e-5, (i, rel)
         rel = ((S1[i].double() - S3[i].double()).abs() / S3[i].double()).max().item()
         assert rel < 1e-5, (i, rel)
 
