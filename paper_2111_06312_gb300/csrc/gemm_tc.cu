@@ -101,6 +101,7 @@ struct GemmOut {
   void *out;
   int64_t ldo;
   int32_t n0, w, tri;
+  int32_t sub;  // FP32 only: out <- out - Q B (the output block read back in the epilogue)
 };
 
 // kRaw: raw panels in flight (refilled by the producers alone); 3 where the
@@ -364,6 +365,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           // multiple of 8 elements); element stores for a ragged tail
           const int n = min(32, o.w - cb);
           if (C::F32) {
+            if (o.sub) {
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                if (j + 4 <= n) {
+                  const float4 old = *reinterpret_cast<const float4 *>(dst + j * 4);
+                  v[j] = __float_as_uint(old.x - __uint_as_float(v[j]));
+                  v[j + 1] = __float_as_uint(old.y - __uint_as_float(v[j + 1]));
+                  v[j + 2] = __float_as_uint(old.z - __uint_as_float(v[j + 2]));
+                  v[j + 3] = __float_as_uint(old.w - __uint_as_float(v[j + 3]));
+                } else {
+#pragma unroll
+                  for (int t = 0; t < 4; ++t)
+                    if (j + t < n)
+                      v[j + t] = __float_as_uint(reinterpret_cast<const float *>(dst)[j + t] - __uint_as_float(v[j + t]));
+                }
+              }
+            }
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
               if (j + 8 <= n) {
@@ -515,14 +533,14 @@ cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t row
 }
 
 cudaError_t gemm_tc_launch(const float *Q, int64_t ldq, int64_t rows, int32_t l, const float *B, int64_t ldb,
-                           int32_t w, float *out, int64_t ldo, bool *launched, cudaStream_t s) {
+                           int32_t w, float *out, int64_t ldo, bool *launched, cudaStream_t s, bool subtract) {
   *launched = false;
   cudaError_t e = gemm_tc_init();
   if (e != cudaSuccess) return e;
   // 16-byte stores and TMA boxes need 16-byte rows; the caller falls back otherwise
   if (rows == 0 || w == 0 || ((uintptr_t)out & 15) || (ldo & 3) || ((uintptr_t)Q & 15) || (ldq & 3))
     return cudaSuccess;
-  const GemmOut o{out, ldo, 0, w, 0};
+  const GemmOut o{out, ldo, 0, w, 0, subtract ? 1 : 0};
   *launched = launch_gemm<DT_F32>(Q, ldq, rows, l, B, ldb, o, PassGate{}, s);
   return cudaGetLastError();
 }

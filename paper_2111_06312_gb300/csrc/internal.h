@@ -202,10 +202,12 @@ cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int
 // Q <- Q B in place on the tensor cores, B (l x l, FP32) upper triangular.
 cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, const float *B,
                                     int64_t ldb, PassGate g, cudaStream_t s);
-// Out[:, 0:w] = Q B[:, 0:w] on the tensor cores (3xTF32), Q rows x l FP32;
-// *launched = false (nothing enqueued) where the layout does not suit it.
+// Out[:, 0:w] = Q B[:, 0:w] on the tensor cores (3xTF32), Q rows x l FP32, or
+// with `subtract` Out[:, 0:w] -= Q B[:, 0:w] (Out must not overlap the columns
+// of Q); *launched = false (nothing enqueued) where the layout does not suit it.
 cudaError_t gemm_tc_launch(const float *Q, int64_t ldq, int64_t rows, int32_t l, const float *B, int64_t ldb,
-                           int32_t w, float *out, int64_t ldo, bool *launched, cudaStream_t s);
+                           int32_t w, float *out, int64_t ldo, bool *launched, cudaStream_t s,
+                           bool subtract = false);
 
 // out (rows x w) = Q (rows x l) B (l x w, FP32, ld ldb); upper: B upper
 // triangular.  out may equal Q (in place) when w == l and out dtype == in dtype.

@@ -8,7 +8,7 @@
 // projected off the panels before it twice,
 //     C = Q_<j^T Y,  Y <- Y - Q_<j C      (C summed in FP64 over row ranges)
 // and then orthonormalised by CholeskyQR2 (Alg. 2, twice, with the shift on
-// breakdown).  The result is the thin QR of the block (the same Q and R, up
+// breakdown); the subtraction happens in the epilogue of the Q_i C product.  The result is the thin QR of the block (the same Q and R, up
 // to rounding, as one CholeskyQR2 of all l columns): R is block upper
 // triangular with the two projections' C above the diagonal and the panels'
 // CholeskyQR factors on it.  Q_i^T Y runs on the tcgen05 A^T B kernel,
@@ -109,12 +109,14 @@ isvd_status wide_orth_enqueue(float *Q, int64_t ldq, int64_t rows, int32_t l, do
         ISVD_CUDA_TRY(cudaGetLastError());
       }
       for (int32_t i = 0; i < j; ++i) {
+        // Y -= Q_i C_i: in the tensor-core epilogue, else through T
         bool launched = false;
         const float *Ci = C32 + (size_t)i * kPanel * kPanel;
-        ISVD_CUDA_TRY(gemm_tc_launch(Q + (size_t)i * kPanel, ldq, rows, kPanel, Ci, wj, wj, T, kPanel, &launched, s));
-        if (!launched)
-          ISVD_CUDA_TRY(gemm_small_launch(Q + (size_t)i * kPanel, ldq, DT_F32, rows, kPanel, Ci, wj, wj, false, T,
-                                          kPanel, DT_F32, PassGate{}, s));
+        ISVD_CUDA_TRY(
+            gemm_tc_launch(Q + (size_t)i * kPanel, ldq, rows, kPanel, Ci, wj, wj, Y, ldq, &launched, s, true));
+        if (launched) continue;
+        ISVD_CUDA_TRY(gemm_small_launch(Q + (size_t)i * kPanel, ldq, DT_F32, rows, kPanel, Ci, wj, wj, false, T,
+                                        kPanel, DT_F32, PassGate{}, s));
         subtract_kernel<<<grid_for_elems(rows * wj), 256, 0, s>>>(Y, ldq, T, kPanel, rows, wj);
         ISVD_CUDA_TRY(cudaGetLastError());
       }
