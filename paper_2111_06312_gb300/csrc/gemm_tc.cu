@@ -102,7 +102,28 @@ struct GemmOut {
   int64_t ldo;
   int32_t n0, w, tri;
   int32_t sub;  // FP32 only: out <- out - Q B (the output block read back in the epilogue)
+  // nullable: column sums of the stored output (the all-ones projection 1^T Q
+  // of the next product), FP64 partials [gridDim.x * 4][cs_ld], one per CTA
+  // and TMEM lane quarter
+  double *colsum;
+  int32_t cs_ld;
 };
+
+// Sum over the 32 lanes of each of x[0..31], lane c receiving column c's
+// sum: five halving exchanges (16 + 8 + 4 + 2 + 1 shuffles).
+__device__ __forceinline__ float lane_column_sum(float x[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float keep = upper ? x[h + i] : x[i];
+      const float give = upper ? x[i] : x[h + i];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, give, h);
+    }
+  }
+  return x[0];
+}
 
 // kRaw: raw panels in flight (refilled by the producers alone); 3 where the
 // shared memory allows, else 2.
@@ -347,6 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     char *Out = reinterpret_cast<char *>(o.out);
     // every row start is 32-byte aligned (the column offsets below are multiples of 32 bytes)
     const bool v32 = ((uintptr_t)Out & 31) == 0 && ((o.ldo * C::ES) & 31) == 0;
+    double cacc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // column sums (chunk cb / 32, column cb + lane)
     for (int64_t lt = 0; lt < my_tiles; ++lt) {
       const int d = (int)(lt & 1);
       if (!mbar_wait_sleep(&dfull[d], (uint32_t)((lt >> 1) & 1), 256)) {
@@ -414,10 +436,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
+        if (o.colsum) {
+          // the values as stored (BF16 rounded), rows past the end and
+          // columns past w as zero
+          const int n = min(32, o.w - cb);
+          float x[32];
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            float y = __uint_as_float(v[t]);
+            if (!C::F32) y = __bfloat162float(__float2bfloat16_rn(y));
+            x[t] = (row < rows && t < n) ? y : 0.f;
+          }
+          const float cs = lane_column_sum(x, lane);
+#pragma unroll
+          for (int k = 0; k < 5; ++k)
+            if (k == cb / 32) cacc[k] += (double)cs;
+        }
       }
       fence_before();
       mbar_arrive(&dfree[d]);
     }
+    if (o.colsum)
+      for (int cb = 0; cb < L.N1; cb += 32)
+        if (cb + lane < o.w) {
+          double c = 0.0;
+#pragma unroll
+          for (int k = 0; k < 5; ++k)
+            if (k == cb / 32) c = cacc[k];
+          o.colsum[((size_t)blockIdx.x * 4 + sub) * o.cs_ld + cb + lane] = c;
+        }
   }
   fence_before();
   __syncthreads();
@@ -521,11 +568,40 @@ bool launch_gemm(const void *Q, int64_t ldq, int64_t rows, int32_t l, const floa
 
 }  // namespace
 
+int32_t gemm_colsum_parts(int64_t rows) {
+  const int64_t ntiles = (rows + 127) / 128;
+  return 4 * (int32_t)std::max<int64_t>(1, std::min<int64_t>(ntiles, kNumSMs));
+}
+
+namespace {
+// out[c] = (float) sum over parts of partial[part][c], c < b; columns
+// b..ldc-1 zero.  One warp per column: lane t adds parts t, t + 32, ... in
+// order, then a fixed shuffle tree (deterministic).
+__global__ void colsum_reduce_kernel(const double *__restrict__ partial, int32_t parts, int32_t ld, int32_t b,
+                                     int32_t ldc, float *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= ldc) return;
+  double s = 0.0;
+  if (c < b)
+    for (int p = lane; p < parts; p += 32) s += partial[(size_t)p * ld + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = (float)s;
+}
+}  // namespace
+
+cudaError_t colsum_reduce_launch(const double *partial, int32_t parts, int32_t ld, int32_t b, int32_t ldc, float *out,
+                                 cudaStream_t s) {
+  colsum_reduce_kernel<<<(unsigned)std::max(1, (ldc + 7) / 8), 256, 0, s>>>(partial, parts, ld, b, ldc, out);
+  return cudaGetLastError();
+}
+
 cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, const float *B,
-                                    int64_t ldb, PassGate g, cudaStream_t s) {
+                                    int64_t ldb, PassGate g, cudaStream_t s, double *colsum) {
   cudaError_t e = gemm_tc_init();
   if (e != cudaSuccess) return e;
-  const GemmOut o{Q, ldq, 0, l, 1};
+  const GemmOut o{Q, ldq, 0, l, 1, 0, colsum, l};
   const bool ok = dtype == DT_F32 ? launch_gemm<DT_F32>(Q, ldq, rows, l, B, ldb, o, g, s)
                                   : launch_gemm<DT_BF16>(Q, ldq, rows, l, B, ldb, o, g, s);
   if (!ok) return cudaErrorInvalidValue;
@@ -540,7 +616,7 @@ cudaError_t gemm_tc_launch(const float *Q, int64_t ldq, int64_t rows, int32_t l,
   // 16-byte stores and TMA boxes need 16-byte rows; the caller falls back otherwise
   if (rows == 0 || w == 0 || ((uintptr_t)out & 15) || (ldo & 3) || ((uintptr_t)Q & 15) || (ldq & 3))
     return cudaSuccess;
-  const GemmOut o{out, ldo, 0, w, 0, subtract ? 1 : 0};
+  const GemmOut o{out, ldo, 0, w, 0, subtract ? 1 : 0, nullptr, 0};
   *launched = launch_gemm<DT_F32>(Q, ldq, rows, l, B, ldb, o, PassGate{}, s);
   return cudaGetLastError();
 }

@@ -200,8 +200,14 @@ cudaError_t gram_launch(const void *Q, int64_t ldq, int dtype, int64_t rows, int
                         int32_t n_part, double *W, PassGate g, cudaStream_t s);
 
 // Q <- Q B in place on the tensor cores, B (l x l, FP32) upper triangular.
+// colsum (nullable): FP64 partial column sums of the stored Q, one row of l
+// per slot, gemm_colsum_parts(rows) slots (the all-ones projection of the
+// product that reads Q next); colsum_reduce_launch sums them in a fixed order.
 cudaError_t gemm_tri_inplace_launch(void *Q, int64_t ldq, int dtype, int64_t rows, int32_t l, const float *B,
-                                    int64_t ldb, PassGate g, cudaStream_t s);
+                                    int64_t ldb, PassGate g, cudaStream_t s, double *colsum = nullptr);
+int32_t gemm_colsum_parts(int64_t rows);
+cudaError_t colsum_reduce_launch(const double *partial, int32_t parts, int32_t ld, int32_t b, int32_t ldc, float *out,
+                                 cudaStream_t s);
 // Out[:, 0:w] = Q B[:, 0:w] on the tensor cores (3xTF32), Q rows x l FP32, or
 // with `subtract` Out[:, 0:w] -= Q B[:, 0:w] (Out must not overlap the columns
 // of Q); *launched = false (nothing enqueued) where the layout does not suit it.
@@ -288,6 +294,7 @@ struct OrthBufs {
   float *Rinv = nullptr;          // l x l FP32
   int32_t *state = nullptr;       // kOrthStateInts
   int32_t n_part = 0;
+  double *colsum = nullptr;       // nullable: gemm_colsum_parts(rows) x l column-sum partials of the result
 };
 isvd_status orth_enqueue(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, double *Racc, const OrthBufs &o,
                          isvd_info *info, cudaStream_t s);
@@ -374,6 +381,11 @@ struct ApplyScratch {
   void *z1 = nullptr, *z2 = nullptr, *p = nullptr;  // Horner temps, CONCAT P block
   float *lr_c = nullptr;
   double *lr_partial = nullptr;
+  // column sums of the input block already formed (by the orthonormalisation
+  // that wrote it): the all-ones projection reduces them instead of reading
+  // the block; ones_parts slots of ones_ld doubles
+  const double *ones_parts = nullptr;
+  int32_t ones_nparts = 0, ones_ld = 0;
   float *heavy_partial = nullptr;
   void *xdense = nullptr;  // dense-X products (CONCAT with dense X)
   void *gz = nullptr;      // row gather: the full-height product (n x b)

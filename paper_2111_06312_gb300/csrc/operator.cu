@@ -961,7 +961,10 @@ static isvd_status apply_poly(isvd_operator *op, const void *G, int64_t ldg, int
   // corrections: c = V^T G with the all-ones vector first (transpose swaps u and v)
   const int ones = d.ones_coeff != 0.0 ? 1 : 0;
   const int r = ones + d.lr_rank;
-  if (r > 0) {
+  if (r > 0 && ones && d.lr_rank == 0 && sc.ones_parts) {
+    // 1^T G from the column sums that the step writing G formed
+    ISVD_CUDA_TRY(colsum_reduce_launch(sc.ones_parts, sc.ones_nparts, sc.ones_ld, b, (int32_t)bseg, sc.lr_c, s));
+  } else if (r > 0) {
     const float *V = transpose ? d.lr_u : d.lr_v;
     ISVD_CUDA_TRY(lowrank_project_launch(G, ldg, dtype, op->n, b, d.lr_rank ? V : nullptr, d.lr_rank, r, ones,
                                          sc.lr_partial, lowrank_partials(op->n), sc.lr_c, bseg, s));

@@ -21,7 +21,7 @@ isvd_status orth_enqueue(void *Q, int64_t ldq, int dt, int64_t rows, int32_t l, 
     PassGate g{o.state, pass};
     ISVD_CUDA_TRY(gram_launch(Q, ldq, dt, rows, l, o.gram_partial, o.n_part, o.W, g, s));
     ISVD_CUDA_TRY(chol_inv_launch(o.W, l, rows, dt, o.Rinv, l, nullptr, Racc, o.tmp, o.state, info, pass, s));
-    ISVD_CUDA_TRY(gemm_tri_inplace_launch(Q, ldq, dt, rows, l, o.Rinv, l, g, s));
+    ISVD_CUDA_TRY(gemm_tri_inplace_launch(Q, ldq, dt, rows, l, o.Rinv, l, g, s, o.colsum));
   }
   return ISVD_OK;
 }
@@ -48,7 +48,7 @@ struct Carver {
 // OrthBufs for blocks of width l; above ISVD_MAX_BLOCK the CholeskyQR2
 // buffers serve the 128-column panels of the wide path, which adds its own
 // (`wide`, may be null when l <= ISVD_MAX_BLOCK).
-void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o, char **wide = nullptr) {
+void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o, char **wide = nullptr, bool colsum = false) {
   if (l > ISVD_MAX_BLOCK) {
     char *w = c.take<char>(wide_orth_bytes(rows, l));
     if (wide) *wide = w;
@@ -60,6 +60,7 @@ void carve_orth(Carver &c, int64_t rows, int32_t l, OrthBufs *o, char **wide = n
   o->tmp = c.take<double>((size_t)l * l);
   o->Rinv = c.take<float>((size_t)l * l);
   o->state = c.take<int32_t>(kOrthStateInts);
+  o->colsum = colsum ? c.take<double>((size_t)gemm_colsum_parts(rows) * l) : nullptr;
 }
 
 // Q (rows x l) <- its orthonormal factor: one CholeskyQR2 up to
@@ -107,7 +108,12 @@ size_t carve_svd(const isvd_operator *op, const SvdPlan &P, char *base, SvdBufs 
   }
   const size_t ab = std::max(apply_scratch_bytes(op, P.l, DT_F32, false), apply_scratch_bytes(op, P.l, DT_F32, true));
   b->apply_base = c.take<char>(ab);
-  carve_orth(c, std::max(rows, cols), P.l, &b->orth, &b->wide);
+  // the Q R^-1 passes also form the column sums of their result when the
+  // operator's next product wants 1^T Q (the all-ones term of a leaf)
+  const isvd_operator_desc &d = op->desc;
+  const bool colsum = P.l <= ISVD_MAX_BLOCK && op->compose < 0 && d.form == ISVD_FORM_POLY && d.ones_coeff != 0.0 &&
+                      d.lr_rank == 0 && !d.gather_rows && op->rows == op->cols;
+  carve_orth(c, std::max(rows, cols), P.l, &b->orth, &b->wide, colsum);
   b->Racc = c.take<double>((size_t)P.l * P.l);
   b->Uo = c.take<double>((size_t)P.l * P.l);
   b->Vo = c.take<double>((size_t)P.l * P.l);
@@ -119,10 +125,17 @@ size_t carve_svd(const isvd_operator *op, const SvdPlan &P, char *base, SvdBufs 
   return c.off;
 }
 
+// `fresh`: `in` is the block the last orthonormalisation wrote, whose column
+// sums that step formed
 isvd_status apply_step(isvd_operator *op, const void *in, void *out, int32_t l, int64_t ld, int dt, bool transpose,
-                       const SvdBufs &b, cudaStream_t s) {
+                       const SvdBufs &b, cudaStream_t s, bool fresh = false) {
   ApplyScratch sc;
   apply_scratch_carve(op, l, dt, transpose, b.apply_base, &sc);
+  if (fresh && b.orth.colsum) {
+    sc.ones_parts = b.orth.colsum;
+    sc.ones_nparts = gemm_colsum_parts(op->rows);  // rows == cols when colsum is carved
+    sc.ones_ld = l;
+  }
   return apply_impl(op, in, ld, l, out, ld, dt, transpose, sc, s);
 }
 
@@ -135,9 +148,9 @@ isvd_status svd_enqueue(isvd_operator *op, const SvdPlan &P, const SvdBufs &b, c
   // Q ~ N(0,1)^{c x l}
   ISVD_CUDA_TRY(gaussian_launch(P.seed, cols, P.l, b.qc, P.ld, dt, s));
   for (int it = 0; it < P.iters; ++it) {
-    ISVD_TRY(apply_step(op, b.qc, b.qr, P.l, P.ld, dt, false, b, s));  // M Q
+    ISVD_TRY(apply_step(op, b.qc, b.qr, P.l, P.ld, dt, false, b, s, it > 0));  // M Q
     ISVD_TRY(orth_any(b.qr, P.ld, dt, rows, P.l, nullptr, b.orth, b.wide, info, s));
-    ISVD_TRY(apply_step(op, b.qr, b.qc, P.l, P.ld, dt, true, b, s));   // M^T Q
+    ISVD_TRY(apply_step(op, b.qr, b.qc, P.l, P.ld, dt, true, b, s, true));     // M^T Q
     ISVD_TRY(orth_any(b.qc, P.ld, dt, cols, P.l, nullptr, b.orth, b.wide, info, s));
   }
   if (mixed) {
@@ -148,10 +161,11 @@ isvd_status svd_enqueue(isvd_operator *op, const SvdPlan &P, const SvdBufs &b, c
                                                                                  b.qc32, n);
     ISVD_CUDA_TRY(cudaGetLastError());
   }
-  ISVD_TRY(apply_step(op, b.qc32, b.qr32, P.l, P.ld, DT_F32, false, b, s));
+  // (in mixed precision qc32 holds qc's values exactly: its column sums stand)
+  ISVD_TRY(apply_step(op, b.qc32, b.qr32, P.l, P.ld, DT_F32, false, b, s, P.iters > 0));
   ISVD_TRY(orth_any(b.qr32, P.ld, DT_F32, rows, P.l, nullptr, b.orth, b.wide, info, s));
   // B^T = M^T Q = Qt R  (CholeskyQR of B^T, R accumulated over the passes)
-  ISVD_TRY(apply_step(op, b.qr32, b.qc32, P.l, P.ld, DT_F32, true, b, s));
+  ISVD_TRY(apply_step(op, b.qr32, b.qc32, P.l, P.ld, DT_F32, true, b, s, true));
   ISVD_TRY(orth_any(b.qc32, P.ld, DT_F32, cols, P.l, b.Racc, b.orth, b.wide, info, s));
   // B = R^T Qt^T;  R = Uo S Vo^T  =>  B = Vo S (Qt Uo)^T:  U = Q Vo, V = Qt Uo
   ISVD_CUDA_TRY(small_svd_launch(b.Racc, P.l, b.Uo, b.So, b.Vo, b.jwork, /*Uk=*/b.Rk, /*Vk=*/b.Lk, /*Sk=*/P.S, P.k,
