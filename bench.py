@@ -537,13 +537,16 @@ def run_ours(args):
           "fp32": {"iters": q, "ms": ms, "max_rel_residual": float(err_fp32.max()),
                    "median_rel_residual": float(np.median(err_fp32))}}
     q_eq, err_m = None, None
+    tried = []
     for qm in range(q, q + 6):
         svd_fn("mixed", qm)()
         checked_status()
         e = relative_residuals(op, U, S, V)
+        tried.append({"iters": qm, "max_rel_residual": float(e.max())})
         if e.max() <= err_fp32.max():
             q_eq, err_m = qm, e
             break
+    eq["mixed_tried"] = tried
     if q_eq is not None:
         fn = svd_fn("mixed", q_eq)
         for _ in range(max(1, args.warmup)):
