@@ -688,6 +688,39 @@ def run_case_orth(args):
                       "orthogonality": orth, "passes": passes}), flush=True)
 
 
+def run_case_wide(args):
+    """The rank-256 SVD with the paper's l = 2k = 512 (FP32) on the default
+    workload, alone (a profiling case): one JSON line with its time per SVD
+    and its error; the timed SVDs run inside the NVTX range "wide_svd"."""
+    import torch
+
+    from paper_2111_06312_gb300 import build as libbuild
+    from paper_2111_06312_gb300 import isvd
+
+    libbuild.build()
+    desc, _, _, q = WORKLOADS[args.workload]
+    g = load_graph(args.workload)
+    k, p = 256, 256
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    with isvd.graph_operator(g, coeffs=coeffs5(), ones_coeff=-LAM) as op:
+        U = isvd.new_block(g.n, k)
+        V = isvd.new_block(g.n, k)
+        S = torch.empty(k, device="cuda")
+        info = torch.zeros(4, dtype=torch.int32, device="cuda")
+        fn = lambda: op.svd(k, p, q, seed=SEED, U=U, S=S, V=V, info=info, check=False)  # noqa: E731
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("wide_svd")
+        ms = timed_steps(fn, args.steps, flush, stream)
+        torch.cuda.nvtx.range_pop()
+        err = relative_residuals(op, U, S, V)
+        st = isvd.info_dict(info)
+    print(json.dumps({"case": "wide", "k": k, "oversample": p, "iters": q, "width": k + p, "ms": float(np.mean(ms)),
+                      "step_ms": ms, "max_rel_residual": float(err.max()), "device_status": st}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -698,13 +731,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and fine-tuning sections")
-    ap.add_argument("--case", choices=["svd", "orth"], default="svd",
-                    help="orth: only the CholeskyQR2 of a --rows x --width block (a profiling case)")
+    ap.add_argument("--case", choices=["svd", "orth", "wide"], default="svd",
+                    help="orth: only the CholeskyQR2 of a --rows x --width block; wide: only the rank-256, "
+                         "l = 512 SVD (profiling cases)")
     ap.add_argument("--rows", type=int, default=1_000_000)
     ap.add_argument("--width", type=int, default=144)
     args = ap.parse_args()
     if args.case == "orth":
         run_case_orth(args)
+    elif args.case == "wide":
+        run_case_wide(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
