@@ -146,3 +146,39 @@ def test_binding_declares_every_entry_point():
     for name in re.findall(r"ISVD_API\s+isvd_status\s+(isvd_\w+)\s*\(", src):
         assert getattr(L, name).restype is C.c_int, f"{name} should return int"
     assert L.isvd_get_tuning(None, None) == 1  # null operator: rejected on the host
+
+
+def _header():
+    return open(os.path.join(ROOT, "include", "isvd.h")).read()
+
+
+def test_binding_constants_match_the_header():
+    from paper_2111_06312_gb300 import isvd
+
+    src = _header()
+    defines = dict(re.findall(r"#define\s+(ISVD_\w+)\s+(\d+)", src))
+    assert int(defines["ISVD_MAX_BLOCK"]) == isvd.MAX_BLOCK
+    assert int(defines["ISVD_MAX_BLOCK_WIDE"]) == isvd.MAX_BLOCK_WIDE
+    assert int(defines["ISVD_PERSISTENT_MAX_BLOCK"]) <= isvd.MAX_BLOCK
+
+
+def test_persistent_options_layout_matches_the_header():
+    """The ctypes mirror of isvd_persistent_options has the header's fields in
+    the header's order (a reordering would pass garbage without an error)."""
+    from paper_2111_06312_gb300 import isvd
+
+    src = _header()
+    end = src.index("} isvd_persistent_options;")
+    body = src[src.rindex("typedef struct {", 0, end):end]
+    fields = re.findall(r"int32_t\s+(\w+);", body)
+    assert fields == [f[0] for f in isvd._PersistentOptions._fields_]
+
+
+def test_persistent_batch_rejects_bad_arguments_on_the_host(libisvd):
+    libisvd.isvd_svd_batched_persistent.restype = C.c_int
+    libisvd.isvd_svd_batched_persistent.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                                    C.c_uint64] + [C.c_void_p] * 6
+    assert libisvd.isvd_svd_batched_persistent(None, None, 1, 4, 1, 0, None, None, None, None, None, None) == 1
+    k = (C.c_int32 * 1)(4)
+    ops = (C.c_void_p * 1)(None)
+    assert libisvd.isvd_svd_batched_persistent(ops, k, 0, 4, 1, 0, ops, ops, ops, None, None, None) == 1
